@@ -54,7 +54,7 @@ def lib():
         L.or_cells.argtypes = [C.POINTER(OrCube), C.POINTER(OrSource), C.c_void_p]
         L.or_cells.restype = None
         L.or_stack.argtypes = [C.POINTER(OrCube), C.POINTER(OrSource), C.c_int32, C.c_void_p,
-                               C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                               C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
                                C.POINTER(OrStats), C.c_int32]
         _lib = L
     return _lib
@@ -135,8 +135,9 @@ def cells(cube, src):
     return out
 
 
-def stack(cube, sources, iv_select=None, nthreads=1):
-    """Returns dict(sum_wv complex128, sum_w, sum_wvv, count uint64, stats, planes)."""
+def stack(cube, sources, iv_select=None, nthreads=1, with_abs=False):
+    """Returns dict(sum_wv complex128, sum_w, sum_wvv, count uint64, stats, planes,
+    and with with_abs=True sum_wabs = sum W w |V|, the scale of the sum_wv bound)."""
     nplanes = cube.nv
     sel = None
     if iv_select is not None:
@@ -148,16 +149,17 @@ def stack(cube, sources, iv_select=None, nthreads=1):
     sum_w = np.zeros(shape, dtype=np.float64)
     sum_wvv = np.zeros(shape, dtype=np.float64)
     count = np.zeros(shape, dtype=np.uint64)
+    sum_wabs = np.zeros(shape, dtype=np.float64) if with_abs else None
     arr = (OrSource * max(1, len(sources)))(*[s.c for s in sources])
     st = OrStats()
     rc = lib().or_stack(C.byref(cube), arr, len(sources), _ptr(sel), _ptr(sum_wv), _ptr(sum_w),
-                        _ptr(sum_wvv), _ptr(count), C.byref(st), int(nthreads))
+                        _ptr(sum_wvv), _ptr(sum_wabs), _ptr(count), C.byref(st), int(nthreads))
     if rc != 0:
         raise ValueError("oracle stack failed (%d)" % rc)
     planes = np.arange(cube.nv) if sel is None else np.nonzero(sel)[0]
     return {"sum_wv": sum_wv[..., 0] + 1j * sum_wv[..., 1], "sum_w": sum_w, "sum_wvv": sum_wvv,
-            "count": count, "stats": st.as_dict() if iv_select is None else None,
-            "planes": planes}
+            "sum_wabs": sum_wabs, "count": count,
+            "stats": st.as_dict() if iv_select is None else None, "planes": planes}
 
 
 def default_threads():

@@ -272,7 +272,7 @@ typedef struct {
     chan_tab *const *tabs;
     const int32_t *sel_map;  /* iv -> compact plane index, -1 = not selected */
     int32_t tid, nthreads;
-    double *sum_wv, *sum_w, *sum_wvv;
+    double *sum_wv, *sum_w, *sum_wvv, *sum_wabs;
     uint64_t *count;
     or_stats st;
 } job_t;
@@ -345,6 +345,7 @@ static void *stack_worker(void *arg)
                         jb->sum_wv[2 * ci_ + 1] += ww * sim;
                         jb->sum_w[ci_] += ww;
                         jb->sum_wvv[ci_] += ww * a2;
+                        if (jb->sum_wabs) jb->sum_wabs[ci_] += ww * sqrt(a2);
                         jb->count[ci_] += 1;
                         if (!jb->sel_map) jb->st.w_cube += ww;
                     }
@@ -361,13 +362,15 @@ static void *stack_worker(void *arg)
  *              planes, in increasing iv (sampled parity at large sizes).
  *   outputs:   sum_wv [planes][nu][nrest][npol][2], sum_w / sum_wvv / count
  *              [planes][nu][nrest][npol].
+ *   sum_wabs:  optional (may be NULL): sum of W w_kj |V| per cell, the scale
+ *              of the cancellation-aware error bound on sum_wv.
  *   stats:     filled only when iv_select is NULL.
  *   nthreads:  worker threads; thread t owns the planes iv with iv % T == t,
  *              so no two threads write the same output and the result does
  *              not depend on T.
  * Returns 0, or negative on bad input / allocation failure. */
 int or_stack(const or_cube *c, const or_source *srcs, int32_t nsrc, const uint8_t *iv_select,
-             double *sum_wv, double *sum_w, double *sum_wvv, uint64_t *count,
+             double *sum_wv, double *sum_w, double *sum_wvv, double *sum_wabs, uint64_t *count,
              or_stats *stats, int32_t nthreads)
 {
     if (nthreads < 1) nthreads = 1;
@@ -412,7 +415,7 @@ int or_stack(const or_cube *c, const or_source *srcs, int32_t nsrc, const uint8_
         else {
             for (int t = 0; t < nthreads; ++t) {
                 jobs[t] = (job_t){c, srcs, nsrc, tabs, sel_map, t, nthreads,
-                                  sum_wv, sum_w, sum_wvv, count, {0}};
+                                  sum_wv, sum_w, sum_wvv, sum_wabs, count, {0}};
             }
             for (int t = 1; t < nthreads; ++t) pthread_create(&th[t], NULL, stack_worker, &jobs[t]);
             stack_worker(&jobs[0]);
