@@ -1,0 +1,229 @@
+/*
+ * vista.h -- C ABI of libvista, GB300-native visibility stacking in the
+ * Fourier domain (the hot path of ViSta, arxiv 2609.01897).
+ *
+ * For every source, row, channel and polarisation the library
+ *   1. phase-shifts the visibility to the source position
+ *      V' = V exp(+2 pi i nu_k tau / c),  tau = u l + v m + w (sqrt(1-l^2-m^2) - 1)
+ *      (paper Eq. 2 with the rotation of Eq. 1 taken as the identity; the sign
+ *      makes a point source at (l, m) real),
+ *   2. maps the observed channel to the rest frame, nu_rest = nu_obs (1+z)
+ *      (Eq. 1's frequency scaling), spreading it over the output bins of a
+ *      common rest lattice with the channel-overlap weights of Eqs. 3-4,
+ *   3. accumulates sum W w_kj V', sum W w_kj, sum W w_kj |V|^2 and a count into
+ *      a cube [nv][nu][nrest][npol] of uv cells x rest channels x pol planes.
+ *
+ * Conventions shared by every call
+ *   - Every call returns VISTA_OK (0) or a negative VISTA_E_* status.  A
+ *     failing call leaves the handle as it was.  vista_last_error() gives a
+ *     one-line reason.
+ *   - A handle is used by one host thread at a time.
+ *   - Device work is asynchronous on the stream given at open; only
+ *     vista_read_cube(), vista_get_stats() and vista_close() wait for it.
+ *   - Sizes are element counts, not bytes.
+ */
+#ifndef VISTA_H
+#define VISTA_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define VISTA_ABI_VERSION 1
+#define VISTA_MAX_BINS 4      /* rest bins one input channel may touch */
+#define VISTA_MAX_POL 4
+
+enum {
+    VISTA_OK = 0,
+    VISTA_E_ARG = -1,      /* invalid argument or descriptor field */
+    VISTA_E_STATE = -2,    /* call not valid in the handle's state, or unknown/closed handle */
+    VISTA_E_NOMEM = -3,    /* host or device allocation failed */
+    VISTA_E_CUDA = -4,     /* a CUDA runtime call failed */
+    VISTA_E_RANGE = -5,    /* inputs exceed a supported size */
+    VISTA_E_TIMEOUT = -6   /* a bounded device-side wait gave up (reported by read/stats) */
+};
+
+enum { VISTA_VIS_C64 = 0, VISTA_VIS_C128 = 1, VISTA_VIS_F16X2 = 2, VISTA_VIS_BF16X2 = 3 };
+enum { VISTA_BIN_OVERLAP = 0, VISTA_BIN_NEAREST = 1 };
+enum { VISTA_PREC_MIXED = 0, VISTA_PREC_FP64 = 1 };
+enum { VISTA_MEM_DEVICE = 0, VISTA_MEM_HOST = 1 };
+
+typedef struct vista_stack vista_stack;   /* opaque handle */
+
+/* The output cube.
+ *   nu, nv     uv cells along u and v; even, >= 2.  Cell iu holds
+ *              floor(u_lambda / du) + nu/2 (and the same for v).
+ *   nrest      rest-frame output channels, >= 1.
+ *   npol       cube polarisation planes, 1..4.
+ *   du, dv     uv cell size in wavelengths, > 0.
+ *   rest_f0    lower edge of rest bin 0, Hz (used when rest_df > 0).
+ *   rest_df    rest bin width, Hz; 0 selects the paper's rule (Sec. 3.1):
+ *              the widest rest-frame input channel of the sources added
+ *              before the first vista_run(), with the lattice centred on
+ *              central_freq.  The lattice is fixed at the first run.
+ *   central_freq  Hz, used only when rest_df == 0.
+ *   bin_mode   VISTA_BIN_OVERLAP (Eqs. 3-4) or VISTA_BIN_NEAREST.
+ *   precision  VISTA_PREC_MIXED: FP64 geometry, tables and phase seeds,
+ *              FP32 per-visibility body, FP32 cube; VISTA_PREC_FP64: the
+ *              plain form, FP64 throughout with an FP64 cube.
+ *   hermitian_fold  1: rows with v < 0 (or v == 0, u < 0) are negated and
+ *              their shifted visibility conjugated before binning.
+ *   stream     cudaStream_t for all device work (NULL = legacy default stream). */
+typedef struct {
+    int32_t nu, nv, nrest, npol;
+    double du, dv;
+    double rest_f0, rest_df;
+    double central_freq;
+    int32_t bin_mode, precision, hermitian_fold, reserved0;
+    void *stream;
+} vista_cube_desc;
+
+/* One (source, spectral window).
+ *   nrow, nchan, npol  nrow >= 0; nchan >= 1 (>= 2 in overlap mode, which
+ *              needs a channel width); npol in {1, 2, 4}.
+ *   uvw        [nrow][3] float64, metres.
+ *   freqs      HOST [nchan] float64, observed channel centres in Hz, finite,
+ *              > 0, strictly monotone (either direction).  Copied by the call.
+ *   vis        [nrow][nchan][npol] complex values of type vis_type:
+ *              C64 (2 x float32), C128 (2 x float64), F16X2 / BF16X2
+ *              (2 x 16-bit, value = stored * vis_scale).  Base address
+ *              aligned to the size of one channel's npol values, capped
+ *              at 16 bytes.
+ *   vis_scale  dequantisation scale of the 16-bit types (ignored otherwise).
+ *   weights    [nrow][npol] float32, >= 0 (the MS WEIGHT column).
+ *   flags      [nrow][nchan][npol] uint8, nonzero = flagged; NULL = none.
+ *   pol_map    HOST [npol] int32: cube plane of each input pol, -1 = skip;
+ *              NULL = identity (needs npol <= cube npol).  Copied by the call.
+ *   l, m       direction cosines of the source relative to the phase
+ *              centre, l^2 + m^2 < 1.
+ *   z          redshift, > -1.
+ *   mem        VISTA_MEM_DEVICE: uvw/vis/weights/flags are device pointers,
+ *              borrowed: they must stay valid and unchanged until the stream
+ *              work of the vista_run() that consumes them has completed.
+ *              VISTA_MEM_HOST: they are host pointers (pinned memory gives
+ *              asynchronous copies); vista_run() copies them to device
+ *              buffers owned by the handle, and they must stay valid until
+ *              vista_run() returns. */
+typedef struct {
+    int64_t nrow;
+    int32_t nchan, npol;
+    const double *uvw;
+    const double *freqs;
+    const void *vis;
+    int32_t vis_type;
+    float vis_scale;
+    const float *weights;
+    const uint8_t *flags;
+    const int32_t *pol_map;
+    double l, m, z;
+    int32_t mem, reserved0;
+} vista_source_desc;
+
+/* Counters over the visibilities of every channel that reaches the cube
+ * (at least one rest bin inside [0, nrest)) and every mapped pol, summed
+ * over all runs since open (or the last vista_zero_cube()). */
+typedef struct {
+    uint64_t n_vis;         /* visibilities read */
+    uint64_t n_flagged;     /* of those, flagged */
+    uint64_t n_dropped_uv;  /* unflagged, outside the uv grid */
+    uint64_t n_stacked;     /* unflagged, accumulated into the cube */
+} vista_stats;
+
+/* Launch shape of the mixed-precision path (0 fields = library default).
+ *   rows_per_item   rows one warp walks through per work item.
+ *   chans_per_lane  channels per lane in one item (item = 32 x this many
+ *                   channels); also the FP32 phasor recurrence length
+ *                   between FP64-derived seeds.
+ *   warps_per_cta   warps per block of the stacking kernel.
+ *   sort_rows       1: order rows by uv cell before stacking (fewer
+ *                   global reductions), 0: stack in input order. */
+typedef struct {
+    int32_t rows_per_item, chans_per_lane, warps_per_cta, sort_rows;
+} vista_tuning;
+
+/* Open a cube (zeroed) on the current CUDA device.  Allocates the cube.
+ * E_ARG on an invalid descriptor, E_NOMEM / E_CUDA on allocation failure.
+ * On failure *out is set to NULL and vista_last_error(NULL) has the reason. */
+int vista_open_stack(const vista_cube_desc *desc, vista_stack **out);
+
+/* Queue one (source, spectral window) for the next vista_run().  Validates
+ * every host-visible field (sizes, freqs, l, m, z, pol_map, pointer
+ * alignment); the contents of device arrays are not inspected. */
+int vista_add_source(vista_stack *h, const vista_source_desc *src);
+
+/* Stack every queued source into the cube (additive across runs) and clear
+ * the queue.  Host planning happens here; device work is queued on the
+ * stream and the call returns without waiting for it (except that host-memory
+ * sources are copied before it returns).  E_STATE if nothing is queued,
+ * E_RANGE if a channel would touch more than VISTA_MAX_BINS rest bins. */
+int vista_run(vista_stack *h);
+
+/* Wait for the stream, then copy the cube out.  Any pointer may be NULL to
+ * skip that array.  Layout [nv][nu][nrest][npol] (sum_wv with a trailing
+ * [2] = re, im).  dst_is_device: 1 = device pointers, 0 = host.  Returns
+ * E_TIMEOUT if a device-side wait of an earlier run gave up. */
+int vista_read_cube(vista_stack *h, float *sum_wv, float *sum_w, float *sum_wvv,
+                    uint32_t *count, int dst_is_device);
+
+/* As vista_read_cube() with float64 sums (exact copies of the FP64 cube of
+ * VISTA_PREC_FP64; widened from FP32 for VISTA_PREC_MIXED). */
+int vista_read_cube_f64(vista_stack *h, double *sum_wv, double *sum_w, double *sum_wvv,
+                        uint32_t *count, int dst_is_device);
+
+/* Zero the cube and the counters (the lattice stays fixed). */
+int vista_zero_cube(vista_stack *h);
+
+/* Wait for the stream and copy the counters. */
+int vista_get_stats(vista_stack *h, vista_stats *out);
+
+/* The rest lattice in use (after the first run; E_STATE before it unless
+ * the descriptor fixed rest_df). */
+int vista_get_lattice(vista_stack *h, double *rest_f0, double *rest_df);
+
+int vista_set_tuning(vista_stack *h, const vista_tuning *t);
+int vista_get_tuning(vista_stack *h, vista_tuning *t);
+
+/* Wait for the stream, free every device and host resource, and forget the
+ * handle; any later call with it returns E_STATE. */
+int vista_close(vista_stack *h);
+
+/* One-line reason for the last failure on h (NULL: the calling thread's last
+ * failure without a handle).  Valid until the next call on the same handle. */
+const char *vista_last_error(const vista_stack *h);
+
+int vista_abi_version(void);
+
+/* ---- host-only planner entry points (no GPU needed) ---------------------
+ * The FP64 tables the library builds, exposed for inspection and tests. */
+
+/* Rest lattice of Sec. 3.1 for nsrc windows: width = max over windows and
+ * channels of Delta nu_k (1+z), lower edge = central_freq - (nrest/2) width. */
+int vista_plan_lattice(const double *const *freqs, const int32_t *nchan, const double *z,
+                       int32_t nsrc, int32_t nrest, double central_freq,
+                       double *rest_f0, double *rest_df);
+
+/* Rest bins of every channel of one window (Eqs. 3-4, or nearest): for
+ * channel k, bins j0[k] .. j0[k]+nb[k]-1 inside [0, nrest) carry the weights
+ * w[k*VISTA_MAX_BINS + b]; nb[k] = 0 when none.  E_RANGE if a channel touches
+ * more than VISTA_MAX_BINS bins. */
+int vista_plan_channels(const double *freqs, int32_t nchan, double z, double rest_f0,
+                        double rest_df, int32_t nrest, int32_t bin_mode,
+                        int32_t *j0, int32_t *nb, double *w);
+
+/* ---- debug exports of the device arithmetic -------------------------------
+ * Run the mixed (or FP64) path's own phase and cell code for source `src`
+ * (index among the sources of the last vista_run, in add order) and write,
+ * for every row and every channel the path reads, the phasor exp(+2 pi i
+ * nu_k tau / c) as [nrow][nchan][2] float64, or the cell (iu, iv) as
+ * [nrow][nchan][2] int32 ((-1, -1) outside the grid).  Entries of channels
+ * the path does not read are left untouched.  dst is a device pointer. */
+int vista_debug_phasors(vista_stack *h, int32_t src, double *dst);
+int vista_debug_cells(vista_stack *h, int32_t src, int32_t *dst);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* VISTA_H */

@@ -1,0 +1,716 @@
+// libvista C ABI: handle life cycle, validation, host planning and launch
+// orchestration (see include/vista.h for the contract of every call).
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <set>
+#include <string>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "planner.h"
+#include "vista.h"
+#include "vista_internal.h"
+
+using namespace vista;
+
+namespace {
+
+thread_local std::string g_err;
+std::mutex g_mu;
+std::set<const vista_stack *> g_live;
+
+struct DevBuf {
+    void *p = nullptr;
+    size_t cap = 0;
+    cudaError_t ensure(size_t bytes)
+    {
+        if (bytes <= cap) return cudaSuccess;
+        if (p) cudaFree(p);
+        p = nullptr;
+        cap = 0;
+        size_t want = bytes + bytes / 8 + 256;   // some headroom against regrowth
+        cudaError_t e = cudaMalloc(&p, want);
+        if (e == cudaSuccess) cap = want;
+        return e;
+    }
+    void release()
+    {
+        if (p) cudaFree(p);
+        p = nullptr;
+        cap = 0;
+    }
+};
+
+struct SrcHost {
+    vista_source_desc d;
+    std::vector<double> freqs;
+    std::vector<int32_t> pol_map;   // npol entries (identity filled in)
+};
+
+// One launch class of a run: windows that share (vis_type, npol).
+struct ClassRun {
+    int npol_vt = 0;
+    RunArgs args{};
+    std::vector<int> members;       // run-order index of each window
+};
+
+bool is_fin(double x) { return std::isfinite(x); }
+
+}  // namespace
+
+struct vista_stack {
+    vista_cube_desc desc{};
+    cudaStream_t stream = nullptr;
+    int device = 0;
+    bool lattice_fixed = false;
+    double f0 = 0.0, df = 0.0;
+    std::vector<SrcHost> pending, last;
+    void *cube = nullptr;
+    uint32_t *count = nullptr;
+    int64_t nentries = 0;
+    DevStats *stats = nullptr;
+    int32_t *err = nullptr;
+    DevBuf b_srcs, b_chf, b_chd, b_recs, b_off, b_stage, b_unpack;
+    std::vector<ClassRun> classes;
+    LaunchCfg cfg{64, 4, 4, 0};
+    std::string msg;
+};
+
+namespace {
+
+int fail(vista_stack *h, int code, const char *fmt, ...) __attribute__((format(printf, 3, 4)));
+int fail(vista_stack *h, int code, const char *fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    if (h)
+        h->msg = buf;
+    else
+        g_err = buf;
+    return code;
+}
+
+int cuda_fail(vista_stack *h, cudaError_t e, const char *what)
+{
+    return fail(h, e == cudaErrorMemoryAllocation ? VISTA_E_NOMEM : VISTA_E_CUDA, "%s: %s", what,
+                cudaGetErrorString(e));
+}
+
+bool live(const vista_stack *h)
+{
+    std::lock_guard<std::mutex> lk(g_mu);
+    return h && g_live.count(h) != 0;
+}
+
+#define CHECK_HANDLE(h)                                                                \
+    do {                                                                               \
+        if (!live(h)) return fail(nullptr, VISTA_E_STATE, "unknown or closed handle"); \
+    } while (0)
+
+size_t vis_elem_bytes(int vt)
+{
+    switch (vt) {
+    case VISTA_VIS_C64: return 8;
+    case VISTA_VIS_C128: return 16;
+    default: return 4;
+    }
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------ open
+
+extern "C" int vista_abi_version(void) { return VISTA_ABI_VERSION; }
+
+extern "C" int vista_open_stack(const vista_cube_desc *d, vista_stack **out)
+{
+    if (out) *out = nullptr;
+    if (!d || !out) return fail(nullptr, VISTA_E_ARG, "null descriptor or output pointer");
+    if (d->nu < 2 || d->nv < 2 || (d->nu & 1) || (d->nv & 1))
+        return fail(nullptr, VISTA_E_ARG, "nu and nv must be even and >= 2 (got %d, %d)", d->nu, d->nv);
+    if (d->nrest < 1) return fail(nullptr, VISTA_E_ARG, "nrest must be >= 1");
+    if (d->npol < 1 || d->npol > VISTA_MAX_POL) return fail(nullptr, VISTA_E_ARG, "npol must be 1..4");
+    if (!(d->du > 0.0) || !(d->dv > 0.0) || !is_fin(d->du) || !is_fin(d->dv))
+        return fail(nullptr, VISTA_E_ARG, "du and dv must be finite and > 0");
+    if (!(d->rest_df >= 0.0) || !is_fin(d->rest_df))
+        return fail(nullptr, VISTA_E_ARG, "rest_df must be finite and >= 0");
+    if (d->rest_df > 0.0 && !is_fin(d->rest_f0)) return fail(nullptr, VISTA_E_ARG, "rest_f0 must be finite");
+    if (d->rest_df == 0.0 && !(is_fin(d->central_freq) && d->central_freq > 0.0))
+        return fail(nullptr, VISTA_E_ARG, "central_freq must be finite and > 0 when rest_df == 0");
+    if (d->bin_mode != VISTA_BIN_OVERLAP && d->bin_mode != VISTA_BIN_NEAREST)
+        return fail(nullptr, VISTA_E_ARG, "bad bin_mode %d", d->bin_mode);
+    if (d->precision != VISTA_PREC_MIXED && d->precision != VISTA_PREC_FP64)
+        return fail(nullptr, VISTA_E_ARG, "bad precision %d", d->precision);
+    if (d->hermitian_fold != 0 && d->hermitian_fold != 1)
+        return fail(nullptr, VISTA_E_ARG, "hermitian_fold must be 0 or 1");
+    const int64_t ncell = (int64_t)d->nu * d->nv;
+    if (ncell > (int64_t)0x7fffffff) return fail(nullptr, VISTA_E_RANGE, "nu*nv exceeds 2^31-1");
+    const int64_t n = ncell * d->nrest * d->npol;
+
+    vista_stack *h = new (std::nothrow) vista_stack();
+    if (!h) return fail(nullptr, VISTA_E_NOMEM, "host allocation failed");
+    h->desc = *d;
+    h->stream = (cudaStream_t)d->stream;
+    h->nentries = n;
+    if (d->rest_df > 0.0) {
+        h->lattice_fixed = true;
+        h->f0 = d->rest_f0;
+        h->df = d->rest_df;
+    }
+    cudaError_t e = cudaGetDevice(&h->device);
+    const size_t esz = d->precision == VISTA_PREC_FP64 ? 32 : 16;
+    if (e == cudaSuccess) e = cudaMalloc(&h->cube, (size_t)n * esz);
+    if (e == cudaSuccess) e = cudaMalloc((void **)&h->count, (size_t)n * sizeof(uint32_t));
+    if (e == cudaSuccess) e = cudaMalloc((void **)&h->stats, sizeof(DevStats));
+    if (e == cudaSuccess) e = cudaMalloc((void **)&h->err, sizeof(int32_t));
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->cube, 0, (size_t)n * esz, h->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->count, 0, (size_t)n * sizeof(uint32_t), h->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->stats, 0, sizeof(DevStats), h->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->err, 0, sizeof(int32_t), h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) {
+        int rc = cuda_fail(nullptr, e, "cube allocation");
+        cudaFree(h->cube);
+        cudaFree(h->count);
+        cudaFree(h->stats);
+        cudaFree(h->err);
+        delete h;
+        return rc;
+    }
+    {
+        std::lock_guard<std::mutex> lk(g_mu);
+        g_live.insert(h);
+    }
+    *out = h;
+    return VISTA_OK;
+}
+
+// ------------------------------------------------------------- add source
+
+extern "C" int vista_add_source(vista_stack *h, const vista_source_desc *s)
+{
+    CHECK_HANDLE(h);
+    if (!s) return fail(h, VISTA_E_ARG, "null source descriptor");
+    const vista_cube_desc &c = h->desc;
+    if (s->nrow < 0) return fail(h, VISTA_E_ARG, "nrow must be >= 0");
+    if (s->nrow > (int64_t)0x7fffffff) return fail(h, VISTA_E_RANGE, "nrow exceeds 2^31-1");
+    if (s->nchan < 1) return fail(h, VISTA_E_ARG, "nchan must be >= 1");
+    if (c.bin_mode == VISTA_BIN_OVERLAP && s->nchan < 2)
+        return fail(h, VISTA_E_ARG, "overlap binning needs >= 2 channels (channel width from centred differences)");
+    if (s->npol != 1 && s->npol != 2 && s->npol != 4) return fail(h, VISTA_E_ARG, "npol must be 1, 2 or 4");
+    if (s->vis_type < VISTA_VIS_C64 || s->vis_type > VISTA_VIS_BF16X2)
+        return fail(h, VISTA_E_ARG, "bad vis_type %d", s->vis_type);
+    if ((s->vis_type == VISTA_VIS_F16X2 || s->vis_type == VISTA_VIS_BF16X2) &&
+        !(std::isfinite(s->vis_scale) && s->vis_scale > 0.0f))
+        return fail(h, VISTA_E_ARG, "vis_scale must be finite and > 0 for 16-bit visibilities");
+    if (s->mem != VISTA_MEM_DEVICE && s->mem != VISTA_MEM_HOST) return fail(h, VISTA_E_ARG, "bad mem %d", s->mem);
+    if (!s->freqs) return fail(h, VISTA_E_ARG, "freqs is NULL");
+    if (s->nrow > 0 && (!s->uvw || !s->vis || !s->weights))
+        return fail(h, VISTA_E_ARG, "uvw, vis and weights must be non-NULL when nrow > 0");
+    if (!(is_fin(s->l) && is_fin(s->m) && s->l * s->l + s->m * s->m < 1.0))
+        return fail(h, VISTA_E_ARG, "need finite l, m with l^2 + m^2 < 1");
+    if (!(is_fin(s->z) && s->z > -1.0)) return fail(h, VISTA_E_ARG, "need finite z > -1");
+    for (int32_t k = 0; k < s->nchan; ++k) {
+        const double f = s->freqs[k];
+        if (!(is_fin(f) && f > 0.0)) return fail(h, VISTA_E_ARG, "freqs[%d] is not finite and > 0", k);
+    }
+    if (s->nchan >= 2) {
+        const bool up = s->freqs[1] > s->freqs[0];
+        for (int32_t k = 1; k < s->nchan; ++k) {
+            const bool ok = up ? s->freqs[k] > s->freqs[k - 1] : s->freqs[k] < s->freqs[k - 1];
+            if (!ok) return fail(h, VISTA_E_ARG, "freqs must be strictly monotone (index %d)", k);
+        }
+    }
+    SrcHost sh;
+    sh.d = *s;
+    sh.freqs.assign(s->freqs, s->freqs + s->nchan);
+    sh.pol_map.resize((size_t)s->npol);
+    for (int p = 0; p < s->npol; ++p) {
+        const int32_t q = s->pol_map ? s->pol_map[p] : p;
+        if (q < -1 || q >= c.npol)
+            return fail(h, VISTA_E_ARG, "pol %d maps to plane %d outside [-1, %d)", p, q, c.npol);
+        sh.pol_map[(size_t)p] = q;
+    }
+    if (s->mem == VISTA_MEM_DEVICE && s->nrow > 0) {
+        const size_t ve = vis_elem_bytes(s->vis_type) * (size_t)s->npol;
+        const size_t va = ve < 16 ? ve : 16;
+        if ((uintptr_t)s->vis % va) return fail(h, VISTA_E_ARG, "vis must be %zu-byte aligned", va);
+        if ((uintptr_t)s->uvw % 8) return fail(h, VISTA_E_ARG, "uvw must be 8-byte aligned");
+        if ((uintptr_t)s->weights % 4) return fail(h, VISTA_E_ARG, "weights must be 4-byte aligned");
+        if (s->flags && ((uintptr_t)s->flags % (size_t)s->npol))
+            return fail(h, VISTA_E_ARG, "flags must be %d-byte aligned", s->npol);
+    }
+    sh.d.freqs = nullptr;
+    sh.d.pol_map = nullptr;
+    h->pending.push_back(std::move(sh));
+    return VISTA_OK;
+}
+
+// -------------------------------------------------------------------- run
+
+namespace {
+
+struct Plan {
+    int32_t k_lo = 0, k_hi = 0;
+    bool linear = true;
+    double step = 0.0;
+    std::vector<ChanF> chf;
+    std::vector<ChanD> chd;
+};
+
+int plan_source(vista_stack *h, const SrcHost &s, double gu, double gv, Plan &pl)
+{
+    const int32_t n = s.d.nchan;
+    std::vector<int32_t> j0((size_t)n), nb((size_t)n);
+    std::vector<double> w((size_t)n * VISTA_MAX_BINS);
+    int rc = channel_bins(s.freqs.data(), n, s.d.z, h->f0, h->df, h->desc.nrest, h->desc.bin_mode, j0.data(),
+                          nb.data(), w.data());
+    if (rc == VISTA_E_RANGE)
+        return fail(h, VISTA_E_RANGE, "a channel touches more than %d rest bins (rest_df too small)",
+                    VISTA_MAX_BINS);
+    if (rc != VISTA_OK) return fail(h, rc, "channel planning failed");
+    int32_t lo = -1, hi = -1;
+    for (int32_t k = 0; k < n; ++k)
+        if (nb[(size_t)k] > 0) {
+            if (lo < 0) lo = k;
+            hi = k + 1;
+        }
+    if (lo < 0) lo = hi = 0;
+    pl.k_lo = lo;
+    pl.k_hi = hi;
+    pl.linear = linear_axis(s.freqs.data(), n, &pl.step);
+    pl.chf.resize((size_t)(hi - lo));
+    pl.chd.resize((size_t)(hi - lo));
+    for (int32_t k = lo; k < hi; ++k) {
+        ChanD &d = pl.chd[(size_t)(k - lo)];
+        ChanF &f = pl.chf[(size_t)(k - lo)];
+        d.su = s.freqs[(size_t)k] * gu;
+        d.sv = s.freqs[(size_t)k] * gv;
+        d.nu = s.freqs[(size_t)k];
+        d.j0 = j0[(size_t)k];
+        d.nb = nb[(size_t)k];
+        f.su = (float)d.su;
+        f.sv = (float)d.sv;
+        f.j0 = d.j0;
+        f.nb = d.nb;
+        for (int b = 0; b < VISTA_MAX_BINS; ++b) {
+            d.w[b] = w[(size_t)k * VISTA_MAX_BINS + b];
+            f.w[b] = (float)d.w[b];
+        }
+    }
+    return VISTA_OK;
+}
+
+template <typename T>
+cudaError_t upload(DevBuf &b, const std::vector<T> &v, cudaStream_t st)
+{
+    const size_t bytes = v.size() * sizeof(T);
+    cudaError_t e = b.ensure(bytes > 0 ? bytes : 16);
+    if (e != cudaSuccess || bytes == 0) return e;
+    return cudaMemcpyAsync(b.p, v.data(), bytes, cudaMemcpyHostToDevice, st);
+}
+
+}  // namespace
+
+extern "C" int vista_run(vista_stack *h)
+{
+    CHECK_HANDLE(h);
+    if (h->pending.empty()) return fail(h, VISTA_E_STATE, "vista_run with no queued source");
+    const vista_cube_desc &c = h->desc;
+    const bool fp64 = c.precision == VISTA_PREC_FP64;
+    cudaError_t e;
+
+    // 1. the rest lattice (fixed at the first run)
+    double f0 = h->f0, df = h->df;
+    if (!h->lattice_fixed) {
+        double best = 0.0;
+        for (const SrcHost &s : h->pending) {
+            if (s.d.nchan < 2)
+                return fail(h, VISTA_E_ARG, "the automatic rest lattice needs >= 2 channels per window");
+            const double wdt = widest_rest_channel(s.freqs.data(), s.d.nchan, s.d.z);
+            if (wdt > best) best = wdt;
+        }
+        if (!(best > 0.0)) return fail(h, VISTA_E_ARG, "automatic rest lattice: zero channel width");
+        df = best;
+        f0 = lattice_f0(c.central_freq, c.nrest, best);
+    }
+    const double saved_f0 = h->f0, saved_df = h->df;
+    h->f0 = f0;
+    h->df = df;
+
+    // 2. channel tables
+    const double gu = 1.0 / (C_LIGHT * c.du), gv = 1.0 / (C_LIGHT * c.dv);
+    const int nsrc = (int)h->pending.size();
+    std::vector<Plan> plans((size_t)nsrc);
+    for (int i = 0; i < nsrc; ++i) {
+        int rc = plan_source(h, h->pending[(size_t)i], gu, gv, plans[(size_t)i]);
+        if (rc != VISTA_OK) {
+            h->f0 = saved_f0;
+            h->df = saved_df;
+            return rc;
+        }
+    }
+    h->lattice_fixed = true;
+
+    // 3. launch classes and flattened host tables
+    const LaunchCfg cfg = h->cfg;
+    const int cw = 32 * cfg.chans_per_lane;
+    std::vector<ClassRun> classes;
+    std::vector<int> cls_of((size_t)nsrc);
+    for (int i = 0; i < nsrc; ++i) {
+        const SrcHost &s = h->pending[(size_t)i];
+        const int key = fp64 ? 0 : ((s.d.vis_type << 8) | s.d.npol);
+        int ci = -1;
+        for (size_t j = 0; j < classes.size(); ++j)
+            if (classes[j].npol_vt == key) ci = (int)j;
+        if (ci < 0) {
+            classes.emplace_back();
+            classes.back().npol_vt = key;
+            ci = (int)classes.size() - 1;
+        }
+        classes[(size_t)ci].members.push_back(i);
+        cls_of[(size_t)i] = ci;
+    }
+    std::vector<ChanF> chf;
+    std::vector<ChanD> chd;
+    std::vector<int32_t> chan_off((size_t)nsrc);
+    for (int i = 0; i < nsrc; ++i) {
+        chan_off[(size_t)i] = (int32_t)chf.size();
+        chf.insert(chf.end(), plans[(size_t)i].chf.begin(), plans[(size_t)i].chf.end());
+        chd.insert(chd.end(), plans[(size_t)i].chd.begin(), plans[(size_t)i].chd.end());
+    }
+    if (chf.size() > (size_t)0x7fffffff) return fail(h, VISTA_E_RANGE, "too many channels in one run");
+
+    // host-memory windows: staging layout
+    size_t stage_bytes = 0;
+    auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
+    for (const SrcHost &s : h->pending)
+        if (s.d.mem == VISTA_MEM_HOST && s.d.nrow > 0) {
+            const size_t nr = (size_t)s.d.nrow, nvv = nr * (size_t)s.d.nchan * (size_t)s.d.npol;
+            stage_bytes += al(nr * 24) + al(nvv * vis_elem_bytes(s.d.vis_type)) + al(nr * 4 * (size_t)s.d.npol) +
+                           (s.d.flags ? al(nvv) : 0);
+        }
+    if (stage_bytes) {
+        e = h->b_stage.ensure(stage_bytes);
+        if (e != cudaSuccess) return cuda_fail(h, e, "staging allocation");
+    }
+
+    std::vector<SrcDev> sdev;
+    std::vector<int64_t> offs;     // per class: row_off[n+1] then item_off[n+1]
+    std::vector<size_t> cls_src0(classes.size()), cls_off0(classes.size());
+    int64_t rec_total = 0;
+    size_t stage_pos = 0;
+    for (size_t ci = 0; ci < classes.size(); ++ci) {
+        ClassRun &cr = classes[ci];
+        cls_src0[ci] = sdev.size();
+        cls_off0[ci] = offs.size();
+        const size_t m = cr.members.size();
+        std::vector<int64_t> roff(m + 1, 0), ioff(m + 1, 0);
+        for (size_t t = 0; t < m; ++t) {
+            const int i = cr.members[t];
+            const SrcHost &s = h->pending[(size_t)i];
+            const Plan &pl = plans[(size_t)i];
+            SrcDev d{};
+            d.uvw = s.d.uvw;
+            d.vis = s.d.vis;
+            d.wts = s.d.weights;
+            d.flags = s.d.flags;
+            if (s.d.mem == VISTA_MEM_HOST && s.d.nrow > 0) {
+                const size_t nr = (size_t)s.d.nrow, nvv = nr * (size_t)s.d.nchan * (size_t)s.d.npol;
+                char *base = (char *)h->b_stage.p;
+                const size_t b_uvw = nr * 24, b_vis = nvv * vis_elem_bytes(s.d.vis_type),
+                             b_w = nr * 4 * (size_t)s.d.npol;
+                char *p_uvw = base + stage_pos;
+                stage_pos += al(b_uvw);
+                char *p_vis = base + stage_pos;
+                stage_pos += al(b_vis);
+                char *p_w = base + stage_pos;
+                stage_pos += al(b_w);
+                char *p_f = nullptr;
+                if (s.d.flags) {
+                    p_f = base + stage_pos;
+                    stage_pos += al(nvv);
+                }
+                e = cudaMemcpyAsync(p_uvw, s.d.uvw, b_uvw, cudaMemcpyHostToDevice, h->stream);
+                if (e == cudaSuccess) e = cudaMemcpyAsync(p_vis, s.d.vis, b_vis, cudaMemcpyHostToDevice, h->stream);
+                if (e == cudaSuccess) e = cudaMemcpyAsync(p_w, s.d.weights, b_w, cudaMemcpyHostToDevice, h->stream);
+                if (e == cudaSuccess && p_f) e = cudaMemcpyAsync(p_f, s.d.flags, nvv, cudaMemcpyHostToDevice, h->stream);
+                if (e != cudaSuccess) return cuda_fail(h, e, "host-to-device copy of a host-memory window");
+                d.uvw = (const double *)p_uvw;
+                d.vis = p_vis;
+                d.wts = (const float *)p_w;
+                d.flags = (const uint8_t *)p_f;
+            }
+            d.nrow = s.d.nrow;
+            d.nchan = s.d.nchan;
+            d.npol = s.d.npol;
+            d.vis_type = s.d.vis_type;
+            d.vis_scale = (s.d.vis_type == VISTA_VIS_F16X2 || s.d.vis_type == VISTA_VIS_BF16X2) ? s.d.vis_scale : 1.0f;
+            d.l = s.d.l;
+            d.m = s.d.m;
+            d.n1 = std::sqrt(1.0 - s.d.l * s.d.l - s.d.m * s.d.m) - 1.0;
+            d.step_c = pl.step / C_LIGHT;
+            d.k_lo = pl.k_lo;
+            d.k_hi = pl.k_hi;
+            d.chan_off = chan_off[(size_t)i];
+            d.linear = pl.linear ? 1 : 0;
+            for (int p = 0; p < 4; ++p) d.plane[p] = p < s.d.npol ? s.pol_map[(size_t)p] : -1;
+            d.nchunk = pl.k_hi > pl.k_lo ? (pl.k_hi - pl.k_lo + cw - 1) / cw : 0;
+            d.rec_off = rec_total;
+            if (!fp64) rec_total += (int64_t)d.nchunk * d.nrow;
+            const int64_t ntile = (d.nrow + cfg.rows_per_item - 1) / cfg.rows_per_item;
+            roff[t + 1] = roff[t] + d.nrow;
+            ioff[t + 1] = ioff[t] + (int64_t)d.nchunk * ntile;
+            sdev.push_back(d);
+        }
+        offs.insert(offs.end(), roff.begin(), roff.end());
+        offs.insert(offs.end(), ioff.begin(), ioff.end());
+        cr.args.nsrc = (int32_t)m;
+        cr.args.nrows_total = roff[m];
+        cr.args.nitems_total = ioff[m];
+    }
+
+    // 4. uploads
+    if ((e = upload(h->b_srcs, sdev, h->stream)) != cudaSuccess) return cuda_fail(h, e, "source table upload");
+    if ((e = upload(h->b_chf, chf, h->stream)) != cudaSuccess) return cuda_fail(h, e, "channel table upload");
+    if ((e = upload(h->b_chd, chd, h->stream)) != cudaSuccess) return cuda_fail(h, e, "channel table upload");
+    if ((e = upload(h->b_off, offs, h->stream)) != cudaSuccess) return cuda_fail(h, e, "offset table upload");
+    if (!fp64 && (e = h->b_recs.ensure((size_t)(rec_total > 0 ? rec_total : 1) * sizeof(RowRec))) != cudaSuccess)
+        return cuda_fail(h, e, "row record allocation");
+
+    // 5. launches
+    CubeGeom g{c.nu, c.nv, c.nrest, c.npol, gu, gv, c.hermitian_fold, 0};
+    for (size_t ci = 0; ci < classes.size(); ++ci) {
+        ClassRun &cr = classes[ci];
+        RunArgs &a = cr.args;
+        a.srcs = (const SrcDev *)h->b_srcs.p + cls_src0[ci];
+        a.chf = (const ChanF *)h->b_chf.p;
+        a.chd = (const ChanD *)h->b_chd.p;
+        a.recs = (RowRec *)h->b_recs.p;
+        a.row_off = (const int64_t *)h->b_off.p + cls_off0[ci];
+        a.item_off = a.row_off + (cr.members.size() + 1);
+        a.g = g;
+        a.cube = h->cube;
+        a.count = h->count;
+        a.stats = h->stats;
+        a.err = h->err;
+        if (fp64) {
+            e = launch_fp64(a, h->stream);
+        } else {
+            e = launch_prepass(a, cfg, h->stream);
+            if (e == cudaSuccess) e = launch_mixed(a, cfg, cr.npol_vt, h->stream);
+        }
+        if (e != cudaSuccess) return cuda_fail(h, e, "kernel launch");
+    }
+    bool any_host = false;
+    for (const SrcHost &s : h->pending) any_host |= s.d.mem == VISTA_MEM_HOST;
+    if (any_host && (e = cudaStreamSynchronize(h->stream)) != cudaSuccess)
+        return cuda_fail(h, e, "stream synchronize after host-memory copies");
+    h->classes = std::move(classes);
+    h->last = std::move(h->pending);
+    h->pending.clear();
+    return VISTA_OK;
+}
+
+// --------------------------------------------------------------- readback
+
+namespace {
+
+int read_common(vista_stack *h, void *sum_wv, void *sum_w, void *sum_wvv, uint32_t *count, int dst_dev,
+                int out_f64)
+{
+    cudaError_t e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "stream synchronize");
+    int32_t err = 0;
+    e = cudaMemcpy(&err, h->err, sizeof err, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(h, e, "error word read");
+    if (err != 0) return fail(h, VISTA_E_TIMEOUT, "a device-side wait gave up (code %d)", err);
+    const int fp64 = h->desc.precision == VISTA_PREC_FP64;
+    const int64_t n = h->nentries;
+    const size_t fe = out_f64 ? 8 : 4;
+    if (dst_dev) {
+        e = launch_unpack(h->cube, h->count, fp64, n, sum_wv, sum_w, sum_wvv, count, out_f64, h->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+        if (e != cudaSuccess) return cuda_fail(h, e, "cube unpack");
+        return VISTA_OK;
+    }
+    // host destination: unpack into a device scratch area, then copy
+    const size_t b_wv = sum_wv ? (size_t)n * 2 * fe : 0, b_w = sum_w ? (size_t)n * fe : 0,
+                 b_vv = sum_wvv ? (size_t)n * fe : 0, b_c = count ? (size_t)n * 4 : 0;
+    e = h->b_unpack.ensure(b_wv + b_w + b_vv + b_c + 64);
+    if (e != cudaSuccess) return cuda_fail(h, e, "readback scratch allocation");
+    char *p = (char *)h->b_unpack.p;
+    char *d_wv = sum_wv ? p : nullptr;
+    char *d_w = sum_w ? p + b_wv : nullptr;
+    char *d_vv = sum_wvv ? p + b_wv + b_w : nullptr;
+    uint32_t *d_c = count ? (uint32_t *)(p + b_wv + b_w + b_vv) : nullptr;
+    e = launch_unpack(h->cube, h->count, fp64, n, d_wv, d_w, d_vv, d_c, out_f64, h->stream);
+    if (e == cudaSuccess && sum_wv) e = cudaMemcpyAsync(sum_wv, d_wv, b_wv, cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess && sum_w) e = cudaMemcpyAsync(sum_w, d_w, b_w, cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess && sum_wvv) e = cudaMemcpyAsync(sum_wvv, d_vv, b_vv, cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess && count) e = cudaMemcpyAsync(count, d_c, b_c, cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "cube readback");
+    return VISTA_OK;
+}
+
+}  // namespace
+
+extern "C" int vista_read_cube(vista_stack *h, float *sum_wv, float *sum_w, float *sum_wvv, uint32_t *count,
+                               int dst_is_device)
+{
+    CHECK_HANDLE(h);
+    return read_common(h, sum_wv, sum_w, sum_wvv, count, dst_is_device, 0);
+}
+
+extern "C" int vista_read_cube_f64(vista_stack *h, double *sum_wv, double *sum_w, double *sum_wvv,
+                                   uint32_t *count, int dst_is_device)
+{
+    CHECK_HANDLE(h);
+    return read_common(h, sum_wv, sum_w, sum_wvv, count, dst_is_device, 1);
+}
+
+extern "C" int vista_zero_cube(vista_stack *h)
+{
+    CHECK_HANDLE(h);
+    const size_t esz = h->desc.precision == VISTA_PREC_FP64 ? 32 : 16;
+    cudaError_t e = cudaMemsetAsync(h->cube, 0, (size_t)h->nentries * esz, h->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->count, 0, (size_t)h->nentries * 4, h->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->stats, 0, sizeof(DevStats), h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "cube zeroing");
+    return VISTA_OK;
+}
+
+extern "C" int vista_get_stats(vista_stack *h, vista_stats *out)
+{
+    CHECK_HANDLE(h);
+    if (!out) return fail(h, VISTA_E_ARG, "null output");
+    DevStats s;
+    cudaError_t e = cudaStreamSynchronize(h->stream);
+    if (e == cudaSuccess) e = cudaMemcpy(&s, h->stats, sizeof s, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(h, e, "stats readback");
+    out->n_vis = s.n_vis;
+    out->n_flagged = s.n_flagged;
+    out->n_dropped_uv = s.n_dropped_uv;
+    out->n_stacked = s.n_stacked;
+    return VISTA_OK;
+}
+
+extern "C" int vista_get_lattice(vista_stack *h, double *rest_f0, double *rest_df)
+{
+    CHECK_HANDLE(h);
+    if (!rest_f0 || !rest_df) return fail(h, VISTA_E_ARG, "null output");
+    if (!h->lattice_fixed) return fail(h, VISTA_E_STATE, "the automatic lattice is fixed at the first run");
+    *rest_f0 = h->f0;
+    *rest_df = h->df;
+    return VISTA_OK;
+}
+
+extern "C" int vista_set_tuning(vista_stack *h, const vista_tuning *t)
+{
+    CHECK_HANDLE(h);
+    if (!t) return fail(h, VISTA_E_ARG, "null tuning");
+    LaunchCfg c = h->cfg;
+    if (t->rows_per_item) {
+        if (t->rows_per_item < 1 || t->rows_per_item > (1 << 20))
+            return fail(h, VISTA_E_ARG, "rows_per_item must be in [1, 2^20]");
+        c.rows_per_item = t->rows_per_item;
+    }
+    if (t->chans_per_lane) {
+        if (t->chans_per_lane != 1 && t->chans_per_lane != 2 && t->chans_per_lane != 4)
+            return fail(h, VISTA_E_ARG, "chans_per_lane must be 1, 2 or 4");
+        c.chans_per_lane = t->chans_per_lane;
+    }
+    if (t->warps_per_cta) {
+        if (t->warps_per_cta != 1 && t->warps_per_cta != 2 && t->warps_per_cta != 4 && t->warps_per_cta != 8)
+            return fail(h, VISTA_E_ARG, "warps_per_cta must be 1, 2, 4 or 8");
+        c.warps_per_cta = t->warps_per_cta;
+    }
+    if (t->sort_rows < 0 || t->sort_rows > 1) return fail(h, VISTA_E_ARG, "sort_rows must be 0 or 1");
+    c.sort_rows = t->sort_rows;
+    h->cfg = c;
+    return VISTA_OK;
+}
+
+extern "C" int vista_get_tuning(vista_stack *h, vista_tuning *t)
+{
+    CHECK_HANDLE(h);
+    if (!t) return fail(h, VISTA_E_ARG, "null output");
+    t->rows_per_item = h->cfg.rows_per_item;
+    t->chans_per_lane = h->cfg.chans_per_lane;
+    t->warps_per_cta = h->cfg.warps_per_cta;
+    t->sort_rows = h->cfg.sort_rows;
+    return VISTA_OK;
+}
+
+extern "C" int vista_close(vista_stack *h)
+{
+    CHECK_HANDLE(h);
+    {
+        std::lock_guard<std::mutex> lk(g_mu);
+        g_live.erase(h);
+    }
+    cudaStreamSynchronize(h->stream);
+    cudaFree(h->cube);
+    cudaFree(h->count);
+    cudaFree(h->stats);
+    cudaFree(h->err);
+    h->b_srcs.release();
+    h->b_chf.release();
+    h->b_chd.release();
+    h->b_recs.release();
+    h->b_off.release();
+    h->b_stage.release();
+    h->b_unpack.release();
+    delete h;
+    return VISTA_OK;
+}
+
+extern "C" const char *vista_last_error(const vista_stack *h)
+{
+    if (h && live(h)) return h->msg.c_str();
+    return g_err.c_str();
+}
+
+// ------------------------------------------------------------------- debug
+
+namespace {
+
+int debug_common(vista_stack *h, int32_t src, double *ph, int32_t *cells)
+{
+    if (src < 0 || (size_t)src >= h->last.size()) return fail(h, VISTA_E_ARG, "no source %d in the last run", src);
+    for (const ClassRun &cr : h->classes) {
+        for (size_t t = 0; t < cr.members.size(); ++t) {
+            if (cr.members[t] != src) continue;
+            cudaError_t e = launch_debug(cr.args, h->cfg, (int)t, h->desc.precision == VISTA_PREC_FP64, ph,
+                                         cells, h->stream);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+            if (e != cudaSuccess) return cuda_fail(h, e, "debug export");
+            return VISTA_OK;
+        }
+    }
+    return fail(h, VISTA_E_STATE, "source %d not found in the last run", src);
+}
+
+}  // namespace
+
+extern "C" int vista_debug_phasors(vista_stack *h, int32_t src, double *dst)
+{
+    CHECK_HANDLE(h);
+    if (!dst) return fail(h, VISTA_E_ARG, "null output");
+    return debug_common(h, src, dst, nullptr);
+}
+
+extern "C" int vista_debug_cells(vista_stack *h, int32_t src, int32_t *dst)
+{
+    CHECK_HANDLE(h);
+    if (!dst) return fail(h, VISTA_E_ARG, "null output");
+    return debug_common(h, src, nullptr, dst);
+}

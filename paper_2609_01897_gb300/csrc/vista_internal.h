@@ -1,0 +1,113 @@
+// Internal data layout shared by the libvista host code and its kernels.
+#pragma once
+#include <cstdint>
+
+#include <cuda_runtime.h>
+
+#include "vista.h"
+
+namespace vista {
+
+constexpr double C_LIGHT = 299792458.0;   // m/s
+
+// Cube geometry as the kernels see it.
+struct CubeGeom {
+    int32_t nu, nv, nrest, npol;
+    double gu, gv;      // fl(1 / fl(c du)), fl(1 / fl(c dv))
+    int32_t fold, pad;
+};
+
+// Per channel the path reads, mixed path (32 B).  su/sv are fl32(s_k).
+struct ChanF {
+    float su, sv;
+    int32_t j0, nb;
+    float w[4];
+};
+
+// Per channel, exact FP64 values (64 B): s_k = fl(nu_k gu) as the cell rule
+// defines it, the channel centre, and the FP64 weights.
+struct ChanD {
+    double su, sv, nu;
+    int32_t j0, nb;
+    double w[4];
+};
+
+// One (source, window) as the kernels see it.
+struct SrcDev {
+    const double *uvw;
+    const void *vis;
+    const float *wts;
+    const uint8_t *flags;
+    int64_t nrow;
+    int32_t nchan, npol;
+    int32_t vis_type;
+    float vis_scale;
+    double l, m, n1;        // n1 = sqrt(1 - l^2 - m^2) - 1
+    double step_c;          // channel step / c (linear axes)
+    int32_t k_lo, k_hi;     // channels [k_lo, k_hi) are read
+    int32_t chan_off;       // table entry of channel k is chan_off + (k - k_lo)
+    int32_t linear;         // 1: f_k = f_0 + k step (one recurrence step)
+    int32_t plane[4];       // cube plane of each input pol, -1 = skip
+    int32_t nchunk;         // work chunks along the channel axis
+    int32_t pad;
+    int64_t rec_off;        // first row record of this window
+};
+
+// Per (row, chunk) record written by the mixed path's FP64 pre-pass (48 B).
+//   t0          frac(tau nu_c0 / c), turns, nu_c0 = first channel of the chunk
+//   dhi, dlo    D = frac(tau step / c) split so that lane * dhi is exact
+//               (dhi has at most 19 significant bits), dlo = D - dhi
+//   sre, sim    exp(2 pi i frac(32 D)): the lane-to-lane stride of the
+//               per-lane recurrence
+//   u, v        fl32 of the (folded) uvw, metres
+//   rowf        row index | (fold << 31)
+//   W[4]        the row's weights
+// For windows without a linear axis, dhi/dlo carry the bits of tau (FP64).
+struct __align__(16) RowRec {
+    float t0, dhi, dlo, sre;
+    float sim, u, v;
+    uint32_t rowf;
+    float W[4];
+};
+
+// Counters (device), see vista_stats.
+struct DevStats {
+    unsigned long long n_vis, n_flagged, n_dropped_uv, n_stacked;
+};
+
+struct LaunchCfg {
+    int32_t rows_per_item;
+    int32_t chans_per_lane;
+    int32_t warps_per_cta;
+    int32_t sort_rows;
+};
+
+// Everything one mixed or FP64 run needs on the device.
+struct RunArgs {
+    const SrcDev *srcs;
+    int32_t nsrc;
+    const ChanF *chf;
+    const ChanD *chd;
+    RowRec *recs;
+    const int64_t *row_off;     // [nsrc+1] cumulative rows
+    const int64_t *item_off;    // [nsrc+1] cumulative work items
+    int64_t nrows_total, nitems_total;
+    CubeGeom g;
+    void *cube;                 // float4 (mixed) or double[4] (FP64) per entry
+    uint32_t *count;
+    DevStats *stats;
+    int32_t *err;
+};
+
+// Kernel launchers (vista_kernels.cu).  Return a cudaError_t.
+cudaError_t launch_prepass(const RunArgs &a, const LaunchCfg &c, cudaStream_t st);
+// npol_vt = (vis_type << 8) | npol: every window of one launch shares both.
+cudaError_t launch_mixed(const RunArgs &a, const LaunchCfg &c, int npol_vt, cudaStream_t st);
+cudaError_t launch_fp64(const RunArgs &a, cudaStream_t st);
+cudaError_t launch_unpack(const void *cube, const uint32_t *count, int fp64, int64_t n,
+                          void *sum_wv, void *sum_w, void *sum_wvv, uint32_t *cnt_out,
+                          int out_f64, cudaStream_t st);
+cudaError_t launch_debug(const RunArgs &a, const LaunchCfg &c, int src, int fp64, double *ph,
+                         int32_t *cells, cudaStream_t st);
+
+}  // namespace vista

@@ -1,0 +1,285 @@
+"""Python binding of libvista (include/vista.h): argument marshalling only.
+
+Every step of the stacking runs in the library's CUDA kernels; this module
+converts torch tensors into pointers and sizes, and C status codes into
+exceptions.  It raises if libvista.so has not been built -- there is no
+fallback implementation.
+"""
+import ctypes as C
+import os
+
+import numpy as np
+import torch
+
+from . import build as _build
+
+VISTA_OK, E_ARG, E_STATE, E_NOMEM, E_CUDA, E_RANGE, E_TIMEOUT = 0, -1, -2, -3, -4, -5, -6
+VIS_C64, VIS_C128, VIS_F16X2, VIS_BF16X2 = 0, 1, 2, 3
+BIN_OVERLAP, BIN_NEAREST = 0, 1
+PREC_MIXED, PREC_FP64 = 0, 1
+MEM_DEVICE, MEM_HOST = 0, 1
+MAX_BINS = 4
+
+_CODES = {E_ARG: "VISTA_E_ARG", E_STATE: "VISTA_E_STATE", E_NOMEM: "VISTA_E_NOMEM",
+          E_CUDA: "VISTA_E_CUDA", E_RANGE: "VISTA_E_RANGE", E_TIMEOUT: "VISTA_E_TIMEOUT"}
+
+
+class CubeDesc(C.Structure):
+    _fields_ = [("nu", C.c_int32), ("nv", C.c_int32), ("nrest", C.c_int32), ("npol", C.c_int32),
+                ("du", C.c_double), ("dv", C.c_double), ("rest_f0", C.c_double),
+                ("rest_df", C.c_double), ("central_freq", C.c_double),
+                ("bin_mode", C.c_int32), ("precision", C.c_int32),
+                ("hermitian_fold", C.c_int32), ("reserved0", C.c_int32), ("stream", C.c_void_p)]
+
+
+class SourceDesc(C.Structure):
+    _fields_ = [("nrow", C.c_int64), ("nchan", C.c_int32), ("npol", C.c_int32),
+                ("uvw", C.c_void_p), ("freqs", C.c_void_p), ("vis", C.c_void_p),
+                ("vis_type", C.c_int32), ("vis_scale", C.c_float),
+                ("weights", C.c_void_p), ("flags", C.c_void_p), ("pol_map", C.c_void_p),
+                ("l", C.c_double), ("m", C.c_double), ("z", C.c_double),
+                ("mem", C.c_int32), ("reserved0", C.c_int32)]
+
+
+class Stats(C.Structure):
+    _fields_ = [("n_vis", C.c_uint64), ("n_flagged", C.c_uint64),
+                ("n_dropped_uv", C.c_uint64), ("n_stacked", C.c_uint64)]
+
+    def as_dict(self):
+        return {k: int(getattr(self, k)) for k, _ in self._fields_}
+
+
+class Tuning(C.Structure):
+    _fields_ = [("rows_per_item", C.c_int32), ("chans_per_lane", C.c_int32),
+                ("warps_per_cta", C.c_int32), ("sort_rows", C.c_int32)]
+
+
+class VistaError(RuntimeError):
+    def __init__(self, call, code, msg):
+        super().__init__("%s failed: %s: %s" % (call, _CODES.get(code, code), msg))
+        self.code = code
+
+
+# Every symbol include/vista.h declares, with (restype, argtypes).
+_P = C.c_void_p
+SIGNATURES = {
+    "vista_open_stack": (C.c_int, [C.POINTER(CubeDesc), C.POINTER(_P)]),
+    "vista_add_source": (C.c_int, [_P, C.POINTER(SourceDesc)]),
+    "vista_run": (C.c_int, [_P]),
+    "vista_read_cube": (C.c_int, [_P, _P, _P, _P, _P, C.c_int]),
+    "vista_read_cube_f64": (C.c_int, [_P, _P, _P, _P, _P, C.c_int]),
+    "vista_zero_cube": (C.c_int, [_P]),
+    "vista_get_stats": (C.c_int, [_P, C.POINTER(Stats)]),
+    "vista_get_lattice": (C.c_int, [_P, C.POINTER(C.c_double), C.POINTER(C.c_double)]),
+    "vista_set_tuning": (C.c_int, [_P, C.POINTER(Tuning)]),
+    "vista_get_tuning": (C.c_int, [_P, C.POINTER(Tuning)]),
+    "vista_close": (C.c_int, [_P]),
+    "vista_last_error": (C.c_char_p, [_P]),
+    "vista_abi_version": (C.c_int, []),
+    "vista_plan_lattice": (C.c_int, [_P, _P, _P, C.c_int32, C.c_int32, C.c_double,
+                                     C.POINTER(C.c_double), C.POINTER(C.c_double)]),
+    "vista_plan_channels": (C.c_int, [_P, C.c_int32, C.c_double, C.c_double, C.c_double,
+                                      C.c_int32, C.c_int32, _P, _P, _P]),
+    "vista_debug_phasors": (C.c_int, [_P, C.c_int32, _P]),
+    "vista_debug_cells": (C.c_int, [_P, C.c_int32, _P]),
+}
+
+_lib = None
+
+
+def lib_path():
+    return _build.LIB
+
+
+def lib():
+    """Load libvista.so (raises if it is missing: build it first)."""
+    global _lib
+    if _lib is None:
+        path = _build.LIB
+        if not os.path.exists(path):
+            raise RuntimeError("libvista.so not found at %s: run paper_2609_01897_gb300.build.build() "
+                               "(there is no CPU fallback)" % path)
+        L = C.CDLL(path)
+        for name, (res, args) in SIGNATURES.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+def last_error(h=None):
+    s = lib().vista_last_error(h)
+    return s.decode() if s else ""
+
+
+def _check(call, rc, h=None):
+    if rc != VISTA_OK:
+        raise VistaError(call, rc, last_error(h))
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    if isinstance(t, np.ndarray):
+        return t.ctypes.data
+    return t.data_ptr()
+
+
+def _vis_type(vis):
+    if vis.dtype == torch.complex64:
+        return VIS_C64
+    if vis.dtype == torch.complex128:
+        return VIS_C128
+    if vis.dtype == torch.float16:
+        return VIS_F16X2
+    if vis.dtype == torch.bfloat16:
+        return VIS_BF16X2
+    raise TypeError("vis must be complex64, complex128, or float16/bfloat16 [..., 2]")
+
+
+class Stack:
+    """One stacking cube (vista_open_stack ... vista_close)."""
+
+    def __init__(self, nu, nv, nrest, npol, du, dv, *, rest_f0=0.0, rest_df=0.0, central_freq=0.0,
+                 bin_mode=BIN_OVERLAP, precision=PREC_MIXED, hermitian_fold=False, stream=None):
+        if stream is None and torch.cuda.is_available():
+            stream = torch.cuda.current_stream()
+        sp = stream.cuda_stream if hasattr(stream, "cuda_stream") else stream
+        self.desc = CubeDesc(nu, nv, nrest, npol, du, dv, rest_f0, rest_df, central_freq,
+                             bin_mode, precision, 1 if hermitian_fold else 0, 0, sp)
+        h = _P()
+        _check("vista_open_stack", lib().vista_open_stack(C.byref(self.desc), C.byref(h)))
+        self.h = h
+        self.shape = (nv, nu, nrest, npol)
+        self._pending = []
+        self._inflight = []
+
+    # -- sources
+    def add_source(self, uvw, freqs, vis, weights, flags=None, *, l, m, z, pol_map=None,
+                   vis_scale=1.0):
+        """uvw [nrow,3] f64, freqs [nchan] f64 (host), vis [nrow,nchan,npol] complex
+        (or 16-bit [nrow,nchan,npol,2]), weights [nrow,npol] f32, flags u8 or None.
+        CUDA tensors are borrowed device arrays; CPU tensors are host arrays
+        (pin them for asynchronous copies)."""
+        vt = _vis_type(vis)
+        nrow, nchan, npol = int(vis.shape[0]), int(vis.shape[1]), int(vis.shape[2])
+        if vt in (VIS_F16X2, VIS_BF16X2) and (vis.dim() != 4 or vis.shape[3] != 2):
+            raise ValueError("16-bit visibilities are [nrow, nchan, npol, 2]")
+        for name, t in (("uvw", uvw), ("vis", vis), ("weights", weights), ("flags", flags)):
+            if t is not None and not t.is_contiguous():
+                raise ValueError("%s must be contiguous" % name)
+        dev = vis.is_cuda
+        for name, t in (("uvw", uvw), ("weights", weights), ("flags", flags)):
+            if t is not None and t.is_cuda != dev:
+                raise ValueError("%s must live on the same side (host/device) as vis" % name)
+        if uvw.dtype != torch.float64 or weights.dtype != torch.float32:
+            raise TypeError("uvw must be float64 and weights float32")
+        if flags is not None and flags.dtype != torch.uint8:
+            raise TypeError("flags must be uint8")
+        f = np.ascontiguousarray(np.asarray(freqs, dtype=np.float64))
+        pm = None if pol_map is None else np.ascontiguousarray(np.asarray(pol_map, dtype=np.int32))
+        d = SourceDesc(nrow, nchan, npol, _ptr(uvw), f.ctypes.data, _ptr(vis), vt, float(vis_scale),
+                       _ptr(weights), _ptr(flags), None if pm is None else pm.ctypes.data,
+                       float(l), float(m), float(z), MEM_DEVICE if dev else MEM_HOST, 0)
+        _check("vista_add_source", lib().vista_add_source(self.h, C.byref(d)), self.h)
+        self._pending.append((uvw, vis, weights, flags))
+
+    def run(self):
+        _check("vista_run", lib().vista_run(self.h), self.h)
+        self._inflight = self._pending
+        self._pending = []
+
+    # -- results
+    def read_cube(self, device=True, f64=False, which=("sum_wv", "sum_w", "sum_wvv", "count")):
+        nv, nu, nrest, npol = self.shape
+        dt = torch.float64 if f64 else torch.float32
+        kw = {"device": "cuda"} if device else {"pin_memory": torch.cuda.is_available()}
+        out = {}
+        out["sum_wv"] = torch.empty((nv, nu, nrest, npol, 2), dtype=dt, **kw) if "sum_wv" in which else None
+        out["sum_w"] = torch.empty((nv, nu, nrest, npol), dtype=dt, **kw) if "sum_w" in which else None
+        out["sum_wvv"] = torch.empty((nv, nu, nrest, npol), dtype=dt, **kw) if "sum_wvv" in which else None
+        out["count"] = torch.empty((nv, nu, nrest, npol), dtype=torch.int32, **kw) if "count" in which else None
+        fn = lib().vista_read_cube_f64 if f64 else lib().vista_read_cube
+        _check("vista_read_cube", fn(self.h, _ptr(out["sum_wv"]), _ptr(out["sum_w"]),
+                                     _ptr(out["sum_wvv"]), _ptr(out["count"]), 1 if device else 0),
+               self.h)
+        self._inflight = []
+        return {k: v for k, v in out.items() if v is not None}
+
+    def stats(self):
+        s = Stats()
+        _check("vista_get_stats", lib().vista_get_stats(self.h, C.byref(s)), self.h)
+        return s.as_dict()
+
+    def lattice(self):
+        f0, df = C.c_double(), C.c_double()
+        _check("vista_get_lattice", lib().vista_get_lattice(self.h, C.byref(f0), C.byref(df)), self.h)
+        return f0.value, df.value
+
+    def zero(self):
+        _check("vista_zero_cube", lib().vista_zero_cube(self.h), self.h)
+
+    def set_tuning(self, rows_per_item=0, chans_per_lane=0, warps_per_cta=0, sort_rows=0):
+        t = Tuning(rows_per_item, chans_per_lane, warps_per_cta, sort_rows)
+        _check("vista_set_tuning", lib().vista_set_tuning(self.h, C.byref(t)), self.h)
+
+    def tuning(self):
+        t = Tuning()
+        _check("vista_get_tuning", lib().vista_get_tuning(self.h, C.byref(t)), self.h)
+        return {k: getattr(t, k) for k, _ in Tuning._fields_}
+
+    def debug_phasors(self, src, nrow, nchan):
+        out = torch.zeros((nrow, nchan, 2), dtype=torch.float64, device="cuda")
+        _check("vista_debug_phasors", lib().vista_debug_phasors(self.h, src, _ptr(out)), self.h)
+        return out
+
+    def debug_cells(self, src, nrow, nchan):
+        out = torch.full((nrow, nchan, 2), -7, dtype=torch.int32, device="cuda")
+        _check("vista_debug_cells", lib().vista_debug_cells(self.h, src, _ptr(out)), self.h)
+        return out
+
+    def close(self):
+        if self.h is not None:
+            _check("vista_close", lib().vista_close(self.h))
+            self.h = None
+            self._inflight = []
+            self._pending = []
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            if getattr(self, "h", None) is not None:
+                lib().vista_close(self.h)
+        except Exception:
+            pass
+
+
+# -- host-only planner entry points
+
+def plan_lattice(freq_list, z_list, nrest, central_freq):
+    fs = [np.ascontiguousarray(f, dtype=np.float64) for f in freq_list]
+    ptrs = (C.c_void_p * len(fs))(*[f.ctypes.data for f in fs])
+    n = np.array([f.size for f in fs], dtype=np.int32)
+    z = np.ascontiguousarray(z_list, dtype=np.float64)
+    f0, df = C.c_double(), C.c_double()
+    _check("vista_plan_lattice", lib().vista_plan_lattice(C.cast(ptrs, C.c_void_p), n.ctypes.data,
+                                                          z.ctypes.data, len(fs), nrest, central_freq,
+                                                          C.byref(f0), C.byref(df)))
+    return f0.value, df.value
+
+
+def plan_channels(freqs, z, f0, df, nrest, bin_mode=BIN_OVERLAP):
+    f = np.ascontiguousarray(freqs, dtype=np.float64)
+    j0 = np.zeros(f.size, dtype=np.int32)
+    nb = np.zeros(f.size, dtype=np.int32)
+    w = np.zeros((f.size, MAX_BINS), dtype=np.float64)
+    _check("vista_plan_channels", lib().vista_plan_channels(f.ctypes.data, f.size, z, f0, df, nrest,
+                                                            bin_mode, j0.ctypes.data, nb.ctypes.data,
+                                                            w.ctypes.data))
+    return j0, nb, w
