@@ -1,0 +1,408 @@
+#!/usr/bin/env python
+"""Stacked visibilities per second on GB300 (ViSta hot path, libvista).
+
+One step = one full stacking job: zero the cube, queue every (source, window)
+of the workload, vista_run.  The inputs (seeded synthetic ALMA-compact-like
+stack: 64 sources x 2 windows x 120 channels x 2 pols, 43 antennas, 120
+integrations; cube 256 x 256 uv cells x 512 rest channels x 2 pols) are
+resident in HBM before the timed region; they total ~30 GB, far larger than
+L2, so no L2 flush is needed between steps.
+
+Prints one JSON line (rank 0).  --impl reference times the FP64 CPU oracle on
+the host cores instead, on bounded samples of the same workload.
+
+Launch: python bench.py [--gpus N --steps K --warmup W]; for N > 1 under
+torchrun, one rank per GPU, each stacking its own 64 sources (weak scaling,
+no collective on the data path).
+"""
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+import torch  # noqa: E402
+
+METRIC = "stacked vis/s and % HBM roofline, mixed+batched vs plain FP64 GPU, <=1e-5 rel err"
+UNIT = "vis/s"
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=10)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--config", default="alma_compact", choices=["alma_compact", "tiny", "wideband_hi"])
+    p.add_argument("--sources", type=int, default=0, help="sources per rank (0 = the workload's own)")
+    p.add_argument("--fp64-steps", type=int, default=2, help="timed steps of the plain FP64 leg (0 = skip)")
+    p.add_argument("--e2e-steps", type=int, default=2, help="timed host-memory steps (0 = skip)")
+    p.add_argument("--cpu-sample", type=int, default=2, help="windows timed in the oracle baseline (0 = skip)")
+    p.add_argument("--tuning", default="", help="rows,chans_per_lane,warps,sort")
+    return p.parse_args()
+
+
+# ------------------------------------------------------------------ plumbing
+
+def dist_setup(args):
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if ws > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    elif torch.cuda.is_available():
+        torch.cuda.set_device(0)
+    return ws, rank, local
+
+
+def barrier(ws):
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def allmax(ws, x):
+    if ws == 1:
+        return x
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during a region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.p = None
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "--query-gpu=" + self.Q, "--format=csv,noheader,nounits",
+                                       "-i", str(gpu_index), "-lms", "200"], stdout=self.f,
+                                      stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.p = None
+        time.sleep(0.3)
+
+    def stop(self):
+        if self.p is None:
+            return None
+        time.sleep(0.25)
+        self.p.terminate()
+        try:
+            self.p.wait(5)
+        except subprocess.TimeoutExpired:
+            self.p.kill()
+        self.f.flush()
+        self.f.seek(0)
+        sm, mx, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.f:
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx = max(mx, float(parts[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        os.unlink(self.f.name)
+        if not sm:
+            return None
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+# ------------------------------------------------------------------ workload
+
+def make_workload(args, rank, device):
+    from paper_2609_01897_gb300 import synth
+    if args.config == "tiny":
+        return synth.tiny(device)
+    n = args.sources or (64 if args.config == "alma_compact" else 24)
+    ids = range(rank * n, rank * n + n)
+    if args.config == "alma_compact":
+        return synth.alma_compact(device, n_sources=n, src_ids=ids)
+    return synth.wideband_hi(device, n_sources=n, src_ids=ids)
+
+
+def vis_bytes(v):
+    return {torch.complex64: 8, torch.complex128: 16, torch.float16: 4, torch.bfloat16: 4}[v.dtype]
+
+
+def algorithmic_bytes(wl, f0, df, touched):
+    """Bytes a stacking pass must move at least: every visibility of a channel
+    that reaches the cube (value + u8 flag), uvw + weights of every row that
+    has such a channel, and one read-modify-write (2 x 20 B) per touched
+    cube entry."""
+    from paper_2609_01897_gb300 import vista as V
+    tot_vis, tot_bytes = 0, 0
+    for s in wl.spws:
+        j0, nb, _ = V.plan_channels(s.freqs, s.z, f0, df, wl.nrest, V.BIN_OVERLAP)
+        nin = int((nb > 0).sum())
+        nrow, npol = int(s.vis.shape[0]), int(s.vis.shape[2])
+        nv = nrow * nin * npol
+        tot_vis += nv
+        tot_bytes += nv * (vis_bytes(s.vis) + (1 if s.flags is not None else 0))
+        if nin:
+            tot_bytes += nrow * (24 + 4 * npol)
+    tot_bytes += int(touched) * 40
+    return tot_vis, tot_bytes
+
+
+def one_step(st, wl, host=None):
+    st.zero()
+    srcs = wl.spws if host is None else host
+    for s in srcs:
+        st.add_source(s.uvw, s.freqs, s.vis, s.weights, s.flags, l=s.l, m=s.m, z=s.z, pol_map=s.pol_map)
+    st.run()
+
+
+# ------------------------------------------------------------------ our arm
+
+def open_stack(wl, precision, tuning):
+    from paper_2609_01897_gb300 import vista as V
+    st = V.Stack(wl.nu, wl.nv, wl.nrest, wl.npol, wl.du, wl.dv, central_freq=wl.central_freq,
+                 precision=precision)
+    if tuning:
+        st.set_tuning(*tuning)
+    return st
+
+
+def timed_steps(st, wl, steps, warmup, ws, host=None):
+    stream = torch.cuda.current_stream()
+    for _ in range(warmup):
+        one_step(st, wl, host)
+    torch.cuda.synchronize()
+    barrier(ws)
+    torch.cuda.synchronize()
+    st.enable_timing(True)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        one_step(st, wl, host)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier(ws)
+    ms = e0.elapsed_time(e1) / steps
+    t = st.timing()
+    st.enable_timing(False)
+    return ms, t
+
+
+def cpu_baseline(wl, f0, df, nsample):
+    from oracle import oracle as O
+    srcs = []
+    for s in wl.spws[:nsample]:
+        srcs.append(O.Source(s.uvw.cpu().numpy(), s.freqs, s.vis.cpu().numpy(), s.weights.cpu().numpy(),
+                             None if s.flags is None else s.flags.cpu().numpy(), s.l, s.m, s.z, s.pol_map))
+    cube = O.make_cube(wl.nu, wl.nv, wl.nrest, wl.npol, wl.du, wl.dv, f0, df, 0, 0)
+    nthreads = os.cpu_count() or 1
+    t0 = time.perf_counter()
+    out = O.stack(cube, srcs, nthreads=nthreads)
+    dt = time.perf_counter() - t0
+    n = int(out["stats"]["n_vis"])
+    return {"value": n / dt, "unit": UNIT, "cores": nthreads, "kind": "oracle",
+            "sample": "%d of %d windows (%d visibilities), %.1f s" % (nsample, len(wl.spws), n, dt)}
+
+
+def run_ours(args):
+    from paper_2609_01897_gb300 import build as B
+    from paper_2609_01897_gb300 import vista as V
+    ws, rank, local = dist_setup(args)
+    B.build()
+    V.lib()
+    tuning = tuple(int(x) for x in args.tuning.split(",")) if args.tuning else None
+    wl = make_workload(args, rank, "cuda")
+    torch.cuda.synchronize()
+
+    # mixed-precision path (the headline)
+    st = open_stack(wl, V.PREC_MIXED, tuning)
+    one_step(st, wl)
+    f0, df = st.lattice()
+    cnt = st.read_cube(which=("count",))["count"]
+    touched = int((cnt > 0).sum())
+    del cnt
+    stats = st.stats()
+    n_vis, alg = algorithmic_bytes(wl, f0, df, touched)
+    assert n_vis == stats["n_vis"], (n_vis, stats)
+    clk = Clocks(local)
+    ms, tm = timed_steps(st, wl, args.steps, args.warmup, ws)
+    clocks = clk.stop()
+    ms_max = allmax(ws, ms)
+    value = n_vis * ws / (ms_max * 1e-3)
+    stack_ms = tm["stack_ms"] / max(1, args.steps)
+    peak, peak_kind = measured_peaks()
+    achieved = alg / (stack_ms * 1e-3) / 1e9
+    launches = int(tm["launches"])
+    st.close()
+
+    # plain FP64 GPU form on the same inputs
+    fp64 = None
+    if args.fp64_steps > 0:
+        st64 = open_stack(wl, V.PREC_FP64, None)
+        ms64, _ = timed_steps(st64, wl, args.fp64_steps, 1, ws)
+        st64.close()
+        ms64 = allmax(ws, ms64)
+        fp64 = {"value": n_vis * ws / (ms64 * 1e-3), "unit": UNIT, "ms_per_step": ms64,
+                "speedup_mixed_vs_fp64": ms64 / ms_max}
+
+    # end to end through the C ABI with host buffers
+    e2e = None
+    if args.e2e_steps > 0:
+        try:
+            e2e = run_e2e(args, wl, tuning, n_vis, ws)
+        except (RuntimeError, MemoryError) as exc:
+            e2e = {"error": str(exc)[:200]}
+
+    cpu = None
+    if rank == 0 and ws == 1 and args.cpu_sample > 0:
+        cpu = cpu_baseline(wl, f0, df, args.cpu_sample)
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32 (FP64 geometry, tables, seeds)", "data": "synthetic",
+            "config": {"workload": workload_name(wl), "n_vis_per_step": n_vis, "touched_cube_entries": touched,
+                       "l2_flush": "none needed: ~%.0f GB of inputs per step, L2 is 0.13 GB" % (alg / 1e9),
+                       "tuning": st_tuning_str(tuning), "parallelism": "replicas" if ws > 1 else "single"},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": None, "kernel": "stack_mixed",
+                         "algorithmic_bytes_per_launch": alg, "kernel_ms": stack_ms,
+                         "peak_source": peak_kind},
+            "prepass_ms": tm["prepass_ms"] / max(1, args.steps),
+            "fp64_gpu": fp64,
+            "e2e": e2e,
+            "cpu_baseline": cpu,
+            "gpu_launches": launches,
+            "clocks": clocks,
+        }
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def to_pinned(t):
+    if t is None:
+        return None
+    out = torch.empty(t.shape, dtype=t.dtype, pin_memory=True)
+    out.copy_(t)
+    return out
+
+
+def run_e2e(args, wl, tuning, n_vis, ws):
+    """Same metric through the public API with pinned HOST buffers: every step
+    copies its inputs host->device (inside vista_run) and reads the cube back
+    to host memory."""
+    from paper_2609_01897_gb300 import synth
+    from paper_2609_01897_gb300 import vista as V
+    host, h2d = [], 0
+    for s in wl.spws:
+        hs = synth.SourceSpw(to_pinned(s.uvw), s.freqs, to_pinned(s.vis), to_pinned(s.weights),
+                             to_pinned(s.flags), s.l, s.m, s.z, s.pol_map)
+        h2d += sum(t.numel() * t.element_size() for t in (hs.uvw, hs.vis, hs.weights, hs.flags)
+                   if t is not None)
+        host.append(hs)
+    ste = open_stack(wl, V.PREC_MIXED, tuning)
+    outs, t0 = None, 0.0
+    for it in range(1 + args.e2e_steps):
+        if it == 1:
+            torch.cuda.synchronize()
+            barrier(ws)
+            t0 = time.perf_counter()
+        one_step(ste, wl, host)
+        outs = ste.read_cube(device=False)
+    dt = (time.perf_counter() - t0) / args.e2e_steps
+    d2h = sum(v.numel() * v.element_size() for v in outs.values())
+    ste.close()
+    dt = allmax(ws, dt)
+    return {"value": n_vis * ws / dt, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+            "d2h_bytes_per_step": int(d2h), "ms_per_step": dt * 1e3}
+
+
+def workload_name(wl):
+    s0 = wl.spws[0]
+    return "%s: %d windows (%d sources), %d rows/window, %d ch x %d pol c64; cube %dx%dx%dx%d" % (
+        wl.name, len(wl.spws), len({s.source for s in wl.spws}), int(s0.vis.shape[0]), int(s0.vis.shape[1]),
+        int(s0.vis.shape[2]), wl.nv, wl.nu, wl.nrest, wl.npol)
+
+
+def st_tuning_str(t):
+    return "default" if not t else "rows=%d cpl=%d warps=%d sort=%d" % t
+
+
+# ------------------------------------------------------------------ reference arm
+
+def run_reference(args):
+    """The FP64 CPU oracle on the host cores, each step a bounded sample."""
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    from oracle import oracle as O
+    dev = "cuda" if torch.cuda.is_available() else "cpu"
+    nsample = max(1, args.cpu_sample)
+    a2 = argparse.Namespace(**vars(args))
+    a2.sources = max(1, math.ceil(nsample / 2)) if args.config != "tiny" else 0
+    wl = make_workload(a2, 0, dev)
+    spws = wl.spws[:nsample]
+    f0, df = O.auto_lattice([s.freqs for s in wl.spws], [s.z for s in wl.spws], wl.nrest, wl.central_freq)
+    srcs = [O.Source(s.uvw.cpu().numpy(), s.freqs, s.vis.cpu().numpy(), s.weights.cpu().numpy(),
+                     None if s.flags is None else s.flags.cpu().numpy(), s.l, s.m, s.z, s.pol_map) for s in spws]
+    cube = O.make_cube(wl.nu, wl.nv, wl.nrest, wl.npol, wl.du, wl.dv, f0, df, 0, 0)
+    nthreads = os.cpu_count() or 1
+    times, n = [], 0
+    for it in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        out = O.stack(cube, srcs, nthreads=nthreads)
+        dt = time.perf_counter() - t0
+        n = int(out["stats"]["n_vis"])
+        if it >= args.warmup:
+            times.append(dt)
+        del out
+    ms = 1e3 * float(np.mean(times))
+    value = n / (ms * 1e-3)
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": workload_name(wl) + " (sample of %d windows per step)" % nsample,
+                       "n_vis_per_step": n},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": nthreads, "kind": "oracle",
+                             "sample": "%d windows (%d visibilities) per step" % (nsample, n)},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+if __name__ == "__main__":
+    a = parse()
+    if a.impl == "reference":
+        run_reference(a)
+    else:
+        run_ours(a)

@@ -185,6 +185,22 @@ int vista_get_lattice(vista_stack *h, double *rest_f0, double *rest_df);
 int vista_set_tuning(vista_stack *h, const vista_tuning *t);
 int vista_get_tuning(vista_stack *h, vista_tuning *t);
 
+/* Per-phase device time of vista_run(), measured with CUDA events recorded
+ * on the handle's stream around each phase (the paper's compute_s timer,
+ * Sec. 4.2, split by kernel).  Accumulated over runs while enabled. */
+typedef struct {
+    double prepass_ms;   /* FP64 per-row pre-pass (and row ordering) kernels */
+    double stack_ms;     /* the stacking kernel(s) */
+    double other_ms;     /* host-memory copies and zeroing inside runs */
+    int64_t runs;        /* runs timed */
+    int64_t launches;    /* kernels launched by those runs */
+} vista_timing;
+
+/* on = 1 enables event timing (and resets the totals), 0 disables it. */
+int vista_enable_timing(vista_stack *h, int on);
+/* Waits for the stream, then reports the totals since timing was enabled. */
+int vista_get_timing(vista_stack *h, vista_timing *out);
+
 /* Wait for the stream, free every device and host resource, and forget the
  * handle; any later call with it returns E_STATE. */
 int vista_close(vista_stack *h);

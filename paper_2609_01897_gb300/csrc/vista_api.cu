@@ -78,6 +78,15 @@ struct vista_stack {
     std::vector<ClassRun> classes;
     LaunchCfg cfg{64, 4, 4, 0};
     std::string msg;
+    // event timing (vista_enable_timing)
+    bool timing = false;
+    struct Span {
+        cudaEvent_t a, b;
+        int kind;   // 0 prepass, 1 stack, 2 other
+    };
+    std::vector<Span> spans;
+    std::vector<cudaEvent_t> ev_pool;
+    vista_timing tacc{};
 };
 
 namespace {
@@ -113,6 +122,34 @@ bool live(const vista_stack *h)
     do {                                                                               \
         if (!live(h)) return fail(nullptr, VISTA_E_STATE, "unknown or closed handle"); \
     } while (0)
+
+cudaEvent_t take_event(vista_stack *h)
+{
+    if (!h->ev_pool.empty()) {
+        cudaEvent_t e = h->ev_pool.back();
+        h->ev_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+    return e;
+}
+
+// Open a timed span on the stream (no-op unless timing is enabled).
+int span_begin(vista_stack *h, int kind)
+{
+    if (!h->timing) return -1;
+    cudaEvent_t a = take_event(h), b = take_event(h);
+    if (!a || !b) return -1;
+    cudaEventRecord(a, h->stream);
+    h->spans.push_back({a, b, kind});
+    return (int)h->spans.size() - 1;
+}
+
+void span_end(vista_stack *h, int id)
+{
+    if (id >= 0) cudaEventRecord(h->spans[(size_t)id].b, h->stream);
+}
 
 size_t vis_elem_bytes(int vt)
 {
@@ -407,6 +444,7 @@ extern "C" int vista_run(vista_stack *h)
     std::vector<size_t> cls_src0(classes.size()), cls_off0(classes.size());
     int64_t rec_total = 0;
     size_t stage_pos = 0;
+    const int span_copy = stage_bytes ? span_begin(h, 2) : -1;
     for (size_t ci = 0; ci < classes.size(); ++ci) {
         ClassRun &cr = classes[ci];
         cls_src0[ci] = sdev.size();
@@ -476,6 +514,7 @@ extern "C" int vista_run(vista_stack *h)
         cr.args.nrows_total = roff[m];
         cr.args.nitems_total = ioff[m];
     }
+    span_end(h, span_copy);
 
     // 4. uploads
     if ((e = upload(h->b_srcs, sdev, h->stream)) != cudaSuccess) return cuda_fail(h, e, "source table upload");
@@ -502,13 +541,23 @@ extern "C" int vista_run(vista_stack *h)
         a.stats = h->stats;
         a.err = h->err;
         if (fp64) {
+            const int sp = span_begin(h, 1);
             e = launch_fp64(a, h->stream);
+            span_end(h, sp);
+            h->tacc.launches += h->timing && a.nrows_total > 0;
         } else {
+            int sp = span_begin(h, 0);
             e = launch_prepass(a, cfg, h->stream);
+            span_end(h, sp);
+            h->tacc.launches += h->timing && a.nrows_total > 0;
+            sp = span_begin(h, 1);
             if (e == cudaSuccess) e = launch_mixed(a, cfg, cr.npol_vt, h->stream);
+            span_end(h, sp);
+            h->tacc.launches += h->timing && a.nitems_total > 0;
         }
         if (e != cudaSuccess) return cuda_fail(h, e, "kernel launch");
     }
+    if (h->timing) h->tacc.runs += 1;
     bool any_host = false;
     for (const SrcHost &s : h->pending) any_host |= s.d.mem == VISTA_MEM_HOST;
     if (any_host && (e = cudaStreamSynchronize(h->stream)) != cudaSuccess)
@@ -650,6 +699,41 @@ extern "C" int vista_get_tuning(vista_stack *h, vista_tuning *t)
     return VISTA_OK;
 }
 
+extern "C" int vista_enable_timing(vista_stack *h, int on)
+{
+    CHECK_HANDLE(h);
+    if (on != 0 && on != 1) return fail(h, VISTA_E_ARG, "on must be 0 or 1");
+    cudaError_t e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "stream synchronize");
+    for (auto &s : h->spans) {
+        h->ev_pool.push_back(s.a);
+        h->ev_pool.push_back(s.b);
+    }
+    h->spans.clear();
+    h->tacc = vista_timing{};
+    h->timing = on != 0;
+    return VISTA_OK;
+}
+
+extern "C" int vista_get_timing(vista_stack *h, vista_timing *out)
+{
+    CHECK_HANDLE(h);
+    if (!out) return fail(h, VISTA_E_ARG, "null output");
+    cudaError_t e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "stream synchronize");
+    for (auto &s : h->spans) {
+        float ms = 0.f;
+        e = cudaEventElapsedTime(&ms, s.a, s.b);
+        if (e != cudaSuccess) return cuda_fail(h, e, "event timing");
+        (s.kind == 0 ? h->tacc.prepass_ms : s.kind == 1 ? h->tacc.stack_ms : h->tacc.other_ms) += ms;
+        h->ev_pool.push_back(s.a);
+        h->ev_pool.push_back(s.b);
+    }
+    h->spans.clear();
+    *out = h->tacc;
+    return VISTA_OK;
+}
+
 extern "C" int vista_close(vista_stack *h)
 {
     CHECK_HANDLE(h);
@@ -658,6 +742,11 @@ extern "C" int vista_close(vista_stack *h)
         g_live.erase(h);
     }
     cudaStreamSynchronize(h->stream);
+    for (auto &s : h->spans) {
+        cudaEventDestroy(s.a);
+        cudaEventDestroy(s.b);
+    }
+    for (cudaEvent_t ev : h->ev_pool) cudaEventDestroy(ev);
     cudaFree(h->cube);
     cudaFree(h->count);
     cudaFree(h->stats);

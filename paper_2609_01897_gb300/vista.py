@@ -54,6 +54,14 @@ class Tuning(C.Structure):
                 ("warps_per_cta", C.c_int32), ("sort_rows", C.c_int32)]
 
 
+class Timing(C.Structure):
+    _fields_ = [("prepass_ms", C.c_double), ("stack_ms", C.c_double), ("other_ms", C.c_double),
+                ("runs", C.c_int64), ("launches", C.c_int64)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
 class VistaError(RuntimeError):
     def __init__(self, call, code, msg):
         super().__init__("%s failed: %s: %s" % (call, _CODES.get(code, code), msg))
@@ -73,6 +81,8 @@ SIGNATURES = {
     "vista_get_lattice": (C.c_int, [_P, C.POINTER(C.c_double), C.POINTER(C.c_double)]),
     "vista_set_tuning": (C.c_int, [_P, C.POINTER(Tuning)]),
     "vista_get_tuning": (C.c_int, [_P, C.POINTER(Tuning)]),
+    "vista_enable_timing": (C.c_int, [_P, C.c_int]),
+    "vista_get_timing": (C.c_int, [_P, C.POINTER(Timing)]),
     "vista_close": (C.c_int, [_P]),
     "vista_last_error": (C.c_char_p, [_P]),
     "vista_abi_version": (C.c_int, []),
@@ -228,6 +238,14 @@ class Stack:
         t = Tuning()
         _check("vista_get_tuning", lib().vista_get_tuning(self.h, C.byref(t)), self.h)
         return {k: getattr(t, k) for k, _ in Tuning._fields_}
+
+    def enable_timing(self, on=True):
+        _check("vista_enable_timing", lib().vista_enable_timing(self.h, 1 if on else 0), self.h)
+
+    def timing(self):
+        t = Timing()
+        _check("vista_get_timing", lib().vista_get_timing(self.h, C.byref(t)), self.h)
+        return t.as_dict()
 
     def debug_phasors(self, src, nrow, nchan):
         out = torch.zeros((nrow, nchan, 2), dtype=torch.float64, device="cuda")
