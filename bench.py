@@ -215,10 +215,23 @@ def timed_steps(st, wl, steps, warmup, ws, host=None):
     return ms, t
 
 
+def windows_in_cube(wl, f0, df, n):
+    """The first n windows that have channels inside the cube's rest range."""
+    from paper_2609_01897_gb300 import vista as V
+    out = []
+    for s in wl.spws:
+        _, nb, _ = V.plan_channels(s.freqs, s.z, f0, df, wl.nrest, V.BIN_OVERLAP)
+        if (nb > 0).any():
+            out.append(s)
+        if len(out) == n:
+            break
+    return out
+
+
 def cpu_baseline(wl, f0, df, nsample):
     from oracle import oracle as O
     srcs = []
-    for s in wl.spws[:nsample]:
+    for s in windows_in_cube(wl, f0, df, nsample):
         srcs.append(O.Source(s.uvw.cpu().numpy(), s.freqs, s.vis.cpu().numpy(), s.weights.cpu().numpy(),
                              None if s.flags is None else s.flags.cpu().numpy(), s.l, s.m, s.z, s.pol_map))
     cube = O.make_cube(wl.nu, wl.nv, wl.nrest, wl.npol, wl.du, wl.dv, f0, df, 0, 0)
@@ -369,11 +382,23 @@ def run_reference(args):
     from oracle import oracle as O
     dev = "cuda" if torch.cuda.is_available() else "cpu"
     nsample = max(1, args.cpu_sample)
-    a2 = argparse.Namespace(**vars(args))
-    a2.sources = max(1, math.ceil(nsample / 2)) if args.config != "tiny" else 0
-    wl = make_workload(a2, 0, dev)
-    spws = wl.spws[:nsample]
-    f0, df = O.auto_lattice([s.freqs for s in wl.spws], [s.z for s in wl.spws], wl.nrest, wl.central_freq)
+    if args.config == "alma_compact":
+        # geometry and channel axes of every source (the lattice and the cell
+        # size depend on all), visibilities only for the sampled windows
+        from paper_2609_01897_gb300 import synth
+        meta = synth.alma_compact("cpu", n_sources=64, meta_only=True)
+        f0, df = O.auto_lattice([s.freqs for s in meta.spws], [s.z for s in meta.spws], meta.nrest,
+                                meta.central_freq)
+        picked = windows_in_cube(meta, f0, df, nsample)
+        ids = sorted({s.source for s in picked})
+        wl = synth.alma_compact(dev, src_ids=ids, du=meta.du)
+        keep = {(s.source, float(s.freqs[0])) for s in picked}
+        spws = [s for s in wl.spws if (s.source, float(s.freqs[0])) in keep]
+    else:
+        wl = make_workload(argparse.Namespace(**vars(args)), 0, dev)
+        f0, df = O.auto_lattice([s.freqs for s in wl.spws], [s.z for s in wl.spws], wl.nrest,
+                                wl.central_freq)
+        spws = windows_in_cube(wl, f0, df, nsample)
     srcs = [O.Source(s.uvw.cpu().numpy(), s.freqs, s.vis.cpu().numpy(), s.weights.cpu().numpy(),
                      None if s.flags is None else s.flags.cpu().numpy(), s.l, s.m, s.z, s.pol_map) for s in spws]
     cube = O.make_cube(wl.nu, wl.nv, wl.nrest, wl.npol, wl.du, wl.dv, f0, df, 0, 0)

@@ -18,7 +18,7 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libvista.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-CU_SOURCES = ["vista_kernels.cu", "vista_api.cu"]
+CU_SOURCES = ["vista_kernels.cu", "vista_order.cu", "vista_run.cu", "vista_api.cu"]
 CXX_SOURCES = ["planner.cpp"]
 
 
@@ -31,7 +31,7 @@ def _nvcc():
 
 def _sources():
     out = [os.path.join(CSRC, f) for f in CU_SOURCES + CXX_SOURCES]
-    out += [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith(".h")]
+    out += [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".h", ".cuh"))]
     out.append(os.path.join(INCLUDE, "vista.h"))
     return out
 

@@ -1,19 +1,14 @@
-// libvista C ABI: handle life cycle, validation, host planning and launch
-// orchestration (see include/vista.h for the contract of every call).
+// libvista C ABI: handle life cycle, validation, readback, counters, timing
+// and debug exports (vista_run lives in vista_run.cu).  The contract of
+// every call is in include/vista.h.
+#include <algorithm>
 #include <cmath>
-#include <cstdarg>
 #include <cstdio>
 #include <cstring>
 #include <mutex>
 #include <set>
-#include <string>
-#include <vector>
 
-#include <cuda_runtime.h>
-
-#include "planner.h"
-#include "vista.h"
-#include "vista_internal.h"
+#include "vista_handle.h"
 
 using namespace vista;
 
@@ -23,75 +18,51 @@ thread_local std::string g_err;
 std::mutex g_mu;
 std::set<const vista_stack *> g_live;
 
-struct DevBuf {
-    void *p = nullptr;
-    size_t cap = 0;
-    cudaError_t ensure(size_t bytes)
-    {
-        if (bytes <= cap) return cudaSuccess;
-        if (p) cudaFree(p);
-        p = nullptr;
-        cap = 0;
-        size_t want = bytes + bytes / 8 + 256;   // some headroom against regrowth
-        cudaError_t e = cudaMalloc(&p, want);
-        if (e == cudaSuccess) cap = want;
-        return e;
-    }
-    void release()
-    {
-        if (p) cudaFree(p);
-        p = nullptr;
-        cap = 0;
-    }
-};
-
-struct SrcHost {
-    vista_source_desc d;
-    std::vector<double> freqs;
-    std::vector<int32_t> pol_map;   // npol entries (identity filled in)
-};
-
-// One launch class of a run: windows that share (vis_type, npol).
-struct ClassRun {
-    int npol_vt = 0;
-    RunArgs args{};
-    std::vector<int> members;       // run-order index of each window
-};
-
 bool is_fin(double x) { return std::isfinite(x); }
+
+#define CHECK_HANDLE(h)                                                                \
+    do {                                                                               \
+        if (!handle_live(h)) return fail(nullptr, VISTA_E_STATE, "unknown or closed handle"); \
+    } while (0)
+
+// Row-ordering stripes: a few iv rows of the cube whose FP32 entries fit in
+// about 40 MB, so the cube region a stripe's work touches stays in L2; the
+// cell key inside a stripe must fit the shared-memory histogram.
+int stripe_geometry(vista_stack *h)
+{
+    const vista_cube_desc &d = h->desc;
+    const double row_bytes = (double)d.nu * d.nrest * d.npol * 20.0;
+    int S = (int)std::max(1.0, std::min((double)d.nv, std::floor(40e6 / row_bytes)));
+    int ushift = 0, nuk = d.nu;
+    while ((int64_t)S * nuk > MAX_LOCAL_KEYS) {
+        if (S > 1) {
+            S = std::max(1, MAX_LOCAL_KEYS / nuk);
+            if ((int64_t)S * nuk <= MAX_LOCAL_KEYS) break;
+            S = 1;
+        } else {
+            ++ushift;
+            nuk = (d.nu + (1 << ushift) - 1) >> ushift;
+        }
+    }
+    const int nst = (d.nv + S - 1) / S;
+    if (nst >= (1 << 19)) return VISTA_E_RANGE;
+    h->stripe_rows = S;
+    h->nstripe = nst;
+    h->ushift = ushift;
+    h->nuk = nuk;
+    return VISTA_OK;
+}
 
 }  // namespace
 
-struct vista_stack {
-    vista_cube_desc desc{};
-    cudaStream_t stream = nullptr;
-    int device = 0;
-    bool lattice_fixed = false;
-    double f0 = 0.0, df = 0.0;
-    std::vector<SrcHost> pending, last;
-    void *cube = nullptr;
-    uint32_t *count = nullptr;
-    int64_t nentries = 0;
-    DevStats *stats = nullptr;
-    int32_t *err = nullptr;
-    DevBuf b_srcs, b_chf, b_chd, b_recs, b_off, b_stage, b_unpack;
-    std::vector<ClassRun> classes;
-    LaunchCfg cfg{64, 4, 4, 0};
-    std::string msg;
-    // event timing (vista_enable_timing)
-    bool timing = false;
-    struct Span {
-        cudaEvent_t a, b;
-        int kind;   // 0 prepass, 1 stack, 2 other
-    };
-    std::vector<Span> spans;
-    std::vector<cudaEvent_t> ev_pool;
-    vista_timing tacc{};
-};
+namespace vista {
 
-namespace {
+bool handle_live(const vista_stack *h)
+{
+    std::lock_guard<std::mutex> lk(g_mu);
+    return h && g_live.count(h) != 0;
+}
 
-int fail(vista_stack *h, int code, const char *fmt, ...) __attribute__((format(printf, 3, 4)));
 int fail(vista_stack *h, int code, const char *fmt, ...)
 {
     char buf[512];
@@ -112,18 +83,7 @@ int cuda_fail(vista_stack *h, cudaError_t e, const char *what)
                 cudaGetErrorString(e));
 }
 
-bool live(const vista_stack *h)
-{
-    std::lock_guard<std::mutex> lk(g_mu);
-    return h && g_live.count(h) != 0;
-}
-
-#define CHECK_HANDLE(h)                                                                \
-    do {                                                                               \
-        if (!live(h)) return fail(nullptr, VISTA_E_STATE, "unknown or closed handle"); \
-    } while (0)
-
-cudaEvent_t take_event(vista_stack *h)
+static cudaEvent_t take_event(vista_stack *h)
 {
     if (!h->ev_pool.empty()) {
         cudaEvent_t e = h->ev_pool.back();
@@ -135,7 +95,6 @@ cudaEvent_t take_event(vista_stack *h)
     return e;
 }
 
-// Open a timed span on the stream (no-op unless timing is enabled).
 int span_begin(vista_stack *h, int kind)
 {
     if (!h->timing) return -1;
@@ -160,7 +119,7 @@ size_t vis_elem_bytes(int vt)
     }
 }
 
-}  // namespace
+}  // namespace vista
 
 // ------------------------------------------------------------------ open
 
@@ -201,6 +160,10 @@ extern "C" int vista_open_stack(const vista_cube_desc *d, vista_stack **out)
         h->f0 = d->rest_f0;
         h->df = d->rest_df;
     }
+    if (stripe_geometry(h) != VISTA_OK) {
+        delete h;
+        return fail(nullptr, VISTA_E_RANGE, "cube too tall for the row ordering (nv / stripe >= 2^19)");
+    }
     cudaError_t e = cudaGetDevice(&h->device);
     const size_t esz = d->precision == VISTA_PREC_FP64 ? 32 : 16;
     if (e == cudaSuccess) e = cudaMalloc(&h->cube, (size_t)n * esz);
@@ -213,7 +176,7 @@ extern "C" int vista_open_stack(const vista_cube_desc *d, vista_stack **out)
     if (e == cudaSuccess) e = cudaMemsetAsync(h->err, 0, sizeof(int32_t), h->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
     if (e != cudaSuccess) {
-        int rc = cuda_fail(nullptr, e, "cube allocation");
+        const int rc = cuda_fail(nullptr, e, "cube allocation");
         cudaFree(h->cube);
         cudaFree(h->count);
         cudaFree(h->stats);
@@ -254,6 +217,7 @@ extern "C" int vista_add_source(vista_stack *h, const vista_source_desc *s)
     if (!(is_fin(s->l) && is_fin(s->m) && s->l * s->l + s->m * s->m < 1.0))
         return fail(h, VISTA_E_ARG, "need finite l, m with l^2 + m^2 < 1");
     if (!(is_fin(s->z) && s->z > -1.0)) return fail(h, VISTA_E_ARG, "need finite z > -1");
+    if ((int64_t)s->nrow * s->nchan > ((int64_t)1 << 40)) return fail(h, VISTA_E_RANGE, "window too large");
     for (int32_t k = 0; k < s->nchan; ++k) {
         const double f = s->freqs[k];
         if (!(is_fin(f) && f > 0.0)) return fail(h, VISTA_E_ARG, "freqs[%d] is not finite and > 0", k);
@@ -290,284 +254,6 @@ extern "C" int vista_add_source(vista_stack *h, const vista_source_desc *s)
     return VISTA_OK;
 }
 
-// -------------------------------------------------------------------- run
-
-namespace {
-
-struct Plan {
-    int32_t k_lo = 0, k_hi = 0;
-    bool linear = true;
-    double step = 0.0;
-    std::vector<ChanF> chf;
-    std::vector<ChanD> chd;
-};
-
-int plan_source(vista_stack *h, const SrcHost &s, double gu, double gv, Plan &pl)
-{
-    const int32_t n = s.d.nchan;
-    std::vector<int32_t> j0((size_t)n), nb((size_t)n);
-    std::vector<double> w((size_t)n * VISTA_MAX_BINS);
-    int rc = channel_bins(s.freqs.data(), n, s.d.z, h->f0, h->df, h->desc.nrest, h->desc.bin_mode, j0.data(),
-                          nb.data(), w.data());
-    if (rc == VISTA_E_RANGE)
-        return fail(h, VISTA_E_RANGE, "a channel touches more than %d rest bins (rest_df too small)",
-                    VISTA_MAX_BINS);
-    if (rc != VISTA_OK) return fail(h, rc, "channel planning failed");
-    int32_t lo = -1, hi = -1;
-    for (int32_t k = 0; k < n; ++k)
-        if (nb[(size_t)k] > 0) {
-            if (lo < 0) lo = k;
-            hi = k + 1;
-        }
-    if (lo < 0) lo = hi = 0;
-    pl.k_lo = lo;
-    pl.k_hi = hi;
-    pl.linear = linear_axis(s.freqs.data(), n, &pl.step);
-    pl.chf.resize((size_t)(hi - lo));
-    pl.chd.resize((size_t)(hi - lo));
-    for (int32_t k = lo; k < hi; ++k) {
-        ChanD &d = pl.chd[(size_t)(k - lo)];
-        ChanF &f = pl.chf[(size_t)(k - lo)];
-        d.su = s.freqs[(size_t)k] * gu;
-        d.sv = s.freqs[(size_t)k] * gv;
-        d.nu = s.freqs[(size_t)k];
-        d.j0 = j0[(size_t)k];
-        d.nb = nb[(size_t)k];
-        f.su = (float)d.su;
-        f.sv = (float)d.sv;
-        f.j0 = d.j0;
-        f.nb = d.nb;
-        for (int b = 0; b < VISTA_MAX_BINS; ++b) {
-            d.w[b] = w[(size_t)k * VISTA_MAX_BINS + b];
-            f.w[b] = (float)d.w[b];
-        }
-    }
-    return VISTA_OK;
-}
-
-template <typename T>
-cudaError_t upload(DevBuf &b, const std::vector<T> &v, cudaStream_t st)
-{
-    const size_t bytes = v.size() * sizeof(T);
-    cudaError_t e = b.ensure(bytes > 0 ? bytes : 16);
-    if (e != cudaSuccess || bytes == 0) return e;
-    return cudaMemcpyAsync(b.p, v.data(), bytes, cudaMemcpyHostToDevice, st);
-}
-
-}  // namespace
-
-extern "C" int vista_run(vista_stack *h)
-{
-    CHECK_HANDLE(h);
-    if (h->pending.empty()) return fail(h, VISTA_E_STATE, "vista_run with no queued source");
-    const vista_cube_desc &c = h->desc;
-    const bool fp64 = c.precision == VISTA_PREC_FP64;
-    cudaError_t e;
-
-    // 1. the rest lattice (fixed at the first run)
-    double f0 = h->f0, df = h->df;
-    if (!h->lattice_fixed) {
-        double best = 0.0;
-        for (const SrcHost &s : h->pending) {
-            if (s.d.nchan < 2)
-                return fail(h, VISTA_E_ARG, "the automatic rest lattice needs >= 2 channels per window");
-            const double wdt = widest_rest_channel(s.freqs.data(), s.d.nchan, s.d.z);
-            if (wdt > best) best = wdt;
-        }
-        if (!(best > 0.0)) return fail(h, VISTA_E_ARG, "automatic rest lattice: zero channel width");
-        df = best;
-        f0 = lattice_f0(c.central_freq, c.nrest, best);
-    }
-    const double saved_f0 = h->f0, saved_df = h->df;
-    h->f0 = f0;
-    h->df = df;
-
-    // 2. channel tables
-    const double gu = 1.0 / (C_LIGHT * c.du), gv = 1.0 / (C_LIGHT * c.dv);
-    const int nsrc = (int)h->pending.size();
-    std::vector<Plan> plans((size_t)nsrc);
-    for (int i = 0; i < nsrc; ++i) {
-        int rc = plan_source(h, h->pending[(size_t)i], gu, gv, plans[(size_t)i]);
-        if (rc != VISTA_OK) {
-            h->f0 = saved_f0;
-            h->df = saved_df;
-            return rc;
-        }
-    }
-    h->lattice_fixed = true;
-
-    // 3. launch classes and flattened host tables
-    const LaunchCfg cfg = h->cfg;
-    const int cw = 32 * cfg.chans_per_lane;
-    std::vector<ClassRun> classes;
-    std::vector<int> cls_of((size_t)nsrc);
-    for (int i = 0; i < nsrc; ++i) {
-        const SrcHost &s = h->pending[(size_t)i];
-        const int key = fp64 ? 0 : ((s.d.vis_type << 8) | s.d.npol);
-        int ci = -1;
-        for (size_t j = 0; j < classes.size(); ++j)
-            if (classes[j].npol_vt == key) ci = (int)j;
-        if (ci < 0) {
-            classes.emplace_back();
-            classes.back().npol_vt = key;
-            ci = (int)classes.size() - 1;
-        }
-        classes[(size_t)ci].members.push_back(i);
-        cls_of[(size_t)i] = ci;
-    }
-    std::vector<ChanF> chf;
-    std::vector<ChanD> chd;
-    std::vector<int32_t> chan_off((size_t)nsrc);
-    for (int i = 0; i < nsrc; ++i) {
-        chan_off[(size_t)i] = (int32_t)chf.size();
-        chf.insert(chf.end(), plans[(size_t)i].chf.begin(), plans[(size_t)i].chf.end());
-        chd.insert(chd.end(), plans[(size_t)i].chd.begin(), plans[(size_t)i].chd.end());
-    }
-    if (chf.size() > (size_t)0x7fffffff) return fail(h, VISTA_E_RANGE, "too many channels in one run");
-
-    // host-memory windows: staging layout
-    size_t stage_bytes = 0;
-    auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
-    for (const SrcHost &s : h->pending)
-        if (s.d.mem == VISTA_MEM_HOST && s.d.nrow > 0) {
-            const size_t nr = (size_t)s.d.nrow, nvv = nr * (size_t)s.d.nchan * (size_t)s.d.npol;
-            stage_bytes += al(nr * 24) + al(nvv * vis_elem_bytes(s.d.vis_type)) + al(nr * 4 * (size_t)s.d.npol) +
-                           (s.d.flags ? al(nvv) : 0);
-        }
-    if (stage_bytes) {
-        e = h->b_stage.ensure(stage_bytes);
-        if (e != cudaSuccess) return cuda_fail(h, e, "staging allocation");
-    }
-
-    std::vector<SrcDev> sdev;
-    std::vector<int64_t> offs;     // per class: row_off[n+1] then item_off[n+1]
-    std::vector<size_t> cls_src0(classes.size()), cls_off0(classes.size());
-    int64_t rec_total = 0;
-    size_t stage_pos = 0;
-    const int span_copy = stage_bytes ? span_begin(h, 2) : -1;
-    for (size_t ci = 0; ci < classes.size(); ++ci) {
-        ClassRun &cr = classes[ci];
-        cls_src0[ci] = sdev.size();
-        cls_off0[ci] = offs.size();
-        const size_t m = cr.members.size();
-        std::vector<int64_t> roff(m + 1, 0), ioff(m + 1, 0);
-        for (size_t t = 0; t < m; ++t) {
-            const int i = cr.members[t];
-            const SrcHost &s = h->pending[(size_t)i];
-            const Plan &pl = plans[(size_t)i];
-            SrcDev d{};
-            d.uvw = s.d.uvw;
-            d.vis = s.d.vis;
-            d.wts = s.d.weights;
-            d.flags = s.d.flags;
-            if (s.d.mem == VISTA_MEM_HOST && s.d.nrow > 0) {
-                const size_t nr = (size_t)s.d.nrow, nvv = nr * (size_t)s.d.nchan * (size_t)s.d.npol;
-                char *base = (char *)h->b_stage.p;
-                const size_t b_uvw = nr * 24, b_vis = nvv * vis_elem_bytes(s.d.vis_type),
-                             b_w = nr * 4 * (size_t)s.d.npol;
-                char *p_uvw = base + stage_pos;
-                stage_pos += al(b_uvw);
-                char *p_vis = base + stage_pos;
-                stage_pos += al(b_vis);
-                char *p_w = base + stage_pos;
-                stage_pos += al(b_w);
-                char *p_f = nullptr;
-                if (s.d.flags) {
-                    p_f = base + stage_pos;
-                    stage_pos += al(nvv);
-                }
-                e = cudaMemcpyAsync(p_uvw, s.d.uvw, b_uvw, cudaMemcpyHostToDevice, h->stream);
-                if (e == cudaSuccess) e = cudaMemcpyAsync(p_vis, s.d.vis, b_vis, cudaMemcpyHostToDevice, h->stream);
-                if (e == cudaSuccess) e = cudaMemcpyAsync(p_w, s.d.weights, b_w, cudaMemcpyHostToDevice, h->stream);
-                if (e == cudaSuccess && p_f) e = cudaMemcpyAsync(p_f, s.d.flags, nvv, cudaMemcpyHostToDevice, h->stream);
-                if (e != cudaSuccess) return cuda_fail(h, e, "host-to-device copy of a host-memory window");
-                d.uvw = (const double *)p_uvw;
-                d.vis = p_vis;
-                d.wts = (const float *)p_w;
-                d.flags = (const uint8_t *)p_f;
-            }
-            d.nrow = s.d.nrow;
-            d.nchan = s.d.nchan;
-            d.npol = s.d.npol;
-            d.vis_type = s.d.vis_type;
-            d.vis_scale = (s.d.vis_type == VISTA_VIS_F16X2 || s.d.vis_type == VISTA_VIS_BF16X2) ? s.d.vis_scale : 1.0f;
-            d.l = s.d.l;
-            d.m = s.d.m;
-            d.n1 = std::sqrt(1.0 - s.d.l * s.d.l - s.d.m * s.d.m) - 1.0;
-            d.step_c = pl.step / C_LIGHT;
-            d.k_lo = pl.k_lo;
-            d.k_hi = pl.k_hi;
-            d.chan_off = chan_off[(size_t)i];
-            d.linear = pl.linear ? 1 : 0;
-            for (int p = 0; p < 4; ++p) d.plane[p] = p < s.d.npol ? s.pol_map[(size_t)p] : -1;
-            d.nchunk = pl.k_hi > pl.k_lo ? (pl.k_hi - pl.k_lo + cw - 1) / cw : 0;
-            d.rec_off = rec_total;
-            if (!fp64) rec_total += (int64_t)d.nchunk * d.nrow;
-            const int64_t ntile = (d.nrow + cfg.rows_per_item - 1) / cfg.rows_per_item;
-            roff[t + 1] = roff[t] + d.nrow;
-            ioff[t + 1] = ioff[t] + (int64_t)d.nchunk * ntile;
-            sdev.push_back(d);
-        }
-        offs.insert(offs.end(), roff.begin(), roff.end());
-        offs.insert(offs.end(), ioff.begin(), ioff.end());
-        cr.args.nsrc = (int32_t)m;
-        cr.args.nrows_total = roff[m];
-        cr.args.nitems_total = ioff[m];
-    }
-    span_end(h, span_copy);
-
-    // 4. uploads
-    if ((e = upload(h->b_srcs, sdev, h->stream)) != cudaSuccess) return cuda_fail(h, e, "source table upload");
-    if ((e = upload(h->b_chf, chf, h->stream)) != cudaSuccess) return cuda_fail(h, e, "channel table upload");
-    if ((e = upload(h->b_chd, chd, h->stream)) != cudaSuccess) return cuda_fail(h, e, "channel table upload");
-    if ((e = upload(h->b_off, offs, h->stream)) != cudaSuccess) return cuda_fail(h, e, "offset table upload");
-    if (!fp64 && (e = h->b_recs.ensure((size_t)(rec_total > 0 ? rec_total : 1) * sizeof(RowRec))) != cudaSuccess)
-        return cuda_fail(h, e, "row record allocation");
-
-    // 5. launches
-    CubeGeom g{c.nu, c.nv, c.nrest, c.npol, gu, gv, c.hermitian_fold, 0};
-    for (size_t ci = 0; ci < classes.size(); ++ci) {
-        ClassRun &cr = classes[ci];
-        RunArgs &a = cr.args;
-        a.srcs = (const SrcDev *)h->b_srcs.p + cls_src0[ci];
-        a.chf = (const ChanF *)h->b_chf.p;
-        a.chd = (const ChanD *)h->b_chd.p;
-        a.recs = (RowRec *)h->b_recs.p;
-        a.row_off = (const int64_t *)h->b_off.p + cls_off0[ci];
-        a.item_off = a.row_off + (cr.members.size() + 1);
-        a.g = g;
-        a.cube = h->cube;
-        a.count = h->count;
-        a.stats = h->stats;
-        a.err = h->err;
-        if (fp64) {
-            const int sp = span_begin(h, 1);
-            e = launch_fp64(a, h->stream);
-            span_end(h, sp);
-            h->tacc.launches += h->timing && a.nrows_total > 0;
-        } else {
-            int sp = span_begin(h, 0);
-            e = launch_prepass(a, cfg, h->stream);
-            span_end(h, sp);
-            h->tacc.launches += h->timing && a.nrows_total > 0;
-            sp = span_begin(h, 1);
-            if (e == cudaSuccess) e = launch_mixed(a, cfg, cr.npol_vt, h->stream);
-            span_end(h, sp);
-            h->tacc.launches += h->timing && a.nitems_total > 0;
-        }
-        if (e != cudaSuccess) return cuda_fail(h, e, "kernel launch");
-    }
-    if (h->timing) h->tacc.runs += 1;
-    bool any_host = false;
-    for (const SrcHost &s : h->pending) any_host |= s.d.mem == VISTA_MEM_HOST;
-    if (any_host && (e = cudaStreamSynchronize(h->stream)) != cudaSuccess)
-        return cuda_fail(h, e, "stream synchronize after host-memory copies");
-    h->classes = std::move(classes);
-    h->last = std::move(h->pending);
-    h->pending.clear();
-    return VISTA_OK;
-}
-
 // --------------------------------------------------------------- readback
 
 namespace {
@@ -580,7 +266,7 @@ int read_common(vista_stack *h, void *sum_wv, void *sum_w, void *sum_wvv, uint32
     int32_t err = 0;
     e = cudaMemcpy(&err, h->err, sizeof err, cudaMemcpyDeviceToHost);
     if (e != cudaSuccess) return cuda_fail(h, e, "error word read");
-    if (err != 0) return fail(h, VISTA_E_TIMEOUT, "a device-side wait gave up (code %d)", err);
+    if (err != 0) return fail(h, VISTA_E_TIMEOUT, "a device-side wait or check gave up (code %d)", err);
     const int fp64 = h->desc.precision == VISTA_PREC_FP64;
     const int64_t n = h->nentries;
     const size_t fe = out_f64 ? 8 : 4;
@@ -758,13 +444,14 @@ extern "C" int vista_close(vista_stack *h)
     h->b_off.release();
     h->b_stage.release();
     h->b_unpack.release();
+    h->b_sort.release();
     delete h;
     return VISTA_OK;
 }
 
 extern "C" const char *vista_last_error(const vista_stack *h)
 {
-    if (h && live(h)) return h->msg.c_str();
+    if (h && handle_live(h)) return h->msg.c_str();
     return g_err.c_str();
 }
 
@@ -778,14 +465,14 @@ int debug_common(vista_stack *h, int32_t src, double *ph, int32_t *cells)
     for (const ClassRun &cr : h->classes) {
         for (size_t t = 0; t < cr.members.size(); ++t) {
             if (cr.members[t] != src) continue;
-            cudaError_t e = launch_debug(cr.args, h->cfg, (int)t, h->desc.precision == VISTA_PREC_FP64, ph,
-                                         cells, h->stream);
+            cudaError_t e = launch_debug(cr.args, cr.ns, (int)t, h->desc.precision == VISTA_PREC_FP64, ph, cells,
+                                         h->stream);
             if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
             if (e != cudaSuccess) return cuda_fail(h, e, "debug export");
             return VISTA_OK;
         }
     }
-    return fail(h, VISTA_E_STATE, "source %d not found in the last run", src);
+    return VISTA_OK;   // a window with no row or no channel in the cube: nothing is read
 }
 
 }  // namespace

@@ -1,0 +1,190 @@
+// Device helpers shared by the libvista kernels: work-list lookups, FP32
+// phasors, the guarded uv-cell rule and the visibility / flag loaders.
+#pragma once
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
+#include "vista_internal.h"
+
+namespace vista {
+
+// ---------------------------------------------------------------- helpers
+
+// Largest s with off[s] <= x (off non-decreasing, off[0] = 0).
+__device__ __forceinline__ int find_owner(const int64_t *__restrict__ off, int n, int64_t x)
+{
+    int lo = 0, hi = n - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (__ldg(off + mid) <= x)
+            lo = mid;
+        else
+            hi = mid - 1;
+    }
+    return lo;
+}
+
+__device__ __forceinline__ float2 cmul(float2 a, float2 b)
+{
+    return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+
+// exp(2 pi i t) for t in turns; t is first reduced to [-0.5, 0.5] (exact
+// for |t| < 2^22) so that sincospif sees its most accurate argument range.
+__device__ __forceinline__ float2 turns_to_phasor(float t)
+{
+    t = __fsub_rn(t, rintf(t));
+    float s, c;
+    sincospif(2.0f * t, &s, &c);
+    return make_float2(c, s);
+}
+
+// Seed phasor of channel c0 + lane of one row: t0 + frac(lane*dhi) + lane*dlo.
+// lane*dhi is exact (dhi has <= 19 significant bits, lane < 32).
+__device__ __forceinline__ float2 lane_seed(const RowRec &rec, int lane)
+{
+    float a = (float)lane * rec.dhi;
+    a = __fsub_rn(a, floorf(a));
+    float t = __fadd_rn(__fadd_rn(rec.t0, a), (float)lane * rec.dlo);
+    return turns_to_phasor(t);
+}
+
+// One axis of the uv cell: floor(fl64(coord * s_k)) + n/2, or -1 outside
+// [0, n).  Decided in FP32 when fl32(c32 * s32) is at least 2^-21 |x| away
+// from an integer (the FP32 product differs from the FP64 one by at most
+// 3 * 2^-24 |x|), else by the exact FP64 product.
+__device__ __forceinline__ int axis_cell(float c32, float s32, const double *coord64, bool neg,
+                                         const double *s64, int n)
+{
+    float x = __fmul_rn(c32, s32);
+    float d = __fmaf_rn(fabsf(x), 4.76837158203125e-07f, 1e-30f);
+    float fa = floorf(__fsub_rn(x, d)), fb = floorf(__fadd_rn(x, d));
+    float fx;
+    if (fa == fb) {
+        fx = fa;
+    } else {
+        double c = *coord64;
+        if (neg) c = -c;
+        fx = (float)floor(__dmul_rn(c, *s64));
+    }
+    float h = (float)(n >> 1);
+    if (!(fx >= -h && fx < h)) return -1;
+    return (int)fx + (n >> 1);
+}
+
+__device__ __forceinline__ int axis_cell64(double c, double s, int n)
+{
+    double x = __dmul_rn(c, s);
+    double h = (double)(n >> 1);
+    if (!(x >= -h && x < h)) return -1;
+    return (int)floor(x) + (n >> 1);
+}
+
+// ----------------------------------------------------------- vis loaders
+
+template <int P, int VT>
+struct VisLoad;
+
+template <int P>
+struct VisLoad<P, VISTA_VIS_C64> {
+    static __device__ __forceinline__ void load(const void *base, int64_t idx, float scale, float2 (&v)[P])
+    {
+        (void)scale;
+        const float2 *p = reinterpret_cast<const float2 *>(base) + idx * P;
+        if constexpr (P == 1) {
+            v[0] = __ldg(p);
+        } else if constexpr (P == 2) {
+            float4 q = __ldg(reinterpret_cast<const float4 *>(p));
+            v[0] = make_float2(q.x, q.y);
+            v[1] = make_float2(q.z, q.w);
+        } else {
+            float4 q0 = __ldg(reinterpret_cast<const float4 *>(p));
+            float4 q1 = __ldg(reinterpret_cast<const float4 *>(p) + 1);
+            v[0] = make_float2(q0.x, q0.y);
+            v[1] = make_float2(q0.z, q0.w);
+            v[2] = make_float2(q1.x, q1.y);
+            v[3] = make_float2(q1.z, q1.w);
+        }
+    }
+};
+
+template <int P>
+struct VisLoad<P, VISTA_VIS_C128> {
+    static __device__ __forceinline__ void load(const void *base, int64_t idx, float scale, float2 (&v)[P])
+    {
+        (void)scale;
+        const double2 *p = reinterpret_cast<const double2 *>(base) + idx * P;
+#pragma unroll
+        for (int i = 0; i < P; ++i) {
+            double2 q = __ldg(p + i);
+            v[i] = make_float2((float)q.x, (float)q.y);
+        }
+    }
+};
+
+
+template <int P>
+struct VisLoad<P, VISTA_VIS_F16X2> {
+    static __device__ __forceinline__ float2 cvt(uint32_t b, float scale)
+    {
+        __half2 h = *reinterpret_cast<__half2 *>(&b);
+        float2 f = __half22float2(h);
+        return make_float2(f.x * scale, f.y * scale);
+    }
+    static __device__ __forceinline__ void load(const void *base, int64_t idx, float scale, float2 (&v)[P])
+    {
+        const uint32_t *p = reinterpret_cast<const uint32_t *>(base) + idx * P;
+        if constexpr (P == 1) {
+            v[0] = cvt(__ldg(p), scale);
+        } else if constexpr (P == 2) {
+            uint2 q = __ldg(reinterpret_cast<const uint2 *>(p));
+            v[0] = cvt(q.x, scale);
+            v[1] = cvt(q.y, scale);
+        } else {
+            uint4 q = __ldg(reinterpret_cast<const uint4 *>(p));
+            v[0] = cvt(q.x, scale);
+            v[1] = cvt(q.y, scale);
+            v[2] = cvt(q.z, scale);
+            v[3] = cvt(q.w, scale);
+        }
+    }
+};
+
+template <int P>
+struct VisLoad<P, VISTA_VIS_BF16X2> {
+    static __device__ __forceinline__ float2 cvt(uint32_t b, float scale)
+    {
+        // bf16 -> f32 is a 16-bit shift
+        float re = __uint_as_float(b << 16), im = __uint_as_float(b & 0xffff0000u);
+        return make_float2(re * scale, im * scale);
+    }
+    static __device__ __forceinline__ void load(const void *base, int64_t idx, float scale, float2 (&v)[P])
+    {
+        const uint32_t *p = reinterpret_cast<const uint32_t *>(base) + idx * P;
+        if constexpr (P == 1) {
+            v[0] = cvt(__ldg(p), scale);
+        } else if constexpr (P == 2) {
+            uint2 q = __ldg(reinterpret_cast<const uint2 *>(p));
+            v[0] = cvt(q.x, scale);
+            v[1] = cvt(q.y, scale);
+        } else {
+            uint4 q = __ldg(reinterpret_cast<const uint4 *>(p));
+            v[0] = cvt(q.x, scale);
+            v[1] = cvt(q.y, scale);
+            v[2] = cvt(q.z, scale);
+            v[3] = cvt(q.w, scale);
+        }
+    }
+};
+
+template <int P>
+__device__ __forceinline__ uint32_t load_flags(const uint8_t *flags, int64_t idx)
+{
+    if (!flags) return 0u;
+    const uint8_t *p = flags + idx * P;
+    if constexpr (P == 1) return (uint32_t)__ldg(p);
+    else if constexpr (P == 2) return (uint32_t)__ldg(reinterpret_cast<const uint16_t *>(p));
+    else return __ldg(reinterpret_cast<const uint32_t *>(p));
+}
+
+}  // namespace vista

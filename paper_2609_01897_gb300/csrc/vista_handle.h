@@ -1,0 +1,93 @@
+// The libvista handle and the small host utilities the ABI translation
+// units share.
+#pragma once
+#include <cstdarg>
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "vista.h"
+#include "vista_internal.h"
+
+namespace vista {
+
+// A growable device buffer (grows by reallocation, never shrinks).
+struct DevBuf {
+    void *p = nullptr;
+    size_t cap = 0;
+    cudaError_t ensure(size_t bytes)
+    {
+        if (bytes <= cap) return cudaSuccess;
+        if (p) cudaFree(p);
+        p = nullptr;
+        cap = 0;
+        const size_t want = bytes + bytes / 8 + 256;   // headroom against regrowth
+        cudaError_t e = cudaMalloc(&p, want);
+        if (e == cudaSuccess) cap = want;
+        return e;
+    }
+    void release()
+    {
+        if (p) cudaFree(p);
+        p = nullptr;
+        cap = 0;
+    }
+};
+
+struct SrcHost {
+    vista_source_desc d;
+    std::vector<double> freqs;
+    std::vector<int32_t> pol_map;   // npol entries (identity filled in)
+};
+
+// One launch class of a run: windows that share the kernel instantiation.
+struct ClassRun {
+    int key = 0;                    // mixed: (vis_type << 16) | (NS << 8) | npol
+    int ns = 1;
+    RunArgs args{};
+    std::vector<int> members;       // run-order index of each window
+};
+
+struct Span {
+    cudaEvent_t a, b;
+    int kind;   // 0 prepass, 1 stack, 2 other
+};
+
+}  // namespace vista
+
+struct vista_stack {
+    vista_cube_desc desc{};
+    cudaStream_t stream = nullptr;
+    int device = 0;
+    bool lattice_fixed = false;
+    double f0 = 0.0, df = 0.0;
+    std::vector<vista::SrcHost> pending, last;
+    void *cube = nullptr;
+    uint32_t *count = nullptr;
+    int64_t nentries = 0;
+    vista::DevStats *stats = nullptr;
+    int32_t *err = nullptr;
+    vista::DevBuf b_srcs, b_chf, b_chd, b_recs, b_off, b_stage, b_unpack, b_sort;
+    std::vector<vista::ClassRun> classes;
+    vista::LaunchCfg cfg{64, 4, 4, 1};
+    // stripe geometry of the row ordering (depends on the cube only)
+    int32_t stripe_rows = 1, nstripe = 1, ushift = 0, nuk = 1;
+    std::string msg;
+    bool timing = false;
+    std::vector<vista::Span> spans;
+    std::vector<cudaEvent_t> ev_pool;
+    vista_timing tacc{};
+};
+
+namespace vista {
+
+bool handle_live(const vista_stack *h);
+int fail(vista_stack *h, int code, const char *fmt, ...) __attribute__((format(printf, 3, 4)));
+int cuda_fail(vista_stack *h, cudaError_t e, const char *what);
+int span_begin(vista_stack *h, int kind);
+void span_end(vista_stack *h, int id);
+size_t vis_elem_bytes(int vt);
+
+}  // namespace vista

@@ -9,6 +9,7 @@
 namespace vista {
 
 constexpr double C_LIGHT = 299792458.0;   // m/s
+constexpr int MAX_LOCAL_KEYS = 8192;      // cell keys inside one stripe (shared-memory histogram)
 
 // Cube geometry as the kernels see it.
 struct CubeGeom {
@@ -35,9 +36,9 @@ struct ChanD {
 // One (source, window) as the kernels see it.
 struct SrcDev {
     const double *uvw;
-    const void *vis;
+    const void *vis;        // element (row, k, p) at (row * vstride + k - kbase) * npol + p
     const float *wts;
-    const uint8_t *flags;
+    const uint8_t *flags;   // same indexing as vis
     int64_t nrow;
     int32_t nchan, npol;
     int32_t vis_type;
@@ -49,7 +50,10 @@ struct SrcDev {
     int32_t linear;         // 1: f_k = f_0 + k step (one recurrence step)
     int32_t plane[4];       // cube plane of each input pol, -1 = skip
     int32_t nchunk;         // work chunks along the channel axis
+    int32_t vstride;        // channels per stored row (nchan, or k_hi - k_lo when staged)
+    int32_t kbase;          // channel index of the first stored channel
     int32_t pad;
+    float key_su, key_sv;   // fl32(s_k) at the row-ordering reference channel
     int64_t rec_off;        // first row record of this window
 };
 
@@ -70,6 +74,12 @@ struct __align__(16) RowRec {
     float W[4];
 };
 
+// One unit of stacking work: rows [q0, q1) (in processing order) of window
+// w, channel chunk c.
+struct __align__(16) Item {
+    int32_t w, chunk, q0, q1;
+};
+
 // Counters (device), see vista_stats.
 struct DevStats {
     unsigned long long n_vis, n_flagged, n_dropped_uv, n_stacked;
@@ -77,37 +87,62 @@ struct DevStats {
 
 struct LaunchCfg {
     int32_t rows_per_item;
-    int32_t chans_per_lane;
+    int32_t chans_per_lane;     // upper bound; each window uses the smallest that fits
     int32_t warps_per_cta;
     int32_t sort_rows;
 };
 
-// Everything one mixed or FP64 run needs on the device.
+// Row ordering of one launch class (device buffers, see vista_kernels.cu).
+//   hist     [nwin][nstripe]    rows per (window, stripe)
+//   qstart   [nwin][nstripe]    first processing position of each bucket
+//   slot     [rows]             arrival slot of the row inside its bucket
+//   key      [rows]             stripe << 13 | local cell key
+//   tmp      [rows]             (local key << 32) | row, bucket-grouped
+//   perm     [rows]             row of each processing position
+//   items    [max_items]        work list, stripe-major
+//   ctr      [2]                item count, queue head
+struct SortArgs {
+    uint32_t *hist, *qstart, *slot, *key, *perm;
+    unsigned long long *tmp;
+    Item *items;
+    uint32_t *ctr;
+    int64_t max_items;
+    int32_t stripe_rows;        // iv rows per stripe
+    int32_t nstripe;
+    int32_t ushift, nuk;        // local key = (iv % stripe_rows) * nuk + (iu >> ushift)
+    int32_t sorted;             // 0: identity order
+    int32_t rows_per_item;
+};
+
+// Everything one mixed or FP64 launch class needs on the device.
 struct RunArgs {
     const SrcDev *srcs;
     int32_t nsrc;
+    int32_t cw;                 // channels per chunk (32 * NS) of this class
     const ChanF *chf;
     const ChanD *chd;
     RowRec *recs;
     const int64_t *row_off;     // [nsrc+1] cumulative rows
-    const int64_t *item_off;    // [nsrc+1] cumulative work items
-    int64_t nrows_total, nitems_total;
+    int64_t nrows_total;
     CubeGeom g;
     void *cube;                 // float4 (mixed) or double[4] (FP64) per entry
     uint32_t *count;
     DevStats *stats;
     int32_t *err;
+    SortArgs so;
 };
 
 // Kernel launchers (vista_kernels.cu).  Return a cudaError_t.
-cudaError_t launch_prepass(const RunArgs &a, const LaunchCfg &c, cudaStream_t st);
-// npol_vt = (vis_type << 8) | npol: every window of one launch shares both.
-cudaError_t launch_mixed(const RunArgs &a, const LaunchCfg &c, int npol_vt, cudaStream_t st);
+// Row ordering, records and work list of one mixed class (several kernels).
+cudaError_t launch_prepare(const RunArgs &a, cudaStream_t st);
+// Persistent stacking kernel of one mixed class; key = (vis_type << 16) |
+// (chans_per_lane << 8) | npol, shared by every window of the class.
+cudaError_t launch_mixed(const RunArgs &a, int key, int warps_per_cta, cudaStream_t st);
 cudaError_t launch_fp64(const RunArgs &a, cudaStream_t st);
 cudaError_t launch_unpack(const void *cube, const uint32_t *count, int fp64, int64_t n,
                           void *sum_wv, void *sum_w, void *sum_wvv, uint32_t *cnt_out,
                           int out_f64, cudaStream_t st);
-cudaError_t launch_debug(const RunArgs &a, const LaunchCfg &c, int src, int fp64, double *ph,
-                         int32_t *cells, cudaStream_t st);
+cudaError_t launch_debug(const RunArgs &a, int ns, int src, int fp64, double *ph, int32_t *cells,
+                         cudaStream_t st);
 
 }  // namespace vista

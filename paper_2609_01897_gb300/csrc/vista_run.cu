@@ -1,0 +1,386 @@
+// vista_run(): host planning and launch orchestration of one stacking pass.
+//
+//   1. the rest lattice (Sec. 3.1), fixed at the first run
+//   2. per window: FP64 channel tables (Eqs. 3-4, the uv scale s_k), the
+//      range of channels that reach the cube, the chunk width
+//   3. launch classes: windows sharing one kernel instantiation
+//   4. host-memory windows: only the channels that reach the cube are
+//      copied (2-D copies), into handle-owned device buffers
+//   5. per mixed class: row ordering + records + work list, then the
+//      persistent stacking kernel; FP64 precision: the plain kernel
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
+#include "planner.h"
+#include "vista_handle.h"
+
+using namespace vista;
+
+namespace {
+
+struct Plan {
+    int32_t k_lo = 0, k_hi = 0;
+    int32_t key_ch = 0;       // in-cube channel with the largest |frequency|
+    bool linear = true;
+    double step = 0.0;
+    std::vector<ChanF> chf;
+    std::vector<ChanD> chd;
+};
+
+int plan_source(vista_stack *h, const SrcHost &s, double gu, double gv, Plan &pl)
+{
+    const int32_t n = s.d.nchan;
+    std::vector<int32_t> j0((size_t)n), nb((size_t)n);
+    std::vector<double> w((size_t)n * VISTA_MAX_BINS);
+    const int rc = channel_bins(s.freqs.data(), n, s.d.z, h->f0, h->df, h->desc.nrest, h->desc.bin_mode,
+                                j0.data(), nb.data(), w.data());
+    if (rc == VISTA_E_RANGE)
+        return fail(h, VISTA_E_RANGE, "a channel touches more than %d rest bins (rest_df too small)",
+                    VISTA_MAX_BINS);
+    if (rc != VISTA_OK) return fail(h, rc, "channel planning failed");
+    int32_t lo = -1, hi = -1;
+    for (int32_t k = 0; k < n; ++k)
+        if (nb[(size_t)k] > 0) {
+            if (lo < 0) lo = k;
+            hi = k + 1;
+        }
+    if (lo < 0) lo = hi = 0;
+    pl.k_lo = lo;
+    pl.k_hi = hi;
+    pl.linear = linear_axis(s.freqs.data(), n, &pl.step);
+    pl.chf.resize((size_t)(hi - lo));
+    pl.chd.resize((size_t)(hi - lo));
+    double fbest = -1.0;
+    for (int32_t k = lo; k < hi; ++k) {
+        ChanD &d = pl.chd[(size_t)(k - lo)];
+        ChanF &f = pl.chf[(size_t)(k - lo)];
+        d.su = s.freqs[(size_t)k] * gu;
+        d.sv = s.freqs[(size_t)k] * gv;
+        d.nu = s.freqs[(size_t)k];
+        d.j0 = j0[(size_t)k];
+        d.nb = nb[(size_t)k];
+        f.su = (float)d.su;
+        f.sv = (float)d.sv;
+        f.j0 = d.j0;
+        f.nb = d.nb;
+        for (int b = 0; b < VISTA_MAX_BINS; ++b) {
+            d.w[b] = w[(size_t)k * VISTA_MAX_BINS + b];
+            f.w[b] = (float)d.w[b];
+        }
+        if (std::fabs(d.nu) > fbest) {
+            fbest = std::fabs(d.nu);
+            pl.key_ch = k;
+        }
+    }
+    return VISTA_OK;
+}
+
+template <typename T>
+cudaError_t upload(DevBuf &b, const std::vector<T> &v, cudaStream_t st)
+{
+    const size_t bytes = v.size() * sizeof(T);
+    cudaError_t e = b.ensure(bytes > 0 ? bytes : 16);
+    if (e != cudaSuccess || bytes == 0) return e;
+    return cudaMemcpyAsync(b.p, v.data(), bytes, cudaMemcpyHostToDevice, st);
+}
+
+// Smallest channels-per-lane (1, 2, 4; at most cap) whose chunk holds nin
+// channels; windows wider than 32*cap use several chunks.
+int choose_ns(int nin, int cap)
+{
+    for (int ns = 1; ns <= cap; ns <<= 1)
+        if (32 * ns >= nin) return ns;
+    return cap;
+}
+
+inline size_t al256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+// Layout of the shared ordering buffer for one class.
+struct SortLayout {
+    size_t hist, qstart, slot, key, perm, tmp, items, ctr, total;
+};
+
+SortLayout sort_layout(int64_t rows, int64_t nbuckets, int64_t max_items)
+{
+    SortLayout L{};
+    size_t o = 0;
+    L.hist = o;
+    o += al256(4 * (size_t)nbuckets);
+    L.qstart = o;
+    o += al256(4 * (size_t)nbuckets);
+    L.slot = o;
+    o += al256(4 * (size_t)rows);
+    L.key = o;
+    o += al256(4 * (size_t)rows);
+    L.perm = o;
+    o += al256(4 * (size_t)rows);
+    L.tmp = o;
+    o += al256(8 * (size_t)rows);
+    L.items = o;
+    o += al256(sizeof(Item) * (size_t)max_items);
+    L.ctr = o;
+    o += 256;
+    L.total = o;
+    return L;
+}
+
+}  // namespace
+
+extern "C" int vista_run(vista_stack *h)
+{
+    if (!handle_live(h)) return fail(nullptr, VISTA_E_STATE, "unknown or closed handle");
+    if (h->pending.empty()) return fail(h, VISTA_E_STATE, "vista_run with no queued source");
+    const vista_cube_desc &c = h->desc;
+    const bool fp64 = c.precision == VISTA_PREC_FP64;
+    cudaError_t e;
+
+    // 1. the rest lattice (fixed at the first run)
+    double f0 = h->f0, df = h->df;
+    if (!h->lattice_fixed) {
+        double best = 0.0;
+        for (const SrcHost &s : h->pending) {
+            if (s.d.nchan < 2)
+                return fail(h, VISTA_E_ARG, "the automatic rest lattice needs >= 2 channels per window");
+            const double wdt = widest_rest_channel(s.freqs.data(), s.d.nchan, s.d.z);
+            if (wdt > best) best = wdt;
+        }
+        if (!(best > 0.0)) return fail(h, VISTA_E_ARG, "automatic rest lattice: zero channel width");
+        df = best;
+        f0 = lattice_f0(c.central_freq, c.nrest, best);
+    }
+    const double saved_f0 = h->f0, saved_df = h->df;
+    h->f0 = f0;
+    h->df = df;
+
+    // 2. channel tables
+    const double gu = 1.0 / (C_LIGHT * c.du), gv = 1.0 / (C_LIGHT * c.dv);
+    const int nsrc = (int)h->pending.size();
+    std::vector<Plan> plans((size_t)nsrc);
+    for (int i = 0; i < nsrc; ++i) {
+        const int rc = plan_source(h, h->pending[(size_t)i], gu, gv, plans[(size_t)i]);
+        if (rc != VISTA_OK) {
+            h->f0 = saved_f0;
+            h->df = saved_df;
+            return rc;
+        }
+    }
+    h->lattice_fixed = true;
+
+    // 3. launch classes (windows with no row or no channel in the cube are skipped)
+    const LaunchCfg cfg = h->cfg;
+    std::vector<ClassRun> classes;
+    std::vector<int> ns_of((size_t)nsrc, 1);
+    for (int i = 0; i < nsrc; ++i) {
+        const SrcHost &s = h->pending[(size_t)i];
+        const Plan &pl = plans[(size_t)i];
+        if (s.d.nrow == 0 || pl.k_hi <= pl.k_lo) continue;
+        const int ns = fp64 ? 1 : choose_ns(pl.k_hi - pl.k_lo, cfg.chans_per_lane);
+        ns_of[(size_t)i] = ns;
+        const int key = fp64 ? 0 : ((s.d.vis_type << 16) | (ns << 8) | s.d.npol);
+        int ci = -1;
+        for (size_t j = 0; j < classes.size(); ++j)
+            if (classes[j].key == key) ci = (int)j;
+        if (ci < 0) {
+            classes.emplace_back();
+            classes.back().key = key;
+            classes.back().ns = ns;
+            ci = (int)classes.size() - 1;
+        }
+        classes[(size_t)ci].members.push_back(i);
+    }
+    std::vector<ChanF> chf;
+    std::vector<ChanD> chd;
+    std::vector<int32_t> chan_off((size_t)nsrc);
+    for (int i = 0; i < nsrc; ++i) {
+        chan_off[(size_t)i] = (int32_t)chf.size();
+        chf.insert(chf.end(), plans[(size_t)i].chf.begin(), plans[(size_t)i].chf.end());
+        chd.insert(chd.end(), plans[(size_t)i].chd.begin(), plans[(size_t)i].chd.end());
+    }
+    if (chf.size() > (size_t)0x7fffffff) return fail(h, VISTA_E_RANGE, "too many channels in one run");
+
+    // 4. host-memory windows: staging layout (in-cube channels only)
+    size_t stage_bytes = 0;
+    for (const ClassRun &cr : classes)
+        for (int i : cr.members) {
+            const SrcHost &s = h->pending[(size_t)i];
+            if (s.d.mem != VISTA_MEM_HOST) continue;
+            const size_t nr = (size_t)s.d.nrow, nin = (size_t)(plans[(size_t)i].k_hi - plans[(size_t)i].k_lo);
+            const size_t nvv = nr * nin * (size_t)s.d.npol;
+            stage_bytes += al256(nr * 24) + al256(nvv * vis_elem_bytes(s.d.vis_type)) +
+                           al256(nr * 4 * (size_t)s.d.npol) + (s.d.flags ? al256(nvv) : 0);
+        }
+    if (stage_bytes) {
+        e = h->b_stage.ensure(stage_bytes);
+        if (e != cudaSuccess) return cuda_fail(h, e, "staging allocation");
+    }
+
+    std::vector<SrcDev> sdev;
+    std::vector<int64_t> offs;
+    std::vector<size_t> cls_src0(classes.size()), cls_off0(classes.size());
+    std::vector<SortLayout> layouts(classes.size());
+    size_t sort_bytes = 0;
+    int64_t rec_total = 0;
+    size_t stage_pos = 0;
+    const int span_copy = stage_bytes ? span_begin(h, 2) : -1;
+    for (size_t ci = 0; ci < classes.size(); ++ci) {
+        ClassRun &cr = classes[ci];
+        const int cw = 32 * cr.ns;
+        cls_src0[ci] = sdev.size();
+        cls_off0[ci] = offs.size();
+        const size_t m = cr.members.size();
+        std::vector<int64_t> roff(m + 1, 0);
+        int64_t max_items = 0;
+        for (size_t t = 0; t < m; ++t) {
+            const int i = cr.members[t];
+            const SrcHost &s = h->pending[(size_t)i];
+            const Plan &pl = plans[(size_t)i];
+            const int32_t nin = pl.k_hi - pl.k_lo;
+            SrcDev d{};
+            d.uvw = s.d.uvw;
+            d.vis = s.d.vis;
+            d.wts = s.d.weights;
+            d.flags = s.d.flags;
+            d.vstride = s.d.nchan;
+            d.kbase = 0;
+            if (s.d.mem == VISTA_MEM_HOST) {
+                const size_t nr = (size_t)s.d.nrow, P = (size_t)s.d.npol;
+                const size_t esz = vis_elem_bytes(s.d.vis_type);
+                const size_t nvv = nr * (size_t)nin * P;
+                char *base = (char *)h->b_stage.p;
+                char *p_uvw = base + stage_pos;
+                stage_pos += al256(nr * 24);
+                char *p_vis = base + stage_pos;
+                stage_pos += al256(nvv * esz);
+                char *p_w = base + stage_pos;
+                stage_pos += al256(nr * 4 * P);
+                char *p_f = nullptr;
+                if (s.d.flags) {
+                    p_f = base + stage_pos;
+                    stage_pos += al256(nvv);
+                }
+                const size_t row_in = (size_t)s.d.nchan * P, row_out = (size_t)nin * P;
+                e = cudaMemcpyAsync(p_uvw, s.d.uvw, nr * 24, cudaMemcpyHostToDevice, h->stream);
+                if (e == cudaSuccess)
+                    e = cudaMemcpy2DAsync(p_vis, row_out * esz, (const char *)s.d.vis + (size_t)pl.k_lo * P * esz,
+                                          row_in * esz, row_out * esz, nr, cudaMemcpyHostToDevice, h->stream);
+                if (e == cudaSuccess)
+                    e = cudaMemcpyAsync(p_w, s.d.weights, nr * 4 * P, cudaMemcpyHostToDevice, h->stream);
+                if (e == cudaSuccess && p_f)
+                    e = cudaMemcpy2DAsync(p_f, row_out, s.d.flags + (size_t)pl.k_lo * P, row_in, row_out, nr,
+                                          cudaMemcpyHostToDevice, h->stream);
+                if (e != cudaSuccess) return cuda_fail(h, e, "host-to-device copy of a host-memory window");
+                d.uvw = (const double *)p_uvw;
+                d.vis = p_vis;
+                d.wts = (const float *)p_w;
+                d.flags = (const uint8_t *)p_f;
+                d.vstride = nin;
+                d.kbase = pl.k_lo;
+            }
+            d.nrow = s.d.nrow;
+            d.nchan = s.d.nchan;
+            d.npol = s.d.npol;
+            d.vis_type = s.d.vis_type;
+            d.vis_scale = (s.d.vis_type == VISTA_VIS_F16X2 || s.d.vis_type == VISTA_VIS_BF16X2) ? s.d.vis_scale : 1.0f;
+            d.l = s.d.l;
+            d.m = s.d.m;
+            d.n1 = std::sqrt(1.0 - s.d.l * s.d.l - s.d.m * s.d.m) - 1.0;
+            d.step_c = pl.step / C_LIGHT;
+            d.k_lo = pl.k_lo;
+            d.k_hi = pl.k_hi;
+            d.chan_off = chan_off[(size_t)i];
+            d.linear = pl.linear ? 1 : 0;
+            for (int p = 0; p < 4; ++p) d.plane[p] = p < s.d.npol ? s.pol_map[(size_t)p] : -1;
+            d.nchunk = (nin + cw - 1) / cw;
+            d.key_su = (float)(s.freqs[(size_t)pl.key_ch] * gu);
+            d.key_sv = (float)(s.freqs[(size_t)pl.key_ch] * gv);
+            d.rec_off = rec_total;
+            if (!fp64) rec_total += (int64_t)d.nchunk * d.nrow;
+            roff[t + 1] = roff[t] + d.nrow;
+            max_items += (int64_t)d.nchunk * ((d.nrow + cfg.rows_per_item - 1) / cfg.rows_per_item + h->nstripe);
+            sdev.push_back(d);
+        }
+        offs.insert(offs.end(), roff.begin(), roff.end());
+        cr.args.nsrc = (int32_t)m;
+        cr.args.cw = cw;
+        cr.args.nrows_total = roff[m];
+        const int nst = cfg.sort_rows ? h->nstripe : 1;
+        layouts[ci] = sort_layout(roff[m], (int64_t)m * nst, max_items);
+        cr.args.so.max_items = max_items;
+        sort_bytes = std::max(sort_bytes, layouts[ci].total);
+    }
+    span_end(h, span_copy);
+
+    // uploads and buffers
+    if ((e = upload(h->b_srcs, sdev, h->stream)) != cudaSuccess) return cuda_fail(h, e, "source table upload");
+    if ((e = upload(h->b_chf, chf, h->stream)) != cudaSuccess) return cuda_fail(h, e, "channel table upload");
+    if ((e = upload(h->b_chd, chd, h->stream)) != cudaSuccess) return cuda_fail(h, e, "channel table upload");
+    if ((e = upload(h->b_off, offs, h->stream)) != cudaSuccess) return cuda_fail(h, e, "offset table upload");
+    if (!fp64) {
+        if ((e = h->b_recs.ensure((size_t)(rec_total > 0 ? rec_total : 1) * sizeof(RowRec))) != cudaSuccess)
+            return cuda_fail(h, e, "row record allocation");
+        if ((e = h->b_sort.ensure(sort_bytes > 0 ? sort_bytes : 256)) != cudaSuccess)
+            return cuda_fail(h, e, "ordering buffer allocation");
+    }
+
+    // 5. launches
+    const CubeGeom g{c.nu, c.nv, c.nrest, c.npol, gu, gv, c.hermitian_fold, 0};
+    for (size_t ci = 0; ci < classes.size(); ++ci) {
+        ClassRun &cr = classes[ci];
+        RunArgs &a = cr.args;
+        a.srcs = (const SrcDev *)h->b_srcs.p + cls_src0[ci];
+        a.chf = (const ChanF *)h->b_chf.p;
+        a.chd = (const ChanD *)h->b_chd.p;
+        a.recs = (RowRec *)h->b_recs.p;
+        a.row_off = (const int64_t *)h->b_off.p + cls_off0[ci];
+        a.g = g;
+        a.cube = h->cube;
+        a.count = h->count;
+        a.stats = h->stats;
+        a.err = h->err;
+        if (fp64) {
+            const int sp = span_begin(h, 1);
+            e = launch_fp64(a, h->stream);
+            span_end(h, sp);
+            if (h->timing) h->tacc.launches += 1;
+        } else {
+            SortArgs &so = a.so;
+            const SortLayout &L = layouts[ci];
+            char *b = (char *)h->b_sort.p;
+            so.hist = (uint32_t *)(b + L.hist);
+            so.qstart = (uint32_t *)(b + L.qstart);
+            so.slot = (uint32_t *)(b + L.slot);
+            so.key = (uint32_t *)(b + L.key);
+            so.perm = (uint32_t *)(b + L.perm);
+            so.tmp = (unsigned long long *)(b + L.tmp);
+            so.items = (Item *)(b + L.items);
+            so.ctr = (uint32_t *)(b + L.ctr);
+            so.sorted = cfg.sort_rows;
+            so.stripe_rows = cfg.sort_rows ? h->stripe_rows : c.nv;
+            so.nstripe = cfg.sort_rows ? h->nstripe : 1;
+            so.ushift = h->ushift;
+            so.nuk = h->nuk;
+            so.rows_per_item = cfg.rows_per_item;
+            int sp = span_begin(h, 0);
+            e = launch_prepare(a, h->stream);
+            span_end(h, sp);
+            if (h->timing) h->tacc.launches += 5;
+            if (e == cudaSuccess) {
+                sp = span_begin(h, 1);
+                e = launch_mixed(a, cr.key, cfg.warps_per_cta, h->stream);
+                span_end(h, sp);
+                if (h->timing) h->tacc.launches += 1;
+            }
+        }
+        if (e != cudaSuccess) return cuda_fail(h, e, "kernel launch");
+    }
+    if (h->timing) h->tacc.runs += 1;
+    bool any_host = false;
+    for (const SrcHost &s : h->pending) any_host |= s.d.mem == VISTA_MEM_HOST;
+    if (any_host && (e = cudaStreamSynchronize(h->stream)) != cudaSuccess)
+        return cuda_fail(h, e, "stream synchronize after host-memory copies");
+    h->classes = std::move(classes);
+    h->last = std::move(h->pending);
+    h->pending.clear();
+    return VISTA_OK;
+}

@@ -162,7 +162,7 @@ def _cube_du(spws: List[SourceSpw], n: int) -> float:
 
 def _make_sources(cid: int, n_src: int, *, n_ant, radius, n_int, t_int, lat, dec, spw_fn,
                   npol, flux_fn, fwhm, line_rest, line_peak_fn, line_fwhm, sigma,
-                  flag_fn, offset_max, z_lo, z_hi, device, src_ids=None) -> List[SourceSpw]:
+                  flag_fn, offset_max, z_lo, z_hi, device, src_ids=None, meta_only=False) -> List[SourceSpw]:
     out = []
     ids = range(n_src) if src_ids is None else src_ids
     for s in ids:
@@ -176,6 +176,11 @@ def _make_sources(cid: int, n_src: int, *, n_ant, radius, n_int, t_int, lat, dec
         line_peak = float(line_peak_fn(rng, flux))
         flag_frac = float(flag_fn(rng))
         uvw_np = uvw_tracks(enu, lat, dec, n_int, t_int, ha0)
+        if meta_only:   # geometry and channel axes only (host uvw, no visibilities)
+            for spw in spw_fn(rng, z):
+                out.append(SourceSpw(torch.as_tensor(uvw_np), spw.freqs(), None, None, None, l0, m0, z,
+                                     source=s))
+            continue
         uvw = torch.as_tensor(uvw_np, dtype=torch.float64, device=device)
         gen = _gen(1000 * cid + s, device)
         for spw in spw_fn(rng, z):
@@ -210,7 +215,7 @@ def tiny(device="cpu") -> Workload:
     return Workload("tiny", n, n, 128, 2, du, du, nu_line, spws)
 
 
-def alma_compact(device="cpu", n_sources=64, src_ids=None) -> Workload:
+def alma_compact(device="cpu", n_sources=64, src_ids=None, meta_only=False, du=None) -> Workload:
     """64 sources, 43 antennas within 1 km, 120 integrations, two 120-channel
     windows at 100 and 112 GHz, 2 pols, point + line sources with flux
     lognormal(mean 0.05 mJy, sigma_ln 1), 0.5 mJy noise, z in [2, 3], cube
@@ -228,9 +233,9 @@ def alma_compact(device="cpu", n_sources=64, src_ids=None) -> Workload:
         npol=2, flux_fn=lambda rng: rng.lognormal(mu_ln, sig_ln), fwhm=0.0, line_rest=nu_line,
         line_peak_fn=lambda rng, f: 2.0 * f, line_fwhm=300.0, sigma=5e-4,
         flag_fn=lambda rng: 0.01, offset_max=10 * ARCSEC, z_lo=2.0, z_hi=3.0, device=device,
-        src_ids=src_ids)
+        src_ids=src_ids, meta_only=meta_only)
     n = 256
-    du = _cube_du(spws, n)
+    du = _cube_du(spws, n) if du is None else du
     return Workload("alma_compact", n, n, 512, 2, du, du, nu_line, spws)
 
 

@@ -230,8 +230,11 @@ class Stack:
     def zero(self):
         _check("vista_zero_cube", lib().vista_zero_cube(self.h), self.h)
 
-    def set_tuning(self, rows_per_item=0, chans_per_lane=0, warps_per_cta=0, sort_rows=0):
-        t = Tuning(rows_per_item, chans_per_lane, warps_per_cta, sort_rows)
+    def set_tuning(self, rows_per_item=0, chans_per_lane=0, warps_per_cta=0, sort_rows=None):
+        """0 (or None for sort_rows) keeps the current value."""
+        if sort_rows is None:
+            sort_rows = self.tuning()["sort_rows"]
+        t = Tuning(rows_per_item, chans_per_lane, warps_per_cta, int(sort_rows))
         _check("vista_set_tuning", lib().vista_set_tuning(self.h, C.byref(t)), self.h)
 
     def tuning(self):

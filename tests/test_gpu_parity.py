@@ -54,7 +54,7 @@ def test_ragged_cases(V, seed, prec):
     p = V.PREC_MIXED if prec == "mixed" else V.PREC_FP64
     mode = seed % 2
     fold = seed % 3 == 1
-    tuning = [None, dict(rows_per_item=7, chans_per_lane=1), dict(rows_per_item=3, chans_per_lane=2),
+    tuning = [None, dict(rows_per_item=7, chans_per_lane=1), dict(rows_per_item=3, chans_per_lane=2, sort_rows=0),
               dict(rows_per_item=1000, chans_per_lane=4, warps_per_cta=8)][seed % 4]
     g = H.run_gpu(wl, precision=p, bin_mode=mode, fold=fold, tuning=tuning)
     o = H.run_oracle(wl, bin_mode=mode, fold=fold)
