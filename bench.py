@@ -271,7 +271,7 @@ def run_ours(args):
     value = n_vis * ws / (ms_max * 1e-3)
     stack_ms = tm["stack_ms"] / max(1, args.steps)
     peak, peak_kind = measured_peaks()
-    achieved = alg / (stack_ms * 1e-3) / 1e9
+    achieved = alg / (stack_ms * 1e-3) / 1e9 if stack_ms > 0 else 0.0
     launches = int(tm["launches"])
     st.close()
 

@@ -129,10 +129,13 @@ typedef struct {
     uint64_t n_flagged;     /* of those, flagged */
     uint64_t n_dropped_uv;  /* unflagged, outside the uv grid */
     uint64_t n_stacked;     /* unflagged, accumulated into the cube */
+    uint64_t n_reductions;  /* reductions into the cube issued by the mixed path (one per
+                               cube entry update after on-chip pre-reduction); 0 for FP64 */
 } vista_stats;
 
 /* Launch shape of the mixed-precision path (0 fields = library default).
- *   rows_per_item   rows one warp walks through per work item.
+ *   rows_per_item   rows one warp walks through per work item (1..256; their
+ *                   FP64 records are staged in shared memory).
  *   chans_per_lane  channels per lane in one item (item = 32 x this many
  *                   channels); also the FP32 phasor recurrence length
  *                   between FP64-derived seeds.

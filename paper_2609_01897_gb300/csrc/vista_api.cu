@@ -335,6 +335,7 @@ extern "C" int vista_get_stats(vista_stack *h, vista_stats *out)
     out->n_flagged = s.n_flagged;
     out->n_dropped_uv = s.n_dropped_uv;
     out->n_stacked = s.n_stacked;
+    out->n_reductions = s.n_reductions;
     return VISTA_OK;
 }
 
@@ -354,8 +355,8 @@ extern "C" int vista_set_tuning(vista_stack *h, const vista_tuning *t)
     if (!t) return fail(h, VISTA_E_ARG, "null tuning");
     LaunchCfg c = h->cfg;
     if (t->rows_per_item) {
-        if (t->rows_per_item < 1 || t->rows_per_item > (1 << 20))
-            return fail(h, VISTA_E_ARG, "rows_per_item must be in [1, 2^20]");
+        if (t->rows_per_item < 1 || t->rows_per_item > 256)
+            return fail(h, VISTA_E_ARG, "rows_per_item must be in [1, 256]");
         c.rows_per_item = t->rows_per_item;
     }
     if (t->chans_per_lane) {

@@ -24,6 +24,56 @@ __device__ __forceinline__ int find_owner(const int64_t *__restrict__ off, int n
     return lo;
 }
 
+// ---- TMA bulk copies into shared memory, completed on an mbarrier ----
+
+__device__ __forceinline__ uint32_t smem_addr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_init_fence() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
+
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
+                 : "memory");
+}
+
+// 1-D bulk copy global -> shared (16-byte aligned addresses, size a multiple of 16).
+__device__ __forceinline__ void tma_load_1d(void *dst, const void *src, uint32_t bytes, uint64_t *bar)
+{
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_addr(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_addr(bar))
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Bounded wait: gives up after ~2^24 polls (seconds), records the failure in
+// the error word and returns false; never traps and never spins forever.
+constexpr int32_t ERR_WAIT_TIMEOUT = 1;
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity, int32_t *err)
+{
+    for (uint32_t i = 0; i < (1u << 24); ++i)
+        if (mbar_try_wait(bar, parity)) return true;
+    atomicExch(err, ERR_WAIT_TIMEOUT);
+    return false;
+}
+
 __device__ __forceinline__ float2 cmul(float2 a, float2 b)
 {
     return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
@@ -92,14 +142,14 @@ struct VisLoad<P, VISTA_VIS_C64> {
         (void)scale;
         const float2 *p = reinterpret_cast<const float2 *>(base) + idx * P;
         if constexpr (P == 1) {
-            v[0] = __ldg(p);
+            v[0] = __ldcs(p);
         } else if constexpr (P == 2) {
-            float4 q = __ldg(reinterpret_cast<const float4 *>(p));
+            float4 q = __ldcs(reinterpret_cast<const float4 *>(p));
             v[0] = make_float2(q.x, q.y);
             v[1] = make_float2(q.z, q.w);
         } else {
-            float4 q0 = __ldg(reinterpret_cast<const float4 *>(p));
-            float4 q1 = __ldg(reinterpret_cast<const float4 *>(p) + 1);
+            float4 q0 = __ldcs(reinterpret_cast<const float4 *>(p));
+            float4 q1 = __ldcs(reinterpret_cast<const float4 *>(p) + 1);
             v[0] = make_float2(q0.x, q0.y);
             v[1] = make_float2(q0.z, q0.w);
             v[2] = make_float2(q1.x, q1.y);
@@ -116,7 +166,7 @@ struct VisLoad<P, VISTA_VIS_C128> {
         const double2 *p = reinterpret_cast<const double2 *>(base) + idx * P;
 #pragma unroll
         for (int i = 0; i < P; ++i) {
-            double2 q = __ldg(p + i);
+            double2 q = __ldcs(p + i);
             v[i] = make_float2((float)q.x, (float)q.y);
         }
     }
@@ -135,13 +185,13 @@ struct VisLoad<P, VISTA_VIS_F16X2> {
     {
         const uint32_t *p = reinterpret_cast<const uint32_t *>(base) + idx * P;
         if constexpr (P == 1) {
-            v[0] = cvt(__ldg(p), scale);
+            v[0] = cvt(__ldcs(p), scale);
         } else if constexpr (P == 2) {
-            uint2 q = __ldg(reinterpret_cast<const uint2 *>(p));
+            uint2 q = __ldcs(reinterpret_cast<const uint2 *>(p));
             v[0] = cvt(q.x, scale);
             v[1] = cvt(q.y, scale);
         } else {
-            uint4 q = __ldg(reinterpret_cast<const uint4 *>(p));
+            uint4 q = __ldcs(reinterpret_cast<const uint4 *>(p));
             v[0] = cvt(q.x, scale);
             v[1] = cvt(q.y, scale);
             v[2] = cvt(q.z, scale);
@@ -162,13 +212,13 @@ struct VisLoad<P, VISTA_VIS_BF16X2> {
     {
         const uint32_t *p = reinterpret_cast<const uint32_t *>(base) + idx * P;
         if constexpr (P == 1) {
-            v[0] = cvt(__ldg(p), scale);
+            v[0] = cvt(__ldcs(p), scale);
         } else if constexpr (P == 2) {
-            uint2 q = __ldg(reinterpret_cast<const uint2 *>(p));
+            uint2 q = __ldcs(reinterpret_cast<const uint2 *>(p));
             v[0] = cvt(q.x, scale);
             v[1] = cvt(q.y, scale);
         } else {
-            uint4 q = __ldg(reinterpret_cast<const uint4 *>(p));
+            uint4 q = __ldcs(reinterpret_cast<const uint4 *>(p));
             v[0] = cvt(q.x, scale);
             v[1] = cvt(q.y, scale);
             v[2] = cvt(q.z, scale);
@@ -182,9 +232,9 @@ __device__ __forceinline__ uint32_t load_flags(const uint8_t *flags, int64_t idx
 {
     if (!flags) return 0u;
     const uint8_t *p = flags + idx * P;
-    if constexpr (P == 1) return (uint32_t)__ldg(p);
-    else if constexpr (P == 2) return (uint32_t)__ldg(reinterpret_cast<const uint16_t *>(p));
-    else return __ldg(reinterpret_cast<const uint32_t *>(p));
+    if constexpr (P == 1) return (uint32_t)__ldcs(p);
+    else if constexpr (P == 2) return (uint32_t)__ldcs(reinterpret_cast<const uint16_t *>(p));
+    else return __ldcs(reinterpret_cast<const uint32_t *>(p));
 }
 
 }  // namespace vista

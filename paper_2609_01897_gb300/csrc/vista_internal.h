@@ -82,7 +82,7 @@ struct __align__(16) Item {
 
 // Counters (device), see vista_stats.
 struct DevStats {
-    unsigned long long n_vis, n_flagged, n_dropped_uv, n_stacked;
+    unsigned long long n_vis, n_flagged, n_dropped_uv, n_stacked, n_reductions;
 };
 
 struct LaunchCfg {

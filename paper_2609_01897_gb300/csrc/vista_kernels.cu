@@ -1,13 +1,6 @@
 // libvista stacking kernels for sm_103a.
 //
-//   stack_mixed   persistent: warps pop work items (one window, a run of rows
-//                 in uv-cell order, 32 x NS channels, lane = channel) from a
-//                 queue; per (row, channel): FP32 phasor from the FP64 seed
-//                 and the recurrence stride, guarded-FP32 uv cell (bit-exact
-//                 against the FP64 rule), rest bins from the FP64 channel
-//                 table (Eqs. 3-4); per-lane running sums over consecutive
-//                 rows that share a cell, flushed as vector reductions into
-//                 the FP32 cube
+//   (the mixed-precision stacking kernel is in vista_stack.cu)
 //   stack_fp64    the plain form: thread per (window, row), FP64 phasor
 //                 recurrence, FP64 cells, FP64 atomics into an FP64 cube
 //   debug_mixed   the mixed path's own phasor and cell code, exported
@@ -15,178 +8,6 @@
 #include "vista_device.cuh"
 
 namespace vista {
-
-// ------------------------------------------------------------ stack_mixed
-
-template <int P, int VT, int NS>
-__global__ void __launch_bounds__(256) stack_mixed(RunArgs a)
-{
-    const int lane = threadIdx.x & 31;
-    const uint32_t nitems = a.so.ctr[0];
-    const int npol_c = a.g.npol, nrest = a.g.nrest;
-    float4 *cube4 = reinterpret_cast<float4 *>(a.cube);
-    uint32_t n_vis = 0, n_flag = 0, n_duv = 0, n_stk = 0;
-
-    for (;;) {
-        uint32_t it = 0;
-        if (lane == 0) it = atomicAdd(&a.so.ctr[1], 1u);
-        it = __shfl_sync(0xffffffffu, it, 0);
-        if (it >= nitems) break;
-        const Item item = a.so.items[it];
-        const SrcDev &S = a.srcs[item.w];
-        const int64_t nrow = S.nrow;
-        const int c0 = S.k_lo + item.chunk * 32 * NS;
-        const bool linear = S.linear != 0;
-        const void *vis = S.vis;
-        const uint8_t *flags = S.flags;
-        const float vscale = S.vis_scale;
-        const int64_t vstride = S.vstride, kbase = S.kbase;
-
-        int plane[P];
-#pragma unroll
-        for (int p = 0; p < P; ++p) plane[p] = S.plane[p];
-        // two pols whose counts sit in one aligned 8-byte word: one u64 reduction
-        const bool pack2 = (P == 2) && plane[0] >= 0 && plane[1] == plane[0] + 1 && !(plane[0] & 1) &&
-                           !(npol_c & 1);
-
-        float su[NS], sv[NS], wb[NS][4];
-        int j0[NS], nb[NS], kk[NS];
-#pragma unroll
-        for (int q = 0; q < NS; ++q) {
-            kk[q] = c0 + q * 32 + lane;
-            nb[q] = 0;
-            j0[q] = 0;
-            su[q] = sv[q] = 0.f;
-#pragma unroll
-            for (int b = 0; b < 4; ++b) wb[q][b] = 0.f;
-            if (kk[q] < S.k_hi) {
-                const ChanF cf = a.chf[S.chan_off + (kk[q] - S.k_lo)];
-                su[q] = cf.su;
-                sv[q] = cf.sv;
-                j0[q] = cf.j0;
-                nb[q] = cf.nb;
-#pragma unroll
-                for (int b = 0; b < 4; ++b) wb[q][b] = cf.w[b];
-            }
-        }
-
-        int cell[NS];
-        float4 acc[NS][P];
-        uint32_t cnt[NS][P];
-#pragma unroll
-        for (int q = 0; q < NS; ++q) {
-            cell[q] = -1;
-#pragma unroll
-            for (int p = 0; p < P; ++p) {
-                acc[q][p] = make_float4(0.f, 0.f, 0.f, 0.f);
-                cnt[q][p] = 0;
-            }
-        }
-
-        auto flush = [&](int q) {
-            if (cell[q] < 0) return;
-            const size_t base = ((size_t)cell[q] * nrest + j0[q]) * npol_c;
-#pragma unroll
-            for (int b = 0; b < 4; ++b) {
-                if (b < nb[q]) {
-                    const float ww = wb[q][b];
-                    const size_t e = base + (size_t)b * npol_c;
-#pragma unroll
-                    for (int p = 0; p < P; ++p) {
-                        if (cnt[q][p] == 0) continue;
-                        atomicAdd(cube4 + e + plane[p], make_float4(ww * acc[q][p].x, ww * acc[q][p].y,
-                                                                    ww * acc[q][p].z, ww * acc[q][p].w));
-                        if (!pack2) atomicAdd(a.count + e + plane[p], cnt[q][p]);
-                    }
-                    if (pack2 && (cnt[q][0] | cnt[q][P - 1]))
-                        atomicAdd(reinterpret_cast<unsigned long long *>(a.count + e + plane[0]),
-                                  (unsigned long long)cnt[q][0] | ((unsigned long long)cnt[q][P - 1] << 32));
-                }
-            }
-#pragma unroll
-            for (int p = 0; p < P; ++p) {
-                acc[q][p] = make_float4(0.f, 0.f, 0.f, 0.f);
-                cnt[q][p] = 0;
-            }
-        };
-
-        const RowRec *recs = a.recs + S.rec_off + (int64_t)item.chunk * nrow;
-        for (int64_t i = item.q0; i < item.q1; ++i) {
-            const RowRec rec = recs[i];
-            const int64_t row = (int64_t)(rec.rowf & 0x7fffffffu);
-            const bool fold = (rec.rowf >> 31) != 0;
-            float2 ph = make_float2(1.f, 0.f);
-            double tau = 0.0;
-            if (linear)
-                ph = lane_seed(rec, lane);
-            else
-                tau = __hiloint2double(__float_as_int(rec.dhi), __float_as_int(rec.dlo));
-            const float2 stp = make_float2(rec.sre, rec.sim);
-#pragma unroll
-            for (int q = 0; q < NS; ++q) {
-                if (!linear && kk[q] < S.k_hi) {
-                    double t = tau * (a.chd[S.chan_off + (kk[q] - S.k_lo)].nu * (1.0 / C_LIGHT));
-                    t -= floor(t);
-                    ph = turns_to_phasor((float)t);
-                }
-                if (nb[q] > 0) {
-                    const ChanD *cd = a.chd + S.chan_off + (kk[q] - S.k_lo);
-                    const int iu = axis_cell(rec.u, su[q], S.uvw + 3 * row, fold, &cd->su, a.g.nu);
-                    const int iv = axis_cell(rec.v, sv[q], S.uvw + 3 * row + 1, fold, &cd->sv, a.g.nv);
-                    const int cid = (iu >= 0 && iv >= 0) ? iv * a.g.nu + iu : -1;
-                    const int64_t vidx = row * vstride + (kk[q] - kbase);
-                    float2 V[P];
-                    VisLoad<P, VT>::load(vis, vidx, vscale, V);
-                    const uint32_t fl = load_flags<P>(flags, vidx);
-                    if (cid != cell[q]) {
-                        flush(q);
-                        cell[q] = cid;
-                    }
-#pragma unroll
-                    for (int p = 0; p < P; ++p) {
-                        if (plane[p] < 0) continue;
-                        const bool f = ((fl >> (8 * p)) & 0xffu) != 0;
-                        ++n_vis;
-                        if (f) {
-                            ++n_flag;
-                            continue;
-                        }
-                        if (cid < 0) {
-                            ++n_duv;
-                            continue;
-                        }
-                        ++n_stk;
-                        float2 vs = cmul(V[p], ph);
-                        if (fold) vs.y = -vs.y;
-                        const float W = rec.W[p];
-                        const float a2 = V[p].x * V[p].x + V[p].y * V[p].y;
-                        acc[q][p].x += W * vs.x;
-                        acc[q][p].y += W * vs.y;
-                        acc[q][p].z += W;
-                        acc[q][p].w += W * a2;
-                        cnt[q][p] += 1;
-                    }
-                }
-                if (linear) ph = cmul(ph, stp);
-            }
-        }
-#pragma unroll
-        for (int q = 0; q < NS; ++q) flush(q);
-    }
-
-    // counters: warp sum, one atomic per counter per warp
-    unsigned long long c4[4] = {n_vis, n_flag, n_duv, n_stk};
-#pragma unroll
-    for (int k = 0; k < 4; ++k)
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) c4[k] += __shfl_xor_sync(0xffffffffu, c4[k], o);
-    if (lane == 0) {
-        if (c4[0]) atomicAdd(&a.stats->n_vis, c4[0]);
-        if (c4[1]) atomicAdd(&a.stats->n_flagged, c4[1]);
-        if (c4[2]) atomicAdd(&a.stats->n_dropped_uv, c4[2]);
-        if (c4[3]) atomicAdd(&a.stats->n_stacked, c4[3]);
-    }
-}
 
 // Debug export: the same seed/recurrence/cell code as stack_mixed, writing
 // the phasor and the cell of every (row, channel) of one window.
@@ -404,63 +225,6 @@ __global__ void unpack_kernel(const void *cube, const uint32_t *count, int fp64,
 }
 
 // --------------------------------------------------------------- launchers
-
-static int sm_count()
-{
-    static int n = 0;
-    if (n == 0) {
-        int dev = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
-        if (n <= 0) n = 1;
-    }
-    return n;
-}
-
-template <typename K>
-static cudaError_t launch_persistent(K kern, const RunArgs &a, int wpc, cudaStream_t st)
-{
-    int per_sm = 0;
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, wpc * 32, 0);
-    if (e != cudaSuccess) return e;
-    if (per_sm < 1) per_sm = 1;
-    kern<<<per_sm * sm_count(), wpc * 32, 0, st>>>(a);
-    return cudaGetLastError();
-}
-
-template <int P, int VT>
-static cudaError_t launch_mixed_p(const RunArgs &a, int ns, int wpc, cudaStream_t st)
-{
-    switch (ns) {
-    case 1: return launch_persistent(stack_mixed<P, VT, 1>, a, wpc, st);
-    case 2: return launch_persistent(stack_mixed<P, VT, 2>, a, wpc, st);
-    case 4: return launch_persistent(stack_mixed<P, VT, 4>, a, wpc, st);
-    default: return cudaErrorInvalidValue;
-    }
-}
-
-template <int VT>
-static cudaError_t launch_mixed_vt(const RunArgs &a, int ns, int npol, int wpc, cudaStream_t st)
-{
-    switch (npol) {
-    case 1: return launch_mixed_p<1, VT>(a, ns, wpc, st);
-    case 2: return launch_mixed_p<2, VT>(a, ns, wpc, st);
-    case 4: return launch_mixed_p<4, VT>(a, ns, wpc, st);
-    default: return cudaErrorInvalidValue;
-    }
-}
-
-cudaError_t launch_mixed(const RunArgs &a, int key, int wpc, cudaStream_t st)
-{
-    const int npol = key & 0xff, ns = (key >> 8) & 0xff, vt = key >> 16;
-    switch (vt) {
-    case VISTA_VIS_C64: return launch_mixed_vt<VISTA_VIS_C64>(a, ns, npol, wpc, st);
-    case VISTA_VIS_C128: return launch_mixed_vt<VISTA_VIS_C128>(a, ns, npol, wpc, st);
-    case VISTA_VIS_F16X2: return launch_mixed_vt<VISTA_VIS_F16X2>(a, ns, npol, wpc, st);
-    case VISTA_VIS_BF16X2: return launch_mixed_vt<VISTA_VIS_BF16X2>(a, ns, npol, wpc, st);
-    default: return cudaErrorInvalidValue;
-    }
-}
 
 cudaError_t launch_fp64(const RunArgs &a, cudaStream_t st)
 {

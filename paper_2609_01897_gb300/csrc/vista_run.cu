@@ -175,7 +175,9 @@ extern "C" int vista_run(vista_stack *h)
         const SrcHost &s = h->pending[(size_t)i];
         const Plan &pl = plans[(size_t)i];
         if (s.d.nrow == 0 || pl.k_hi <= pl.k_lo) continue;
-        const int ns = fp64 ? 1 : choose_ns(pl.k_hi - pl.k_lo, cfg.chans_per_lane);
+        // four pols x four channels per lane does not fit the register budget
+        const int cap = s.d.npol == 4 ? std::min(2, (int)cfg.chans_per_lane) : (int)cfg.chans_per_lane;
+        const int ns = fp64 ? 1 : choose_ns(pl.k_hi - pl.k_lo, cap);
         ns_of[(size_t)i] = ns;
         const int key = fp64 ? 0 : ((s.d.vis_type << 16) | (ns << 8) | s.d.npol);
         int ci = -1;

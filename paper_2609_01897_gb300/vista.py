@@ -43,7 +43,8 @@ class SourceDesc(C.Structure):
 
 class Stats(C.Structure):
     _fields_ = [("n_vis", C.c_uint64), ("n_flagged", C.c_uint64),
-                ("n_dropped_uv", C.c_uint64), ("n_stacked", C.c_uint64)]
+                ("n_dropped_uv", C.c_uint64), ("n_stacked", C.c_uint64),
+                ("n_reductions", C.c_uint64)]
 
     def as_dict(self):
         return {k: int(getattr(self, k)) for k, _ in self._fields_}

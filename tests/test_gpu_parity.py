@@ -55,7 +55,7 @@ def test_ragged_cases(V, seed, prec):
     mode = seed % 2
     fold = seed % 3 == 1
     tuning = [None, dict(rows_per_item=7, chans_per_lane=1), dict(rows_per_item=3, chans_per_lane=2, sort_rows=0),
-              dict(rows_per_item=1000, chans_per_lane=4, warps_per_cta=8)][seed % 4]
+              dict(rows_per_item=256, chans_per_lane=4, warps_per_cta=8)][seed % 4]
     g = H.run_gpu(wl, precision=p, bin_mode=mode, fold=fold, tuning=tuning)
     o = H.run_oracle(wl, bin_mode=mode, fold=fold)
     H.compare(g, o, H.TOL_MIXED if prec == "mixed" else H.TOL_FP64, what="random %d" % seed)
@@ -193,7 +193,8 @@ def test_host_memory_mode_matches_device(V, tiny):
     np.testing.assert_array_equal(a["count"], b["count"])
     o = H.run_oracle(tiny)
     H.compare(b, o, H.TOL_MIXED, what="host-mem")
-    assert a["stats"] == b["stats"]
+    for k in ("n_vis", "n_flagged", "n_dropped_uv", "n_stacked"):
+        assert a["stats"][k] == b["stats"][k]
 
 
 def test_runs_are_additive(V, tiny):
