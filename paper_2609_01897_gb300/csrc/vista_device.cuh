@@ -103,20 +103,23 @@ __device__ __forceinline__ float2 lane_seed(const RowRec &rec, int lane)
 // [0, n).  Decided in FP32 when fl32(c32 * s32) is at least 2^-21 |x| away
 // from an integer (the FP32 product differs from the FP64 one by at most
 // 3 * 2^-24 |x|), else by the exact FP64 product.
+// The exact FP64 product, out of line so that the compiler cannot hoist it
+// (and its FP64 work) out of the rarely taken branch below.
+static __device__ __noinline__ float exact_floor_product(const double *coord64, bool neg, const double *s64)
+{
+    double c = *coord64;
+    if (neg) c = -c;
+    return (float)floor(__dmul_rn(c, *s64));
+}
+
 __device__ __forceinline__ int axis_cell(float c32, float s32, const double *coord64, bool neg,
                                          const double *s64, int n)
 {
     float x = __fmul_rn(c32, s32);
     float d = __fmaf_rn(fabsf(x), 4.76837158203125e-07f, 1e-30f);
     float fa = floorf(__fsub_rn(x, d)), fb = floorf(__fadd_rn(x, d));
-    float fx;
-    if (fa == fb) {
-        fx = fa;
-    } else {
-        double c = *coord64;
-        if (neg) c = -c;
-        fx = (float)floor(__dmul_rn(c, *s64));
-    }
+    float fx = fa;
+    if (__builtin_expect(fa != fb, 0)) fx = exact_floor_product(coord64, neg, s64);
     float h = (float)(n >> 1);
     if (!(fx >= -h && fx < h)) return -1;
     return (int)fx + (n >> 1);

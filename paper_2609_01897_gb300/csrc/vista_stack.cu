@@ -91,24 +91,24 @@ __global__ void __launch_bounds__(256) stack_mixed(RunArgs a)
         const bool pack2 = (P == 2) && plane[0] >= 0 && plane[1] == plane[0] + 1 && !(plane[0] & 1) &&
                            !(npol_c & 1);
 
-        float su[NS], sv[NS], wb[NS][4];
-        int j0[NS], nb[NS], kk[NS];
+        // per channel slot: fl32(s_k), first bin | bin count << 28, first two weights
+        // (a third or fourth bin, possible only for user lattices narrower than
+        // a channel, reads its weight from the table)
+        float su[NS], sv[NS], wb[NS][2];
+        int jn[NS];
 #pragma unroll
         for (int q = 0; q < NS; ++q) {
-            kk[q] = c0 + q * 32 + lane;
-            nb[q] = 0;
-            j0[q] = 0;
+            const int k = c0 + q * 32 + lane;
+            jn[q] = 0;
             su[q] = sv[q] = 0.f;
-#pragma unroll
-            for (int b = 0; b < 4; ++b) wb[q][b] = 0.f;
-            if (kk[q] < S.k_hi) {
-                const ChanF cf = a.chf[S.chan_off + (kk[q] - S.k_lo)];
+            wb[q][0] = wb[q][1] = 0.f;
+            if (k < S.k_hi) {
+                const ChanF cf = a.chf[S.chan_off + (k - S.k_lo)];
                 su[q] = cf.su;
                 sv[q] = cf.sv;
-                j0[q] = cf.j0;
-                nb[q] = cf.nb;
-#pragma unroll
-                for (int b = 0; b < 4; ++b) wb[q][b] = cf.w[b];
+                jn[q] = cf.j0 | (cf.nb << 28);
+                wb[q][0] = cf.w[0];
+                wb[q][1] = cf.w[1];
             }
         }
         int cell[NS];
@@ -125,11 +125,13 @@ __global__ void __launch_bounds__(256) stack_mixed(RunArgs a)
         }
         auto flush = [&](int q) {
             if (cell[q] < 0) return;
-            const size_t base = ((size_t)cell[q] * nrest + j0[q]) * npol_c;
+            const int nbq = jn[q] >> 28;
+            const size_t base = ((size_t)cell[q] * nrest + (jn[q] & 0x0fffffff)) * npol_c;
 #pragma unroll
             for (int b = 0; b < 4; ++b) {
-                if (b < nb[q]) {
-                    const float ww = wb[q][b];
+                if (b < nbq) {
+                    const float ww =
+                        b < 2 ? wb[q][b] : a.chf[S.chan_off + (c0 + q * 32 + lane - S.k_lo)].w[b];
                     const size_t e = base + (size_t)b * npol_c;
 #pragma unroll
                     for (int p = 0; p < P; ++p) {
@@ -165,8 +167,8 @@ __global__ void __launch_bounds__(256) stack_mixed(RunArgs a)
 #pragma unroll
             for (int q = 0; q < NS; ++q) {
                 RF[d][q] = 0;
-                if (nb[q] > 0) {
-                    const int64_t vidx = row * vstride + (kk[q] - kbase);
+                if (jn[q] >> 28) {
+                    const int64_t vidx = row * vstride + (c0 + q * 32 + lane - kbase);
                     VisLoad<P, VT>::load(vis, vidx, vscale, RV[d][q]);
                     RF[d][q] = load_flags<P>(flags, vidx);
                 }
@@ -208,13 +210,14 @@ __global__ void __launch_bounds__(256) stack_mixed(RunArgs a)
                 for (int p = 0; p < P; ++p) W[p] = rec.W[p];
 #pragma unroll
                 for (int q = 0; q < NS; ++q) {
-                    if (!linear && kk[q] < S.k_hi) {
-                        double t = tau * (a.chd[S.chan_off + (kk[q] - S.k_lo)].nu * (1.0 / C_LIGHT));
+                    const int k = c0 + q * 32 + lane;
+                    if (!linear && k < S.k_hi) {
+                        double t = tau * (a.chd[S.chan_off + (k - S.k_lo)].nu * (1.0 / C_LIGHT));
                         t -= floor(t);
                         ph = turns_to_phasor((float)t);
                     }
-                    if (nb[q] > 0) {
-                        const ChanD *cd = a.chd + S.chan_off + (kk[q] - S.k_lo);
+                    if (jn[q] >> 28) {
+                        const ChanD *cd = a.chd + S.chan_off + (k - S.k_lo);
                         const int iu = axis_cell(ru, su[q], S.uvw + 3 * row, fold, &cd->su, a.g.nu);
                         const int iv = axis_cell(rv, sv[q], S.uvw + 3 * row + 1, fold, &cd->sv, a.g.nv);
                         const int cid = (iu >= 0 && iv >= 0) ? iv * a.g.nu + iu : -1;
