@@ -320,6 +320,7 @@ extern "C" int vista_zero_cube(vista_stack *h)
     if (e == cudaSuccess) e = cudaMemsetAsync(h->count, 0, (size_t)h->nentries * 4, h->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(h->stats, 0, sizeof(DevStats), h->stream);
     if (e != cudaSuccess) return cuda_fail(h, e, "cube zeroing");
+    h->host_nvis = 0;
     return VISTA_OK;
 }
 
@@ -331,10 +332,12 @@ extern "C" int vista_get_stats(vista_stack *h, vista_stats *out)
     cudaError_t e = cudaStreamSynchronize(h->stream);
     if (e == cudaSuccess) e = cudaMemcpy(&s, h->stats, sizeof s, cudaMemcpyDeviceToHost);
     if (e != cudaSuccess) return cuda_fail(h, e, "stats readback");
-    out->n_vis = s.n_vis;
+    // the kernels count flagged and off-grid visibilities; how many they read
+    // is known from the channel tables
+    out->n_vis = h->host_nvis;
     out->n_flagged = s.n_flagged;
     out->n_dropped_uv = s.n_dropped_uv;
-    out->n_stacked = s.n_stacked;
+    out->n_stacked = h->host_nvis - s.n_flagged - s.n_dropped_uv;
     out->n_reductions = s.n_reductions;
     return VISTA_OK;
 }

@@ -68,10 +68,11 @@ struct vista_stack {
     uint32_t *count = nullptr;
     int64_t nentries = 0;
     vista::DevStats *stats = nullptr;
+    uint64_t host_nvis = 0;   // visibilities read, counted from the channel tables at each run
     int32_t *err = nullptr;
     vista::DevBuf b_srcs, b_chf, b_chd, b_recs, b_off, b_stage, b_unpack, b_sort;
     std::vector<vista::ClassRun> classes;
-    vista::LaunchCfg cfg{64, 4, 4, 1};
+    vista::LaunchCfg cfg{64, 1, 4, 1};
     // stripe geometry of the row ordering (depends on the cube only)
     int32_t stripe_rows = 1, nstripe = 1, ushift = 0, nuk = 1;
     std::string msg;

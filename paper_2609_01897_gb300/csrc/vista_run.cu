@@ -223,6 +223,7 @@ extern "C" int vista_run(vista_stack *h)
     std::vector<SortLayout> layouts(classes.size());
     size_t sort_bytes = 0;
     int64_t rec_total = 0;
+    uint64_t nvis_run = 0;
     size_t stage_pos = 0;
     const int span_copy = stage_bytes ? span_begin(h, 2) : -1;
     for (size_t ci = 0; ci < classes.size(); ++ci) {
@@ -298,6 +299,12 @@ extern "C" int vista_run(vista_stack *h)
             d.key_sv = (float)(s.freqs[(size_t)pl.key_ch] * gv);
             d.rec_off = rec_total;
             if (!fp64) rec_total += (int64_t)d.nchunk * d.nrow;
+            {
+                int64_t nread = 0, npm = 0;
+                for (const ChanF &f : pl.chf) nread += f.nb > 0;
+                for (int p = 0; p < s.d.npol; ++p) npm += s.pol_map[(size_t)p] >= 0;
+                nvis_run += (uint64_t)(d.nrow * nread * npm);
+            }
             roff[t + 1] = roff[t] + d.nrow;
             max_items += (int64_t)d.nchunk * ((d.nrow + cfg.rows_per_item - 1) / cfg.rows_per_item + h->nstripe);
             sdev.push_back(d);
@@ -377,6 +384,7 @@ extern "C" int vista_run(vista_stack *h)
         if (e != cudaSuccess) return cuda_fail(h, e, "kernel launch");
     }
     if (h->timing) h->tacc.runs += 1;
+    h->host_nvis += nvis_run;
     bool any_host = false;
     for (const SrcHost &s : h->pending) any_host |= s.d.mem == VISTA_MEM_HOST;
     if (any_host && (e = cudaStreamSynchronize(h->stream)) != cudaSuccess)

@@ -19,6 +19,40 @@ namespace vista {
 
 constexpr int RB_MAX = 256;   // largest item (rows) the shared-memory buffers hold
 
+// Running sums of one channel slot for one uv cell, written to the cube.
+// Out of line: after row ordering it runs once per several rows, and keeping
+// it out of the unrolled row loop keeps the loop small.
+template <int P>
+static __device__ __noinline__ uint32_t flush_slot(const RunArgs &a, int cell, int jn, float w0, float w1,
+                                                   const float *wtab, const float4 *acc, const uint32_t *cnt,
+                                                   const int *plane, bool pack2)
+{
+    const int npol_c = a.g.npol;
+    const int nbq = jn >> 28;
+    float4 *cube4 = reinterpret_cast<float4 *>(a.cube);
+    const size_t base = ((size_t)cell * a.g.nrest + (jn & 0x0fffffff)) * npol_c;
+    uint32_t nred = 0;
+    for (int b = 0; b < nbq; ++b) {
+        const float ww = b == 0 ? w0 : b == 1 ? w1 : wtab[b];
+        const size_t e = base + (size_t)b * npol_c;
+        for (int p = 0; p < P; ++p) {
+            if (cnt[p] == 0) continue;
+            atomicAdd(cube4 + e + plane[p], make_float4(ww * acc[p].x, ww * acc[p].y, ww * acc[p].z, ww * acc[p].w));
+            ++nred;
+            if (!pack2) {
+                atomicAdd(a.count + e + plane[p], cnt[p]);
+                ++nred;
+            }
+        }
+        if (pack2 && (cnt[0] | cnt[P - 1])) {
+            atomicAdd(reinterpret_cast<unsigned long long *>(a.count + e + plane[0]),
+                      (unsigned long long)cnt[0] | ((unsigned long long)cnt[P - 1] << 32));
+            ++nred;
+        }
+    }
+    return nred;
+}
+
 template <int P, int VT, int NS, int D>
 __global__ void __launch_bounds__(256) stack_mixed(RunArgs a)
 {
@@ -35,9 +69,7 @@ __global__ void __launch_bounds__(256) stack_mixed(RunArgs a)
     __syncwarp();
 
     const uint32_t nitems = a.so.ctr[0];
-    const int npol_c = a.g.npol, nrest = a.g.nrest;
-    float4 *cube4 = reinterpret_cast<float4 *>(a.cube);
-    uint32_t n_vis = 0, n_flag = 0, n_duv = 0, n_stk = 0, n_red = 0;
+    uint32_t n_flag = 0, n_duv = 0, n_red = 0;
     uint32_t phase = 0;   // bit s: parity of the next completion of slot s
 
     auto pop = [&]() -> uint32_t {
@@ -48,8 +80,8 @@ __global__ void __launch_bounds__(256) stack_mixed(RunArgs a)
     // Fetch the records of item `it` into slot s (lane 0 issues the copy).
     auto issue = [&](int s, uint32_t it) -> Item {
         const Item item = a.so.items[it];
-        const SrcDev &S = a.srcs[item.w];
         if (lane == 0) {
+            const SrcDev &S = a.srcs[item.w];
             const RowRec *src = a.recs + S.rec_off + (int64_t)item.chunk * S.nrow + item.q0;
             const uint32_t bytes = (uint32_t)(item.q1 - item.q0) * (uint32_t)sizeof(RowRec);
             fence_proxy_async();
@@ -77,23 +109,17 @@ __global__ void __launch_bounds__(256) stack_mixed(RunArgs a)
         phase ^= 1u << cs;
         const RowRec *rb = rbuf + (size_t)cs * RB;
 
-        // ---- process one item ----
+        // ---- one item ----
         const SrcDev &S = a.srcs[item.w];
         const int c0 = S.k_lo + item.chunk * 32 * NS;
         const bool linear = S.linear != 0;
-        const void *vis = S.vis;
-        const uint8_t *flags = S.flags;
-        const float vscale = S.vis_scale;
-        const int64_t vstride = S.vstride, kbase = S.kbase;
         int plane[P];
 #pragma unroll
         for (int p = 0; p < P; ++p) plane[p] = S.plane[p];
         const bool pack2 = (P == 2) && plane[0] >= 0 && plane[1] == plane[0] + 1 && !(plane[0] & 1) &&
-                           !(npol_c & 1);
+                           !(a.g.npol & 1);
 
         // per channel slot: fl32(s_k), first bin | bin count << 28, first two weights
-        // (a third or fourth bin, possible only for user lattices narrower than
-        // a channel, reads its weight from the table)
         float su[NS], sv[NS], wb[NS][2];
         int jn[NS];
 #pragma unroll
@@ -124,32 +150,12 @@ __global__ void __launch_bounds__(256) stack_mixed(RunArgs a)
             }
         }
         auto flush = [&](int q) {
-            if (cell[q] < 0) return;
-            const int nbq = jn[q] >> 28;
-            const size_t base = ((size_t)cell[q] * nrest + (jn[q] & 0x0fffffff)) * npol_c;
+            uint32_t any = 0;
 #pragma unroll
-            for (int b = 0; b < 4; ++b) {
-                if (b < nbq) {
-                    const float ww =
-                        b < 2 ? wb[q][b] : a.chf[S.chan_off + (c0 + q * 32 + lane - S.k_lo)].w[b];
-                    const size_t e = base + (size_t)b * npol_c;
-#pragma unroll
-                    for (int p = 0; p < P; ++p) {
-                        if (cnt[q][p] == 0) continue;
-                        atomicAdd(cube4 + e + plane[p], make_float4(ww * acc[q][p].x, ww * acc[q][p].y,
-                                                                    ww * acc[q][p].z, ww * acc[q][p].w));
-                        ++n_red;
-                        if (!pack2) {
-                            atomicAdd(a.count + e + plane[p], cnt[q][p]);
-                            ++n_red;
-                        }
-                    }
-                    if (pack2 && (cnt[q][0] | cnt[q][P - 1])) {
-                        atomicAdd(reinterpret_cast<unsigned long long *>(a.count + e + plane[0]),
-                                  (unsigned long long)cnt[q][0] | ((unsigned long long)cnt[q][P - 1] << 32));
-                        ++n_red;
-                    }
-                }
+            for (int p = 0; p < P; ++p) any |= cnt[q][p];
+            if (cell[q] >= 0 && any) {
+                const float *wtab = a.chf[S.chan_off + (c0 + q * 32 + lane - S.k_lo)].w;
+                n_red += flush_slot<P>(a, cell[q], jn[q], wb[q][0], wb[q][1], wtab, acc[q], cnt[q], plane, pack2);
             }
 #pragma unroll
             for (int p = 0; p < P; ++p) {
@@ -168,9 +174,9 @@ __global__ void __launch_bounds__(256) stack_mixed(RunArgs a)
             for (int q = 0; q < NS; ++q) {
                 RF[d][q] = 0;
                 if (jn[q] >> 28) {
-                    const int64_t vidx = row * vstride + (c0 + q * 32 + lane - kbase);
-                    VisLoad<P, VT>::load(vis, vidx, vscale, RV[d][q]);
-                    RF[d][q] = load_flags<P>(flags, vidx);
+                    const int64_t vidx = row * S.vstride + (c0 + q * 32 + lane - S.kbase);
+                    VisLoad<P, VT>::load(S.vis, vidx, S.vis_scale, RV[d][q]);
+                    RF[d][q] = load_flags<P>(S.flags, vidx);
                 }
             }
         };
@@ -197,29 +203,21 @@ __global__ void __launch_bounds__(256) stack_mixed(RunArgs a)
                 const uint32_t rowf = rec.rowf;
                 const int64_t row = (int64_t)(rowf & 0x7fffffffu);
                 const bool fold = (rowf >> 31) != 0;
-                const float ru = rec.u, rv = rec.v;
                 float2 ph = make_float2(1.f, 0.f);
-                double tau = 0.0;
-                if (linear)
-                    ph = lane_seed(rec, lane);
-                else
-                    tau = __hiloint2double(__float_as_int(rec.dhi), __float_as_int(rec.dlo));
-                const float2 stp = make_float2(rec.sre, rec.sim);
-                float W[P];
-#pragma unroll
-                for (int p = 0; p < P; ++p) W[p] = rec.W[p];
+                if (linear) ph = lane_seed(rec, lane);
 #pragma unroll
                 for (int q = 0; q < NS; ++q) {
                     const int k = c0 + q * 32 + lane;
                     if (!linear && k < S.k_hi) {
+                        const double tau = __hiloint2double(__float_as_int(rec.dhi), __float_as_int(rec.dlo));
                         double t = tau * (a.chd[S.chan_off + (k - S.k_lo)].nu * (1.0 / C_LIGHT));
                         t -= floor(t);
                         ph = turns_to_phasor((float)t);
                     }
                     if (jn[q] >> 28) {
                         const ChanD *cd = a.chd + S.chan_off + (k - S.k_lo);
-                        const int iu = axis_cell(ru, su[q], S.uvw + 3 * row, fold, &cd->su, a.g.nu);
-                        const int iv = axis_cell(rv, sv[q], S.uvw + 3 * row + 1, fold, &cd->sv, a.g.nv);
+                        const int iu = axis_cell(rec.u, su[q], S.uvw + 3 * row, fold, &cd->su, a.g.nu);
+                        const int iv = axis_cell(rec.v, sv[q], S.uvw + 3 * row + 1, fold, &cd->sv, a.g.nv);
                         const int cid = (iu >= 0 && iv >= 0) ? iv * a.g.nu + iu : -1;
                         if (cid != cell[q]) {
                             flush(q);
@@ -228,9 +226,7 @@ __global__ void __launch_bounds__(256) stack_mixed(RunArgs a)
 #pragma unroll
                         for (int p = 0; p < P; ++p) {
                             if (plane[p] < 0) continue;
-                            const bool f = ((F[q] >> (8 * p)) & 0xffu) != 0;
-                            ++n_vis;
-                            if (f) {
+                            if ((F[q] >> (8 * p)) & 0xffu) {
                                 ++n_flag;
                                 continue;
                             }
@@ -238,18 +234,18 @@ __global__ void __launch_bounds__(256) stack_mixed(RunArgs a)
                                 ++n_duv;
                                 continue;
                             }
-                            ++n_stk;
                             float2 vs = cmul(V[q][p], ph);
                             if (fold) vs.y = -vs.y;
+                            const float W = rec.W[p];
                             const float a2 = V[q][p].x * V[q][p].x + V[q][p].y * V[q][p].y;
-                            acc[q][p].x += W[p] * vs.x;
-                            acc[q][p].y += W[p] * vs.y;
-                            acc[q][p].z += W[p];
-                            acc[q][p].w += W[p] * a2;
+                            acc[q][p].x += W * vs.x;
+                            acc[q][p].y += W * vs.y;
+                            acc[q][p].z += W;
+                            acc[q][p].w += W * a2;
                             cnt[q][p] += 1;
                         }
                     }
-                    if (linear) ph = cmul(ph, stp);
+                    if (linear && q + 1 < NS) ph = cmul(ph, make_float2(rec.sre, rec.sim));
                 }
             }
         }
@@ -258,18 +254,17 @@ __global__ void __launch_bounds__(256) stack_mixed(RunArgs a)
         s ^= 1;
     }
 
-    // counters: warp sum, one atomic per counter per warp
-    unsigned long long c5[5] = {n_vis, n_flag, n_duv, n_stk, n_red};
+    // counters (the visibilities read are counted on the host from the
+    // channel tables): warp sum, one atomic per counter per warp
+    unsigned long long c3[3] = {n_flag, n_duv, n_red};
 #pragma unroll
-    for (int k = 0; k < 5; ++k)
+    for (int k = 0; k < 3; ++k)
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) c5[k] += __shfl_xor_sync(0xffffffffu, c5[k], o);
+        for (int o = 16; o > 0; o >>= 1) c3[k] += __shfl_xor_sync(0xffffffffu, c3[k], o);
     if (lane == 0) {
-        if (c5[0]) atomicAdd(&a.stats->n_vis, c5[0]);
-        if (c5[1]) atomicAdd(&a.stats->n_flagged, c5[1]);
-        if (c5[2]) atomicAdd(&a.stats->n_dropped_uv, c5[2]);
-        if (c5[3]) atomicAdd(&a.stats->n_stacked, c5[3]);
-        if (c5[4]) atomicAdd(&a.stats->n_reductions, c5[4]);
+        if (c3[0]) atomicAdd(&a.stats->n_flagged, c3[0]);
+        if (c3[1]) atomicAdd(&a.stats->n_dropped_uv, c3[1]);
+        if (c3[2]) atomicAdd(&a.stats->n_reductions, c3[2]);
     }
 }
 
@@ -308,7 +303,7 @@ static cudaError_t launch_mixed_p(const RunArgs &a, int ns, int wpc, cudaStream_
 {
     switch (ns) {
     // prefetch depth D: as many rows ahead as the register budget allows
-    case 1: return launch_persistent(stack_mixed<P, VT, 1, (P <= 2 ? 4 : 2)>, a, wpc, st);
+    case 1: return launch_persistent(stack_mixed<P, VT, 1, 2>, a, wpc, st);
     case 2: return launch_persistent(stack_mixed<P, VT, 2, (P <= 2 ? 2 : 1)>, a, wpc, st);
     case 4: return launch_persistent(stack_mixed<P, VT, 4, 1>, a, wpc, st);
     default: return cudaErrorInvalidValue;
