@@ -141,9 +141,11 @@ typedef struct {
  *                   between FP64-derived seeds.
  *   warps_per_cta   warps per block of the stacking kernel.
  *   sort_rows       1: order rows by uv cell before stacking (fewer
- *                   global reductions), 0: stack in input order. */
+ *                   global reductions), 0: stack in input order.
+ *   prefetch_rows   visibility rows each warp keeps in flight (2, 4 or 8;
+ *                   used with one or two channels per lane and 1-2 pols). */
 typedef struct {
-    int32_t rows_per_item, chans_per_lane, warps_per_cta, sort_rows;
+    int32_t rows_per_item, chans_per_lane, warps_per_cta, sort_rows, prefetch_rows;
 } vista_tuning;
 
 /* Open a cube (zeroed) on the current CUDA device.  Allocates the cube.

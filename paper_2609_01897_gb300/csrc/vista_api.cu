@@ -374,6 +374,11 @@ extern "C" int vista_set_tuning(vista_stack *h, const vista_tuning *t)
     }
     if (t->sort_rows < 0 || t->sort_rows > 1) return fail(h, VISTA_E_ARG, "sort_rows must be 0 or 1");
     c.sort_rows = t->sort_rows;
+    if (t->prefetch_rows) {
+        if (t->prefetch_rows != 2 && t->prefetch_rows != 4 && t->prefetch_rows != 8)
+            return fail(h, VISTA_E_ARG, "prefetch_rows must be 2, 4 or 8");
+        c.prefetch_rows = t->prefetch_rows;
+    }
     h->cfg = c;
     return VISTA_OK;
 }
@@ -386,6 +391,7 @@ extern "C" int vista_get_tuning(vista_stack *h, vista_tuning *t)
     t->chans_per_lane = h->cfg.chans_per_lane;
     t->warps_per_cta = h->cfg.warps_per_cta;
     t->sort_rows = h->cfg.sort_rows;
+    t->prefetch_rows = h->cfg.prefetch_rows;
     return VISTA_OK;
 }
 

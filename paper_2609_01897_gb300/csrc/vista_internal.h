@@ -90,6 +90,7 @@ struct LaunchCfg {
     int32_t chans_per_lane;     // upper bound; each window uses the smallest that fits
     int32_t warps_per_cta;
     int32_t sort_rows;
+    int32_t prefetch_rows;      // visibility rows in flight per warp (2, 4, 8)
 };
 
 // Row ordering of one launch class (device buffers, see vista_kernels.cu).
@@ -137,7 +138,7 @@ struct RunArgs {
 cudaError_t launch_prepare(const RunArgs &a, cudaStream_t st);
 // Persistent stacking kernel of one mixed class; key = (vis_type << 16) |
 // (chans_per_lane << 8) | npol, shared by every window of the class.
-cudaError_t launch_mixed(const RunArgs &a, int key, int warps_per_cta, cudaStream_t st);
+cudaError_t launch_mixed(const RunArgs &a, int key, int warps_per_cta, int prefetch, cudaStream_t st);
 cudaError_t launch_fp64(const RunArgs &a, cudaStream_t st);
 cudaError_t launch_unpack(const void *cube, const uint32_t *count, int fp64, int64_t n,
                           void *sum_wv, void *sum_w, void *sum_wvv, uint32_t *cnt_out,

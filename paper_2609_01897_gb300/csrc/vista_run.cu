@@ -376,7 +376,7 @@ extern "C" int vista_run(vista_stack *h)
             if (h->timing) h->tacc.launches += 5;
             if (e == cudaSuccess) {
                 sp = span_begin(h, 1);
-                e = launch_mixed(a, cr.key, cfg.warps_per_cta, h->stream);
+                e = launch_mixed(a, cr.key, cfg.warps_per_cta, cfg.prefetch_rows, h->stream);
                 span_end(h, sp);
                 if (h->timing) h->tacc.launches += 1;
             }

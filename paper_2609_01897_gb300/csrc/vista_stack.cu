@@ -110,12 +110,34 @@ __global__ void __launch_bounds__(256) stack_mixed(RunArgs a)
         const RowRec *rb = rbuf + (size_t)cs * RB;
 
         // ---- one item ----
-        const SrcDev &S = a.srcs[item.w];
+        // window fields in registers (the cube reductions below could alias
+        // global memory, so references into the table would be re-read)
+        struct WinRegs {
+            const void *vis;
+            const uint8_t *flags;
+            const double *uvw;
+            int64_t vstride, kbase;
+            float vis_scale;
+            int32_t k_lo, k_hi, chan_off, linear;
+        } S;
+        {
+            const SrcDev &G = a.srcs[item.w];
+            S.vis = G.vis;
+            S.flags = G.flags;
+            S.uvw = G.uvw;
+            S.vstride = G.vstride;
+            S.kbase = G.kbase;
+            S.vis_scale = G.vis_scale;
+            S.k_lo = G.k_lo;
+            S.k_hi = G.k_hi;
+            S.chan_off = G.chan_off;
+            S.linear = G.linear;
+        }
         const int c0 = S.k_lo + item.chunk * 32 * NS;
         const bool linear = S.linear != 0;
         int plane[P];
 #pragma unroll
-        for (int p = 0; p < P; ++p) plane[p] = S.plane[p];
+        for (int p = 0; p < P; ++p) plane[p] = a.srcs[item.w].plane[p];
         const bool pack2 = (P == 2) && plane[0] >= 0 && plane[1] == plane[0] + 1 && !(plane[0] & 1) &&
                            !(a.g.npol & 1);
 
@@ -298,37 +320,49 @@ static cudaError_t launch_persistent(K kern, const RunArgs &a, int wpc, cudaStre
     return cudaGetLastError();
 }
 
+// Prefetch depth D (rows of visibilities in flight per warp): deeper rings
+// hide more HBM latency but cost registers; the common storage types get a
+// choice, the rest one depth per channels-per-lane.
 template <int P, int VT>
-static cudaError_t launch_mixed_p(const RunArgs &a, int ns, int wpc, cudaStream_t st)
+static cudaError_t launch_mixed_p(const RunArgs &a, int ns, int pf, int wpc, cudaStream_t st)
 {
+    constexpr bool choice = VT != VISTA_VIS_C128 && P <= 2;
     switch (ns) {
-    // prefetch depth D: as many rows ahead as the register budget allows
-    case 1: return launch_persistent(stack_mixed<P, VT, 1, 2>, a, wpc, st);
-    case 2: return launch_persistent(stack_mixed<P, VT, 2, (P <= 2 ? 2 : 1)>, a, wpc, st);
+    case 1:
+        if constexpr (choice) {
+            if (pf >= 8) return launch_persistent(stack_mixed<P, VT, 1, 8>, a, wpc, st);
+            if (pf >= 4) return launch_persistent(stack_mixed<P, VT, 1, 4>, a, wpc, st);
+        }
+        return launch_persistent(stack_mixed<P, VT, 1, 2>, a, wpc, st);
+    case 2:
+        if constexpr (choice) {
+            if (pf >= 4) return launch_persistent(stack_mixed<P, VT, 2, 4>, a, wpc, st);
+        }
+        return launch_persistent(stack_mixed<P, VT, 2, (P <= 2 ? 2 : 1)>, a, wpc, st);
     case 4: return launch_persistent(stack_mixed<P, VT, 4, 1>, a, wpc, st);
     default: return cudaErrorInvalidValue;
     }
 }
 
 template <int VT>
-static cudaError_t launch_mixed_vt(const RunArgs &a, int ns, int npol, int wpc, cudaStream_t st)
+static cudaError_t launch_mixed_vt(const RunArgs &a, int ns, int pf, int npol, int wpc, cudaStream_t st)
 {
     switch (npol) {
-    case 1: return launch_mixed_p<1, VT>(a, ns, wpc, st);
-    case 2: return launch_mixed_p<2, VT>(a, ns, wpc, st);
-    case 4: return launch_mixed_p<4, VT>(a, ns, wpc, st);
+    case 1: return launch_mixed_p<1, VT>(a, ns, pf, wpc, st);
+    case 2: return launch_mixed_p<2, VT>(a, ns, pf, wpc, st);
+    case 4: return launch_mixed_p<4, VT>(a, ns, pf, wpc, st);
     default: return cudaErrorInvalidValue;
     }
 }
 
-cudaError_t launch_mixed(const RunArgs &a, int key, int wpc, cudaStream_t st)
+cudaError_t launch_mixed(const RunArgs &a, int key, int wpc, int prefetch, cudaStream_t st)
 {
     const int npol = key & 0xff, ns = (key >> 8) & 0xff, vt = key >> 16;
     switch (vt) {
-    case VISTA_VIS_C64: return launch_mixed_vt<VISTA_VIS_C64>(a, ns, npol, wpc, st);
-    case VISTA_VIS_C128: return launch_mixed_vt<VISTA_VIS_C128>(a, ns, npol, wpc, st);
-    case VISTA_VIS_F16X2: return launch_mixed_vt<VISTA_VIS_F16X2>(a, ns, npol, wpc, st);
-    case VISTA_VIS_BF16X2: return launch_mixed_vt<VISTA_VIS_BF16X2>(a, ns, npol, wpc, st);
+    case VISTA_VIS_C64: return launch_mixed_vt<VISTA_VIS_C64>(a, ns, prefetch, npol, wpc, st);
+    case VISTA_VIS_C128: return launch_mixed_vt<VISTA_VIS_C128>(a, ns, prefetch, npol, wpc, st);
+    case VISTA_VIS_F16X2: return launch_mixed_vt<VISTA_VIS_F16X2>(a, ns, prefetch, npol, wpc, st);
+    case VISTA_VIS_BF16X2: return launch_mixed_vt<VISTA_VIS_BF16X2>(a, ns, prefetch, npol, wpc, st);
     default: return cudaErrorInvalidValue;
     }
 }

@@ -52,7 +52,7 @@ class Stats(C.Structure):
 
 class Tuning(C.Structure):
     _fields_ = [("rows_per_item", C.c_int32), ("chans_per_lane", C.c_int32),
-                ("warps_per_cta", C.c_int32), ("sort_rows", C.c_int32)]
+                ("warps_per_cta", C.c_int32), ("sort_rows", C.c_int32), ("prefetch_rows", C.c_int32)]
 
 
 class Timing(C.Structure):
@@ -231,11 +231,12 @@ class Stack:
     def zero(self):
         _check("vista_zero_cube", lib().vista_zero_cube(self.h), self.h)
 
-    def set_tuning(self, rows_per_item=0, chans_per_lane=0, warps_per_cta=0, sort_rows=None):
+    def set_tuning(self, rows_per_item=0, chans_per_lane=0, warps_per_cta=0, sort_rows=None,
+                   prefetch_rows=0):
         """0 (or None for sort_rows) keeps the current value."""
         if sort_rows is None:
             sort_rows = self.tuning()["sort_rows"]
-        t = Tuning(rows_per_item, chans_per_lane, warps_per_cta, int(sort_rows))
+        t = Tuning(rows_per_item, chans_per_lane, warps_per_cta, int(sort_rows), prefetch_rows)
         _check("vista_set_tuning", lib().vista_set_tuning(self.h, C.byref(t)), self.h)
 
     def tuning(self):
