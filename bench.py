@@ -268,6 +268,7 @@ def run_ours(args):
     clk = Clocks(local)
     ms, tm = timed_steps(st, wl, args.steps, args.warmup, ws)
     clocks = clk.stop()
+    red_per_vis = st.stats()["n_reductions"] / max(1, n_vis)
     ms_max = allmax(ws, ms)
     value = n_vis * ws / (ms_max * 1e-3)
     stack_ms = tm["stack_ms"] / max(1, args.steps)
@@ -312,6 +313,7 @@ def run_ours(args):
                          "algorithmic_bytes_per_launch": alg, "kernel_ms": stack_ms,
                          "peak_source": peak_kind},
             "prepass_ms": tm["prepass_ms"] / max(1, args.steps),
+            "cube_reductions_per_vis": red_per_vis,
             "fp64_gpu": fp64,
             "e2e": e2e,
             "cpu_baseline": cpu,

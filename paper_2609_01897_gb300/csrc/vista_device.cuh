@@ -79,14 +79,34 @@ __device__ __forceinline__ float2 cmul(float2 a, float2 b)
     return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
 }
 
-// exp(2 pi i t) for t in turns; t is first reduced to [-0.5, 0.5] (exact
-// for |t| < 2^22) so that sincospif sees its most accurate argument range.
+// exp(2 pi i t) for t in turns, for |t| < 2^21.
+//
+// Own evaluation (textbook quadrant reduction + Taylor series): x = 4t is
+// split into the nearest integer q (quadrant) and r in [-1/2, 1/2]
+// (exact: Sterbenz), theta = r pi/2 in [-pi/4, pi/4], then
+//   sin theta = theta (1 - theta^2/3! + theta^4/5! - theta^6/7! + theta^8/9!)
+//   cos theta = 1 - theta^2/2! + theta^4/4! - theta^6/6! + theta^8/8!
+// whose truncation errors on |theta| <= pi/4 are below 2e-9 and 3e-8, and
+// finally exp(i (q pi/2 + theta)) by rotating (cos, sin) q quarter turns.
+// The phase error is a few 1e-8 rad, far inside the 1e-5 rad budget.
 __device__ __forceinline__ float2 turns_to_phasor(float t)
 {
-    t = __fsub_rn(t, rintf(t));
-    float s, c;
-    sincospif(2.0f * t, &s, &c);
-    return make_float2(c, s);
+    const float x = 4.0f * t;                 // exact
+    const float q = rintf(x);
+    const float r = __fsub_rn(x, q);          // exact, |r| <= 1/2
+    const float th = r * 1.57079632679489662f;
+    const float t2 = th * th;
+    float s = __fmaf_rn(t2, 2.75573192e-06f, -1.98412698e-04f);   // 1/9!, -1/7!
+    s = __fmaf_rn(t2, s, 8.33333333e-03f);                          // 1/5!
+    s = __fmaf_rn(t2, s, -1.66666667e-01f);                         // -1/3!
+    s = __fmaf_rn(t2 * th, s, th);
+    float c = __fmaf_rn(t2, 2.48015873e-05f, -1.38888889e-03f);    // 1/8!, -1/6!
+    c = __fmaf_rn(t2, c, 4.16666667e-02f);                          // 1/4!
+    c = __fmaf_rn(t2, c, -0.5f);
+    c = __fmaf_rn(t2, c, 1.0f);
+    const int qi = ((int)q) & 3;
+    const float cs = (qi & 1) ? s : c, sn = (qi & 1) ? c : s;
+    return make_float2((qi == 1 || qi == 2) ? -cs : cs, (qi >= 2) ? -sn : sn);
 }
 
 // Seed phasor of channel c0 + lane of one row: t0 + frac(lane*dhi) + lane*dlo.

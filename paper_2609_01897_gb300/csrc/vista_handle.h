@@ -72,7 +72,7 @@ struct vista_stack {
     int32_t *err = nullptr;
     vista::DevBuf b_srcs, b_chf, b_chd, b_recs, b_off, b_stage, b_unpack, b_sort;
     std::vector<vista::ClassRun> classes;
-    vista::LaunchCfg cfg{64, 1, 4, 1, 8};
+    vista::LaunchCfg cfg{64, 1, 4, 1, 2};
     // stripe geometry of the row ordering (depends on the cube only)
     int32_t stripe_rows = 1, nstripe = 1, ushift = 0, nuk = 1;
     std::string msg;
