@@ -243,6 +243,12 @@ int vista_plan_channels(const double *freqs, int32_t nchan, double z, double res
 int vista_debug_phasors(vista_stack *h, int32_t src, double *dst);
 int vista_debug_cells(vista_stack *h, int32_t src, int32_t *dst);
 
+/* The order in which the mixed path of the last run walked the rows of
+ * window `src`: dst (device, [nrow] int32) receives row indices in
+ * processing order.  Available when the last run launched a single
+ * (vis type, chunk width, npol) class; E_STATE otherwise. */
+int vista_debug_order(vista_stack *h, int32_t src, int32_t *dst);
+
 #ifdef __cplusplus
 }
 #endif

@@ -500,3 +500,23 @@ extern "C" int vista_debug_cells(vista_stack *h, int32_t src, int32_t *dst)
     if (!dst) return fail(h, VISTA_E_ARG, "null output");
     return debug_common(h, src, nullptr, dst);
 }
+
+extern "C" int vista_debug_order(vista_stack *h, int32_t src, int32_t *dst)
+{
+    CHECK_HANDLE(h);
+    if (!dst) return fail(h, VISTA_E_ARG, "null output");
+    if (h->desc.precision != VISTA_PREC_MIXED || h->classes.size() != 1)
+        return fail(h, VISTA_E_STATE, "the processing order is kept for single-class mixed runs only");
+    const ClassRun &cr = h->classes[0];
+    for (size_t t = 0; t < cr.members.size(); ++t) {
+        if (cr.members[t] != src) continue;
+        int64_t off[2];
+        cudaError_t e = cudaMemcpy(off, cr.args.row_off + t, sizeof off, cudaMemcpyDeviceToHost);
+        if (e == cudaSuccess)
+            e = cudaMemcpy(dst, cr.args.so.perm + off[0], sizeof(int32_t) * (size_t)(off[1] - off[0]),
+                           cudaMemcpyDeviceToDevice);
+        if (e != cudaSuccess) return cuda_fail(h, e, "order export");
+        return VISTA_OK;
+    }
+    return fail(h, VISTA_E_ARG, "window %d has no row in the cube", src);
+}

@@ -93,6 +93,7 @@ SIGNATURES = {
                                       C.c_int32, C.c_int32, _P, _P, _P]),
     "vista_debug_phasors": (C.c_int, [_P, C.c_int32, _P]),
     "vista_debug_cells": (C.c_int, [_P, C.c_int32, _P]),
+    "vista_debug_order": (C.c_int, [_P, C.c_int32, _P]),
 }
 
 _lib = None
@@ -260,6 +261,11 @@ class Stack:
     def debug_cells(self, src, nrow, nchan):
         out = torch.full((nrow, nchan, 2), -7, dtype=torch.int32, device="cuda")
         _check("vista_debug_cells", lib().vista_debug_cells(self.h, src, _ptr(out)), self.h)
+        return out
+
+    def debug_order(self, src, nrow):
+        out = torch.full((nrow,), -1, dtype=torch.int32, device="cuda")
+        _check("vista_debug_order", lib().vista_debug_order(self.h, src, _ptr(out)), self.h)
         return out
 
     def close(self):
