@@ -9,7 +9,7 @@
 namespace vista {
 
 constexpr double C_LIGHT = 299792458.0;   // m/s
-constexpr int MAX_LOCAL_KEYS = 8192;      // cell keys inside one stripe (shared-memory histogram)
+constexpr int MAX_LOCAL_KEYS = 4096;      // cell keys inside one stripe (shared-memory histogram)
 
 // Cube geometry as the kernels see it.
 struct CubeGeom {

@@ -148,6 +148,7 @@ __global__ void __launch_bounds__(256) k_bucket_sort(RunArgs a)
         return;
     }
     __shared__ uint32_t sh[MAX_LOCAL_KEYS];
+    __shared__ uint32_t start[MAX_LOCAL_KEYS];
     __shared__ uint32_t part[256];
     const int nk = so.stripe_rows * so.nuk;
     for (int i = threadIdx.x; i < nk; i += blockDim.x) sh[i] = 0;
@@ -171,6 +172,7 @@ __global__ void __launch_bounds__(256) k_bucket_sort(RunArgs a)
     for (int k = k0; k < k1; ++k) {
         const uint32_t c = sh[k];
         sh[k] = run;
+        start[k] = run;
         run += c;
     }
     __syncthreads();
@@ -178,6 +180,31 @@ __global__ void __launch_bounds__(256) k_bucket_sort(RunArgs a)
         const unsigned long long t = so.tmp[base + i];
         const uint32_t pos = atomicAdd(&sh[(uint32_t)(t >> 32)], 1u);
         so.perm[base + pos] = (uint32_t)t;
+    }
+    __syncthreads();
+    // Rows that share a cell key arrive in arbitrary (atomic) order; order
+    // each such group by row index.  Rows of one baseline are then
+    // consecutive in time, so at the other channels of the window the cell
+    // changes at most once inside the group instead of alternating.
+    // A warp per group: rank of each row = rows of the group with a smaller
+    // index (indices are distinct), written to tmp, then copied back.
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    for (int k = warp; k < nk; k += nwarps) {
+        const uint32_t s0 = start[k], cnt = sh[k] - s0;
+        if (cnt < 2) continue;
+        const uint32_t *g = so.perm + base + s0;
+        for (uint32_t i = lane; i < cnt; i += 32) {
+            const uint32_t ri = g[i];
+            uint32_t rank = 0;
+            for (uint32_t j = 0; j < cnt; ++j) rank += g[j] < ri;
+            so.tmp[base + s0 + rank] = ri;
+        }
+    }
+    __syncthreads();
+    for (int k = warp; k < nk; k += nwarps) {
+        const uint32_t s0 = start[k], cnt = sh[k] - s0;
+        if (cnt < 2) continue;
+        for (uint32_t i = lane; i < cnt; i += 32) so.perm[base + s0 + i] = (uint32_t)so.tmp[base + s0 + i];
     }
 }
 
