@@ -22,11 +22,29 @@ constexpr int RB_MAX = 256;   // largest item (rows) the shared-memory buffers h
 // Running sums of one channel slot for one uv cell, written to the cube.
 // Out of line: after row ordering it runs once per several rows, and keeping
 // it out of the unrolled row loop keeps the loop small.
+// Everything one flush needs, passed by value: taking the address of the
+// live running sums would move them out of registers for the whole loop.
 template <int P>
-static __device__ __noinline__ uint32_t flush_slot(const RunArgs &a, int cell, int jn, float w0, float w1,
-                                                   const float *wtab, const float4 *acc, const uint32_t *cnt,
-                                                   const int *plane, bool pack2)
+struct FlushArgs {
+    float4 acc[P];
+    uint32_t cnt[P];
+    int plane[P];
+    int cell, jn;
+    float w0, w1;
+    const float *wtab;
+    bool pack2;
+};
+
+template <int P>
+static __device__ __noinline__ uint32_t flush_slot(const RunArgs &a, const FlushArgs<P> f)
 {
+    const float4 *acc = f.acc;
+    const uint32_t *cnt = f.cnt;
+    const int *plane = f.plane;
+    const int cell = f.cell, jn = f.jn;
+    const float w0 = f.w0, w1 = f.w1;
+    const float *wtab = f.wtab;
+    const bool pack2 = f.pack2;
     const int npol_c = a.g.npol;
     const int nbq = jn >> 28;
     float4 *cube4 = reinterpret_cast<float4 *>(a.cube);
@@ -176,8 +194,20 @@ __global__ void __launch_bounds__(256) stack_mixed(RunArgs a)
 #pragma unroll
             for (int p = 0; p < P; ++p) any |= cnt[q][p];
             if (cell[q] >= 0 && any) {
-                const float *wtab = a.chf[S.chan_off + (c0 + q * 32 + lane - S.k_lo)].w;
-                n_red += flush_slot<P>(a, cell[q], jn[q], wb[q][0], wb[q][1], wtab, acc[q], cnt[q], plane, pack2);
+                FlushArgs<P> fa;
+#pragma unroll
+                for (int p = 0; p < P; ++p) {
+                    fa.acc[p] = acc[q][p];
+                    fa.cnt[p] = cnt[q][p];
+                    fa.plane[p] = plane[p];
+                }
+                fa.cell = cell[q];
+                fa.jn = jn[q];
+                fa.w0 = wb[q][0];
+                fa.w1 = wb[q][1];
+                fa.wtab = a.chf[S.chan_off + (c0 + q * 32 + lane - S.k_lo)].w;
+                fa.pack2 = pack2;
+                n_red += flush_slot<P>(a, fa);
             }
 #pragma unroll
             for (int p = 0; p < P; ++p) {
