@@ -160,6 +160,7 @@ struct VisLoad;
 
 template <int P>
 struct VisLoad<P, VISTA_VIS_C64> {
+    static constexpr int kBytes = 8;   // bytes per complex value
     static __device__ __forceinline__ void load(const void *base, int64_t idx, float scale, float2 (&v)[P])
     {
         (void)scale;
@@ -183,6 +184,7 @@ struct VisLoad<P, VISTA_VIS_C64> {
 
 template <int P>
 struct VisLoad<P, VISTA_VIS_C128> {
+    static constexpr int kBytes = 16;
     static __device__ __forceinline__ void load(const void *base, int64_t idx, float scale, float2 (&v)[P])
     {
         (void)scale;
@@ -198,6 +200,7 @@ struct VisLoad<P, VISTA_VIS_C128> {
 
 template <int P>
 struct VisLoad<P, VISTA_VIS_F16X2> {
+    static constexpr int kBytes = 4;
     static __device__ __forceinline__ float2 cvt(uint32_t b, float scale)
     {
         __half2 h = *reinterpret_cast<__half2 *>(&b);
@@ -225,6 +228,7 @@ struct VisLoad<P, VISTA_VIS_F16X2> {
 
 template <int P>
 struct VisLoad<P, VISTA_VIS_BF16X2> {
+    static constexpr int kBytes = 4;
     static __device__ __forceinline__ float2 cvt(uint32_t b, float scale)
     {
         // bf16 -> f32 is a 16-bit shift

@@ -11,74 +11,44 @@
 // the lane recurrence (Sec. 3.2), guarded-FP32 uv cell that is bit-exact
 // against the FP64 cell rule, rest bins and Eq. 4 weights from the FP64
 // channel table.  Per lane, running sums over consecutive rows that share a
-// uv cell stay in registers and are flushed as one float4 reduction per
-// (cell, rest bin, pol) and one count reduction (one u64 for a pol pair).
+// uv cell stay in registers.  When a lane's cell changes, its finished run
+// is appended to a per-warp staging area in shared memory (slots from a warp
+// ballot, no divergent branch); the warp drains the staging area together,
+// one lane per run, as float4 reductions per (cell, rest bin, pol) and one
+// count reduction per (cell, rest bin) (one u64 for a pol pair).
 #include "vista_device.cuh"
 
 namespace vista {
 
-constexpr int RB_MAX = 256;   // largest item (rows) the shared-memory buffers hold
+constexpr int RB_MAX = 256;     // largest item (rows) the shared-memory buffers hold
+constexpr int STAGE_CAP = 96;   // staged runs per warp
 
-// Running sums of one channel slot for one uv cell, written to the cube.
-// Out of line: after row ordering it runs once per several rows, and keeping
-// it out of the unrolled row loop keeps the loop small.
-// Everything one flush needs, passed by value: taking the address of the
-// live running sums would move them out of registers for the whole loop.
+// One finished run of one channel slot.
 template <int P>
-struct FlushArgs {
-    float4 acc[P];
+struct __align__(16) Staged {
+    int cell;         // iv * nu + iu
+    int chf;          // channel-table entry (rest bins and weights)
     uint32_t cnt[P];
-    int plane[P];
-    int cell, jn;
-    float w0, w1;
-    const float *wtab;
-    bool pack2;
+    float4 acc[P];    // sum W V'.re, sum W V'.im, sum W, sum W |V|^2
 };
 
 template <int P>
-static __device__ __noinline__ uint32_t flush_slot(const RunArgs &a, const FlushArgs<P> f)
+__host__ __device__ constexpr size_t warp_smem_bytes(int rb)
 {
-    const float4 *acc = f.acc;
-    const uint32_t *cnt = f.cnt;
-    const int *plane = f.plane;
-    const int cell = f.cell, jn = f.jn;
-    const float w0 = f.w0, w1 = f.w1;
-    const float *wtab = f.wtab;
-    const bool pack2 = f.pack2;
-    const int npol_c = a.g.npol;
-    const int nbq = jn >> 28;
-    float4 *cube4 = reinterpret_cast<float4 *>(a.cube);
-    const size_t base = ((size_t)cell * a.g.nrest + (jn & 0x0fffffff)) * npol_c;
-    uint32_t nred = 0;
-    for (int b = 0; b < nbq; ++b) {
-        const float ww = b == 0 ? w0 : b == 1 ? w1 : wtab[b];
-        const size_t e = base + (size_t)b * npol_c;
-        for (int p = 0; p < P; ++p) {
-            if (cnt[p] == 0) continue;
-            atomicAdd(cube4 + e + plane[p], make_float4(ww * acc[p].x, ww * acc[p].y, ww * acc[p].z, ww * acc[p].w));
-            ++nred;
-            if (!pack2) {
-                atomicAdd(a.count + e + plane[p], cnt[p]);
-                ++nred;
-            }
-        }
-        if (pack2 && (cnt[0] | cnt[P - 1])) {
-            atomicAdd(reinterpret_cast<unsigned long long *>(a.count + e + plane[0]),
-                      (unsigned long long)cnt[0] | ((unsigned long long)cnt[P - 1] << 32));
-            ++nred;
-        }
-    }
-    return nred;
+    return 2 * (size_t)rb * sizeof(RowRec) + STAGE_CAP * sizeof(Staged<P>) + 2 * sizeof(uint64_t);
 }
 
 template <int P, int VT, int NS, int D>
 __global__ void __launch_bounds__(256) stack_mixed(RunArgs a)
 {
     extern __shared__ __align__(16) unsigned char smem[];
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const int RB = a.so.rows_per_item;
-    RowRec *rbuf = reinterpret_cast<RowRec *>(smem) + (size_t)wid * 2 * RB;
-    uint64_t *bars = reinterpret_cast<uint64_t *>(smem + (size_t)nwarp * 2 * RB * sizeof(RowRec)) + 2 * wid;
+    unsigned char *wsm = smem + (size_t)wid * warp_smem_bytes<P>(RB);
+    RowRec *rbuf = reinterpret_cast<RowRec *>(wsm);
+    Staged<P> *stage = reinterpret_cast<Staged<P> *>(wsm + 2 * (size_t)RB * sizeof(RowRec));
+    uint64_t *bars = reinterpret_cast<uint64_t *>(wsm + 2 * (size_t)RB * sizeof(RowRec) +
+                                                  STAGE_CAP * sizeof(Staged<P>));
     if (lane == 0) {
         mbar_init(&bars[0], 1);
         mbar_init(&bars[1], 1);
@@ -87,6 +57,9 @@ __global__ void __launch_bounds__(256) stack_mixed(RunArgs a)
     __syncwarp();
 
     const uint32_t nitems = a.so.ctr[0];
+    const int npol_c = a.g.npol, nrest = a.g.nrest;
+    const unsigned lt_mask = (1u << lane) - 1u;
+    float4 *cube4 = reinterpret_cast<float4 *>(a.cube);
     uint32_t n_flag = 0, n_duv = 0, n_red = 0;
     uint32_t phase = 0;   // bit s: parity of the next completion of slot s
 
@@ -128,53 +101,50 @@ __global__ void __launch_bounds__(256) stack_mixed(RunArgs a)
         const RowRec *rb = rbuf + (size_t)cs * RB;
 
         // ---- one item ----
-        // window fields in registers (the cube reductions below could alias
-        // global memory, so references into the table would be re-read)
-        struct WinRegs {
-            const void *vis;
-            const uint8_t *flags;
-            const double *uvw;
-            int64_t vstride, kbase;
-            float vis_scale;
-            int32_t k_lo, k_hi, chan_off, linear;
-        } S;
+        // window fields in registers (the cube reductions could alias global
+        // memory, so references into the table would be re-read)
+        const void *vis;
+        const uint8_t *flags;
+        const double *uvw;
+        int64_t vstride;
+        float vscale;
+        int k_lo, k_hi, chan_off;
+        bool linear;
+        int plane[P];
         {
             const SrcDev &G = a.srcs[item.w];
-            S.vis = G.vis;
-            S.flags = G.flags;
-            S.uvw = G.uvw;
-            S.vstride = G.vstride;
-            S.kbase = G.kbase;
-            S.vis_scale = G.vis_scale;
-            S.k_lo = G.k_lo;
-            S.k_hi = G.k_hi;
-            S.chan_off = G.chan_off;
-            S.linear = G.linear;
-        }
-        const int c0 = S.k_lo + item.chunk * 32 * NS;
-        const bool linear = S.linear != 0;
-        int plane[P];
+            vis = G.vis;
+            flags = G.flags;
+            uvw = G.uvw;
+            vstride = G.vstride;
+            vscale = G.vis_scale;
+            k_lo = G.k_lo;
+            k_hi = G.k_hi;
+            chan_off = G.chan_off;
+            linear = G.linear != 0;
+            const int c0g = G.k_lo + item.chunk * 32 * NS;
+            vis = reinterpret_cast<const char *>(G.vis) +
+                  (int64_t)(c0g + lane - G.kbase) * P * (int64_t)VisLoad<P, VT>::kBytes;
+            if (flags) flags += (int64_t)(c0g + lane - G.kbase) * P;
 #pragma unroll
-        for (int p = 0; p < P; ++p) plane[p] = a.srcs[item.w].plane[p];
-        const bool pack2 = (P == 2) && plane[0] >= 0 && plane[1] == plane[0] + 1 && !(plane[0] & 1) &&
-                           !(a.g.npol & 1);
+            for (int p = 0; p < P; ++p) plane[p] = G.plane[p];
+        }
+        const int c0 = k_lo + item.chunk * 32 * NS;
+        const bool pack2 = (P == 2) && plane[0] >= 0 && plane[1] == plane[0] + 1 && !(plane[0] & 1) && !(npol_c & 1);
 
-        // per channel slot: fl32(s_k), first bin | bin count << 28, first two weights
-        float su[NS], sv[NS], wb[NS][2];
-        int jn[NS];
+        // per channel slot: fl32(s_k) and whether the channel has a rest bin
+        float su[NS], sv[NS];
+        bool act[NS];
 #pragma unroll
         for (int q = 0; q < NS; ++q) {
             const int k = c0 + q * 32 + lane;
-            jn[q] = 0;
+            act[q] = false;
             su[q] = sv[q] = 0.f;
-            wb[q][0] = wb[q][1] = 0.f;
-            if (k < S.k_hi) {
-                const ChanF cf = a.chf[S.chan_off + (k - S.k_lo)];
+            if (k < k_hi) {
+                const ChanF cf = a.chf[chan_off + (k - k_lo)];
                 su[q] = cf.su;
                 sv[q] = cf.sv;
-                jn[q] = cf.j0 | (cf.nb << 28);
-                wb[q][0] = cf.w[0];
-                wb[q][1] = cf.w[1];
+                act[q] = cf.nb > 0;
             }
         }
         int cell[NS];
@@ -189,31 +159,53 @@ __global__ void __launch_bounds__(256) stack_mixed(RunArgs a)
                 cnt[q][p] = 0;
             }
         }
-        auto flush = [&](int q) {
-            uint32_t any = 0;
-#pragma unroll
-            for (int p = 0; p < P; ++p) any |= cnt[q][p];
-            if (cell[q] >= 0 && any) {
-                FlushArgs<P> fa;
+        int nstaged = 0;
+
+        // Stage lane runs that end here (`fl`): convergent, slots by ballot.
+        auto stage_runs = [&](int q, bool fl) {
+            const unsigned bal = __ballot_sync(0xffffffffu, fl);
+            if (fl) {
+                Staged<P> &st = stage[nstaged + __popc(bal & lt_mask)];
+                st.cell = cell[q];
+                st.chf = chan_off + (c0 + q * 32 + lane - k_lo);
 #pragma unroll
                 for (int p = 0; p < P; ++p) {
-                    fa.acc[p] = acc[q][p];
-                    fa.cnt[p] = cnt[q][p];
-                    fa.plane[p] = plane[p];
+                    st.cnt[p] = cnt[q][p];
+                    st.acc[p] = acc[q][p];
                 }
-                fa.cell = cell[q];
-                fa.jn = jn[q];
-                fa.w0 = wb[q][0];
-                fa.w1 = wb[q][1];
-                fa.wtab = a.chf[S.chan_off + (c0 + q * 32 + lane - S.k_lo)].w;
-                fa.pack2 = pack2;
-                n_red += flush_slot<P>(a, fa);
             }
+            nstaged += __popc(bal);
+        };
+        // All lanes write the staged runs to the cube, one run per lane.
+        auto drain = [&]() {
+            __syncwarp();
+            for (int e = lane; e < nstaged; e += 32) {
+                const Staged<P> &st = stage[e];
+                const ChanF cf = a.chf[st.chf];
+                const size_t base = ((size_t)st.cell * nrest + cf.j0) * npol_c;
+                for (int b = 0; b < cf.nb; ++b) {
+                    const float ww = cf.w[b];
+                    const size_t e2 = base + (size_t)b * npol_c;
 #pragma unroll
-            for (int p = 0; p < P; ++p) {
-                acc[q][p] = make_float4(0.f, 0.f, 0.f, 0.f);
-                cnt[q][p] = 0;
+                    for (int p = 0; p < P; ++p) {
+                        if (st.cnt[p] == 0) continue;
+                        const float4 v = st.acc[p];
+                        atomicAdd(cube4 + e2 + plane[p], make_float4(ww * v.x, ww * v.y, ww * v.z, ww * v.w));
+                        ++n_red;
+                        if (!pack2) {
+                            atomicAdd(a.count + e2 + plane[p], st.cnt[p]);
+                            ++n_red;
+                        }
+                    }
+                    if (pack2 && (st.cnt[0] | st.cnt[P - 1])) {
+                        atomicAdd(reinterpret_cast<unsigned long long *>(a.count + e2 + plane[0]),
+                                  (unsigned long long)st.cnt[0] | ((unsigned long long)st.cnt[P - 1] << 32));
+                        ++n_red;
+                    }
+                }
             }
+            __syncwarp();
+            nstaged = 0;
         };
 
         // visibility / flag ring, D rows ahead
@@ -222,13 +214,13 @@ __global__ void __launch_bounds__(256) stack_mixed(RunArgs a)
         uint32_t RF[D][NS];
         auto fetch = [&](int d, int i) {
             const int64_t row = (int64_t)(rb[i].rowf & 0x7fffffffu);
+            const int64_t off = row * vstride;
 #pragma unroll
             for (int q = 0; q < NS; ++q) {
                 RF[d][q] = 0;
-                if (jn[q] >> 28) {
-                    const int64_t vidx = row * S.vstride + (c0 + q * 32 + lane - S.kbase);
-                    VisLoad<P, VT>::load(S.vis, vidx, S.vis_scale, RV[d][q]);
-                    RF[d][q] = load_flags<P>(S.flags, vidx);
+                if (act[q]) {
+                    VisLoad<P, VT>::load(vis, off + q * 32, vscale, RV[d][q]);
+                    RF[d][q] = load_flags<P>(flags, off + q * 32);
                 }
             }
         };
@@ -260,21 +252,33 @@ __global__ void __launch_bounds__(256) stack_mixed(RunArgs a)
 #pragma unroll
                 for (int q = 0; q < NS; ++q) {
                     const int k = c0 + q * 32 + lane;
-                    if (!linear && k < S.k_hi) {
+                    if (!linear && k < k_hi) {
                         const double tau = __hiloint2double(__float_as_int(rec.dhi), __float_as_int(rec.dlo));
-                        double t = tau * (a.chd[S.chan_off + (k - S.k_lo)].nu * (1.0 / C_LIGHT));
+                        double t = tau * (a.chd[chan_off + (k - k_lo)].nu * (1.0 / C_LIGHT));
                         t -= floor(t);
                         ph = turns_to_phasor((float)t);
                     }
-                    if (jn[q] >> 28) {
-                        const ChanD *cd = a.chd + S.chan_off + (k - S.k_lo);
-                        const int iu = axis_cell(rec.u, su[q], S.uvw + 3 * row, fold, &cd->su, a.g.nu);
-                        const int iv = axis_cell(rec.v, sv[q], S.uvw + 3 * row + 1, fold, &cd->sv, a.g.nv);
-                        const int cid = (iu >= 0 && iv >= 0) ? iv * a.g.nu + iu : -1;
-                        if (cid != cell[q]) {
-                            flush(q);
-                            cell[q] = cid;
+                    int cid = cell[q];
+                    if (act[q]) {
+                        const ChanD *cd = a.chd + chan_off + (k - k_lo);
+                        const int iu = axis_cell(rec.u, su[q], uvw + 3 * row, fold, &cd->su, a.g.nu);
+                        const int iv = axis_cell(rec.v, sv[q], uvw + 3 * row + 1, fold, &cd->sv, a.g.nv);
+                        cid = (iu >= 0 && iv >= 0) ? iv * a.g.nu + iu : -1;
+                    }
+                    const bool newcell = cid != cell[q];
+                    uint32_t any = 0;
+#pragma unroll
+                    for (int p = 0; p < P; ++p) any |= cnt[q][p];
+                    stage_runs(q, newcell && cell[q] >= 0 && any != 0);
+                    if (newcell) {
+                        cell[q] = cid;
+#pragma unroll
+                        for (int p = 0; p < P; ++p) {
+                            acc[q][p] = make_float4(0.f, 0.f, 0.f, 0.f);
+                            cnt[q][p] = 0;
                         }
+                    }
+                    if (act[q]) {
 #pragma unroll
                         for (int p = 0; p < P; ++p) {
                             if (plane[p] < 0) continue;
@@ -299,10 +303,18 @@ __global__ void __launch_bounds__(256) stack_mixed(RunArgs a)
                     }
                     if (linear && q + 1 < NS) ph = cmul(ph, make_float2(rec.sre, rec.sim));
                 }
+                if (nstaged > STAGE_CAP - 32 * NS) drain();
             }
         }
 #pragma unroll
-        for (int q = 0; q < NS; ++q) flush(q);
+        for (int q = 0; q < NS; ++q) {
+            uint32_t any = 0;
+#pragma unroll
+            for (int p = 0; p < P; ++p) any |= cnt[q][p];
+            stage_runs(q, cell[q] >= 0 && any != 0);
+            if (nstaged > STAGE_CAP - 32) drain();
+        }
+        drain();
         s ^= 1;
     }
 
@@ -334,12 +346,12 @@ static int sm_count()
     return n;
 }
 
-template <typename K>
+template <int P, typename K>
 static cudaError_t launch_persistent(K kern, const RunArgs &a, int wpc, cudaStream_t st)
 {
     const int rb = a.so.rows_per_item;
     if (rb < 1 || rb > RB_MAX) return cudaErrorInvalidValue;
-    const size_t smem = (size_t)wpc * (2 * (size_t)rb * sizeof(RowRec) + 2 * sizeof(uint64_t));
+    const size_t smem = (size_t)wpc * warp_smem_bytes<P>(rb);
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     int per_sm = 0;
@@ -360,16 +372,16 @@ static cudaError_t launch_mixed_p(const RunArgs &a, int ns, int pf, int wpc, cud
     switch (ns) {
     case 1:
         if constexpr (choice) {
-            if (pf >= 8) return launch_persistent(stack_mixed<P, VT, 1, 8>, a, wpc, st);
-            if (pf >= 4) return launch_persistent(stack_mixed<P, VT, 1, 4>, a, wpc, st);
+            if (pf >= 8) return launch_persistent<P>(stack_mixed<P, VT, 1, 8>, a, wpc, st);
+            if (pf >= 4) return launch_persistent<P>(stack_mixed<P, VT, 1, 4>, a, wpc, st);
         }
-        return launch_persistent(stack_mixed<P, VT, 1, 2>, a, wpc, st);
+        return launch_persistent<P>(stack_mixed<P, VT, 1, 2>, a, wpc, st);
     case 2:
         if constexpr (choice) {
-            if (pf >= 4) return launch_persistent(stack_mixed<P, VT, 2, 4>, a, wpc, st);
+            if (pf >= 4) return launch_persistent<P>(stack_mixed<P, VT, 2, 4>, a, wpc, st);
         }
-        return launch_persistent(stack_mixed<P, VT, 2, (P <= 2 ? 2 : 1)>, a, wpc, st);
-    case 4: return launch_persistent(stack_mixed<P, VT, 4, 1>, a, wpc, st);
+        return launch_persistent<P>(stack_mixed<P, VT, 2, (P <= 2 ? 2 : 1)>, a, wpc, st);
+    case 4: return launch_persistent<P>(stack_mixed<P, VT, 4, 1>, a, wpc, st);
     default: return cudaErrorInvalidValue;
     }
 }
