@@ -132,14 +132,22 @@ static __device__ __noinline__ float exact_floor_product(const double *coord64, 
     return (float)floor(__dmul_rn(c, *s64));
 }
 
-__device__ __forceinline__ int axis_cell(float c32, float s32, const double *coord64, bool neg,
-                                         const double *s64, int n)
+// floor(fl64(coord * s_k)) as a float (exact; see axis_cell).
+__device__ __forceinline__ float axis_floor(float c32, float s32, const double *coord64, bool neg,
+                                            const double *s64)
 {
     float x = __fmul_rn(c32, s32);
     float d = __fmaf_rn(fabsf(x), 4.76837158203125e-07f, 1e-30f);
     float fa = floorf(__fsub_rn(x, d)), fb = floorf(__fadd_rn(x, d));
     float fx = fa;
     if (__builtin_expect(fa != fb, 0)) fx = exact_floor_product(coord64, neg, s64);
+    return fx;
+}
+
+__device__ __forceinline__ int axis_cell(float c32, float s32, const double *coord64, bool neg,
+                                         const double *s64, int n)
+{
+    const float fx = axis_floor(c32, s32, coord64, neg, s64);
     float h = (float)(n >> 1);
     if (!(fx >= -h && fx < h)) return -1;
     return (int)fx + (n >> 1);

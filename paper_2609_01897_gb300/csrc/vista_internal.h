@@ -10,6 +10,7 @@ namespace vista {
 
 constexpr double C_LIGHT = 299792458.0;   // m/s
 constexpr int MAX_LOCAL_KEYS = 4096;      // cell keys inside one stripe (shared-memory histogram)
+constexpr int CELL_MIXED = -2;            // a chunk's channels fall in more than one uv cell
 
 // Cube geometry as the kernels see it.
 struct CubeGeom {
@@ -65,7 +66,10 @@ struct SrcDev {
 //               per-lane recurrence
 //   u, v        fl32 of the (folded) uvw, metres
 //   rowf        row index | (fold << 31)
-//   W[4]        the row's weights
+//   W[4]        the row's weights; for windows with at most two pols W[3]
+//               instead holds (as int bits) the uv cell shared by every
+//               channel of the chunk, -1 if that cell is off the grid, or
+//               CELL_MIXED if the chunk's channels fall in different cells
 // For windows without a linear axis, dhi/dlo carry the bits of tau (FP64).
 struct __align__(16) RowRec {
     float t0, dhi, dlo, sre;

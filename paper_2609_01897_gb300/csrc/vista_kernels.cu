@@ -44,8 +44,17 @@ __global__ void debug_mixed(RunArgs a, int src, double *ph_out, int32_t *cell_ou
                 t -= floor(t);
                 ph = turns_to_phasor((float)t);
             }
-            const int iu = axis_cell(rec.u, cf.su, S.uvw + 3 * row, fold, &cd->su, a.g.nu);
-            const int iv = axis_cell(rec.v, cf.sv, S.uvw + 3 * row + 1, fold, &cd->sv, a.g.nv);
+            // same cell path as the stacking kernel: the chunk's shared cell
+            // from the pre-pass when there is one, else per channel
+            const int cinfo = S.npol <= 2 ? __float_as_int(rec.W[3]) : CELL_MIXED;
+            int iu, iv;
+            if (cinfo != CELL_MIXED) {
+                iu = cinfo < 0 ? -1 : cinfo % a.g.nu;
+                iv = cinfo < 0 ? -1 : cinfo / a.g.nu;
+            } else {
+                iu = axis_cell(rec.u, cf.su, S.uvw + 3 * row, fold, &cd->su, a.g.nu);
+                iv = axis_cell(rec.v, cf.sv, S.uvw + 3 * row + 1, fold, &cd->sv, a.g.nv);
+            }
             const int64_t o = row * S.nchan + k;
             if (ph_out) {
                 ph_out[2 * o] = (double)ph.x;

@@ -244,11 +244,30 @@ __global__ void __launch_bounds__(256) k_records(RunArgs a)
         rec.sim = 0.0f;
     }
     const ChanD *cd = a.chd + S.chan_off;
+    const ChanF *cf = a.chf + S.chan_off;
+    const int nin = S.k_hi - S.k_lo;
     RowRec *out = a.recs + S.rec_off + q;
     for (int c = 0; c < S.nchunk; ++c) {
         double t = tau * (cd[c * a.cw].nu * (1.0 / C_LIGHT));
         t -= floor(t);
         rec.t0 = (float)t;
+        if (S.npol <= 2) {
+            // The cell index is monotone in frequency along a row, so equal
+            // cells at the chunk's two end channels hold for every channel
+            // between them.
+            const int e0 = c * a.cw, e1 = min(nin, (c + 1) * a.cw) - 1;
+            const float fu0 = axis_floor(rec.u, cf[e0].su, uvw, fold, &cd[e0].su);
+            const float fu1 = axis_floor(rec.u, cf[e1].su, uvw, fold, &cd[e1].su);
+            const float fv0 = axis_floor(rec.v, cf[e0].sv, uvw + 1, fold, &cd[e0].sv);
+            const float fv1 = axis_floor(rec.v, cf[e1].sv, uvw + 1, fold, &cd[e1].sv);
+            int info = CELL_MIXED;
+            if (fu0 == fu1 && fv0 == fv1) {
+                const float hu = (float)(a.g.nu >> 1), hv = (float)(a.g.nv >> 1);
+                const bool in = fu0 >= -hu && fu0 < hu && fv0 >= -hv && fv0 < hv;
+                info = in ? ((int)fv0 + (a.g.nv >> 1)) * a.g.nu + ((int)fu0 + (a.g.nu >> 1)) : -1;
+            }
+            rec.W[3] = __int_as_float(info);
+        }
         out[(int64_t)c * S.nrow] = rec;
     }
 }

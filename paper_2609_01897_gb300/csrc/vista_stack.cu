@@ -249,6 +249,8 @@ __global__ void __launch_bounds__(256) stack_mixed(RunArgs a)
                 const bool fold = (rowf >> 31) != 0;
                 float2 ph = make_float2(1.f, 0.f);
                 if (linear) ph = lane_seed(rec, lane);
+                // the chunk's shared cell, if the pre-pass found one (<= 2 pols)
+                const int cinfo = P <= 2 ? __float_as_int(rec.W[3]) : CELL_MIXED;
 #pragma unroll
                 for (int q = 0; q < NS; ++q) {
                     const int k = c0 + q * 32 + lane;
@@ -260,10 +262,14 @@ __global__ void __launch_bounds__(256) stack_mixed(RunArgs a)
                     }
                     int cid = cell[q];
                     if (act[q]) {
-                        const ChanD *cd = a.chd + chan_off + (k - k_lo);
-                        const int iu = axis_cell(rec.u, su[q], uvw + 3 * row, fold, &cd->su, a.g.nu);
-                        const int iv = axis_cell(rec.v, sv[q], uvw + 3 * row + 1, fold, &cd->sv, a.g.nv);
-                        cid = (iu >= 0 && iv >= 0) ? iv * a.g.nu + iu : -1;
+                        if (cinfo != CELL_MIXED) {
+                            cid = cinfo;
+                        } else {
+                            const ChanD *cd = a.chd + chan_off + (k - k_lo);
+                            const int iu = axis_cell(rec.u, su[q], uvw + 3 * row, fold, &cd->su, a.g.nu);
+                            const int iv = axis_cell(rec.v, sv[q], uvw + 3 * row + 1, fold, &cd->sv, a.g.nv);
+                            cid = (iu >= 0 && iv >= 0) ? iv * a.g.nu + iu : -1;
+                        }
                     }
                     const bool newcell = cid != cell[q];
                     uint32_t any = 0;
@@ -281,24 +287,23 @@ __global__ void __launch_bounds__(256) stack_mixed(RunArgs a)
                     if (act[q]) {
 #pragma unroll
                         for (int p = 0; p < P; ++p) {
-                            if (plane[p] < 0) continue;
-                            if ((F[q] >> (8 * p)) & 0xffu) {
-                                ++n_flag;
-                                continue;
-                            }
-                            if (cid < 0) {
-                                ++n_duv;
-                                continue;
-                            }
+                            // short predicated bodies instead of branches
+                            const bool pl = plane[p] >= 0;
+                            const bool f = ((F[q] >> (8 * p)) & 0xffu) != 0;
+                            const bool use = pl && !f && cid >= 0;
+                            n_flag += (pl && f) ? 1u : 0u;
+                            n_duv += (pl && !f && cid < 0) ? 1u : 0u;
                             float2 vs = cmul(V[q][p], ph);
-                            if (fold) vs.y = -vs.y;
+                            vs.y = fold ? -vs.y : vs.y;
                             const float W = rec.W[p];
                             const float a2 = V[q][p].x * V[q][p].x + V[q][p].y * V[q][p].y;
-                            acc[q][p].x += W * vs.x;
-                            acc[q][p].y += W * vs.y;
-                            acc[q][p].z += W;
-                            acc[q][p].w += W * a2;
-                            cnt[q][p] += 1;
+                            if (use) {
+                                acc[q][p].x += W * vs.x;
+                                acc[q][p].y += W * vs.y;
+                                acc[q][p].z += W;
+                                acc[q][p].w += W * a2;
+                                cnt[q][p] += 1;
+                            }
                         }
                     }
                     if (linear && q + 1 < NS) ph = cmul(ph, make_float2(rec.sre, rec.sim));
@@ -351,6 +356,14 @@ static cudaError_t launch_persistent(K kern, const RunArgs &a, int wpc, cudaStre
 {
     const int rb = a.so.rows_per_item;
     if (rb < 1 || rb > RB_MAX) return cudaErrorInvalidValue;
+    static int smem_max = 0;
+    if (smem_max == 0) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    }
+    // fewer warps per block when their staging buffers would not fit
+    while (wpc > 1 && (size_t)wpc * warp_smem_bytes<P>(rb) > (size_t)smem_max) wpc >>= 1;
     const size_t smem = (size_t)wpc * warp_smem_bytes<P>(rb);
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
