@@ -162,10 +162,15 @@ __global__ void __launch_bounds__(256) stack_mixed(RunArgs a)
         int nstaged = 0;
 
         // Stage lane runs that end here (`fl`): convergent, slots by ballot.
+        // The caller drains whenever fewer than 32 slots are free, so the
+        // index below stays inside the buffer; the check records a breach
+        // instead of writing out of bounds.
         auto stage_runs = [&](int q, bool fl) {
             const unsigned bal = __ballot_sync(0xffffffffu, fl);
-            if (fl) {
-                Staged<P> &st = stage[nstaged + __popc(bal & lt_mask)];
+            const int slot = nstaged + __popc(bal & lt_mask);
+            if (fl && slot >= STAGE_CAP) atomicExch(a.err, 3);
+            if (fl && slot < STAGE_CAP) {
+                Staged<P> &st = stage[slot];
                 st.cell = cell[q];
                 st.chf = chan_off + (c0 + q * 32 + lane - k_lo);
 #pragma unroll
@@ -276,6 +281,7 @@ __global__ void __launch_bounds__(256) stack_mixed(RunArgs a)
 #pragma unroll
                     for (int p = 0; p < P; ++p) any |= cnt[q][p];
                     stage_runs(q, newcell && cell[q] >= 0 && any != 0);
+                    if (nstaged > STAGE_CAP - 32) drain();
                     if (newcell) {
                         cell[q] = cid;
 #pragma unroll
@@ -308,7 +314,6 @@ __global__ void __launch_bounds__(256) stack_mixed(RunArgs a)
                     }
                     if (linear && q + 1 < NS) ph = cmul(ph, make_float2(rec.sre, rec.sim));
                 }
-                if (nstaged > STAGE_CAP - 32 * NS) drain();
             }
         }
 #pragma unroll
