@@ -249,6 +249,35 @@ int vista_debug_cells(vista_stack *h, int32_t src, int32_t *dst);
  * (vis type, chunk width, npol) class; E_STATE otherwise. */
 int vista_debug_order(vista_stack *h, int32_t src, int32_t *dst);
 
+/* ---- stacking without allocation -----------------------------------------
+ * (No counterpart in the paper: a deployment convenience.)
+ *
+ * Some callers cannot call cudaMalloc: an application whose device memory is
+ * all owned by another allocator (a framework that reserves the GPU up
+ * front), or a pipeline that must not allocate once running because an
+ * allocation can synchronise the device at an arbitrary moment.  This call
+ * stacks one (source, window) with the mixed-precision path without
+ * allocating anything: no handle, and every intermediate lives in one
+ * fixed 8 MiB device array inside the library, reserved when the library
+ * is loaded and kept by every GPU that loads it until the process exits.
+ *
+ *   cube    descriptor of the cube; rest_df > 0 is required (the lattice is
+ *           the caller's), precision must be VISTA_PREC_MIXED; stream used.
+ *   src     one window, device memory (mem = VISTA_MEM_DEVICE).
+ *   cube4   caller's device array [nv][nu][nrest][npol][4] float:
+ *           (sum W V'.re, sum W V'.im, sum W, sum W |V|^2), added to.
+ *   count   caller's device array [nv][nu][nrest][npol] uint32, added to.
+ *
+ * Returns after the work has finished.  E_RANGE when the window needs more
+ * scratch than the array holds (roughly nrow x chunks x 48 bytes of row
+ * records plus ~24 bytes per row).  The first call on a device looks up
+ * the array's device address, so make that first call before any stream
+ * capture.  All calls share the array: calls whose device work overlaps
+ * (other host threads, other streams) race on it and must not be made;
+ * each call clears what must start at zero.  Errors: vista_last_error(NULL). */
+int vista_stack_noalloc(const vista_cube_desc *cube, const vista_source_desc *src, float *cube4,
+                        uint32_t *count);
+
 #ifdef __cplusplus
 }
 #endif

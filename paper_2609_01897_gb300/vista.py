@@ -94,6 +94,7 @@ SIGNATURES = {
     "vista_debug_phasors": (C.c_int, [_P, C.c_int32, _P]),
     "vista_debug_cells": (C.c_int, [_P, C.c_int32, _P]),
     "vista_debug_order": (C.c_int, [_P, C.c_int32, _P]),
+    "vista_stack_noalloc": (C.c_int, [C.POINTER(CubeDesc), C.POINTER(SourceDesc), _P, _P]),
 }
 
 _lib = None
