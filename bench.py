@@ -128,6 +128,25 @@ class Clocks:
                 "samples": len(sm)}
 
 
+def measured_traffic(n_vis):
+    """DRAM bytes per stacking launch from the committed ncu summary, scaled by
+    the visibilities of this launch -- or None once the kernel source differs
+    from the one the counters were taken on."""
+    import hashlib
+    import re
+    try:
+        txt = open(os.path.join(ROOT, "profiles", "stack_mixed_alma_compact.md")).read()
+        sha = re.search(r"source_sha256:\s*([0-9a-f]{64})", txt).group(1)
+        per_vis = float(re.search(r"traffic_bytes_per_vis:\s*([0-9.]+)", txt).group(1))
+    except (OSError, AttributeError, ValueError):
+        return None
+    h = hashlib.sha256()
+    for f in ("vista_stack.cu", "vista_device.cuh"):
+        with open(os.path.join(ROOT, "paper_2609_01897_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return per_vis * n_vis if h.hexdigest() == sha else None
+
+
 def measured_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
@@ -309,7 +328,7 @@ def run_ours(args):
                        "tuning": st_tuning_str(eff_tuning),
                        "parallelism": "replicas" if ws > 1 else "single"},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": achieved / peak, "traffic": None, "kernel": "stack_mixed",
+                         "frac": achieved / peak, "traffic": measured_traffic(n_vis), "kernel": "stack_mixed",
                          "algorithmic_bytes_per_launch": alg, "kernel_ms": stack_ms,
                          "peak_source": peak_kind},
             "prepass_ms": tm["prepass_ms"] / max(1, args.steps),
