@@ -109,14 +109,26 @@ __device__ __forceinline__ float2 turns_to_phasor(float t)
     return make_float2((qi == 1 || qi == 2) ? -cs : cs, (qi >= 2) ? -sn : sn);
 }
 
-// Seed phasor of channel c0 + lane of one row: t0 + frac(lane*dhi) + lane*dlo.
-// lane*dhi is exact (dhi has <= 19 significant bits, lane < 32).
-__device__ __forceinline__ float2 lane_seed(const RowRec &rec, int lane)
+// exp(+2 pi i tau nu_k / c) from tau and nu_k / c given as float-float
+// pairs.  The product is formed as p + e + x: p = fl(tau_hi nuc_hi), e its
+// exact rounding error (one FMA), x the cross terms; tau_lo nuc_lo is below
+// 2^-48 of the product and dropped.  p minus its nearest integer is exact, so
+// the turns reach turns_to_phasor reduced, with an error of about 2^-25 turn
+// (2e-7 rad) for phases up to 2^23 turns.
+__device__ __forceinline__ float2 shift_phasor(float tau_hi, float tau_lo, float nuc_hi, float nuc_lo)
 {
-    float a = (float)lane * rec.dhi;
-    a = __fsub_rn(a, floorf(a));
-    float t = __fadd_rn(__fadd_rn(rec.t0, a), (float)lane * rec.dlo);
-    return turns_to_phasor(t);
+    const float p = __fmul_rn(tau_hi, nuc_hi);
+    const float e = __fmaf_rn(tau_hi, nuc_hi, -p);
+    const float x = __fmaf_rn(tau_hi, nuc_lo, __fmaf_rn(tau_lo, nuc_hi, e));
+    const float r = __fsub_rn(p, rintf(p));
+    return turns_to_phasor(__fadd_rn(r, x));
+}
+
+// Split a double into a float-float pair hi + lo.
+__device__ __host__ __forceinline__ void split_ff(double x, float &hi, float &lo)
+{
+    hi = (float)x;
+    lo = (float)(x - (double)hi);
 }
 
 // One axis of the uv cell: floor(fl64(coord * s_k)) + n/2, or -1 outside

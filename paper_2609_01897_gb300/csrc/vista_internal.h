@@ -19,11 +19,15 @@ struct CubeGeom {
     int32_t fold, pad;
 };
 
-// Per channel the path reads, mixed path (32 B).  su/sv are fl32(s_k).
+// Per channel the path reads, mixed path (32 B).  su/sv are fl32(s_k);
+// nuc_hi + nuc_lo = nu_k / c as a float-float pair (the phase is
+// tau * nu_k / c); w0, w1 the first two Eq. 4 weights (a third or fourth,
+// possible only for lattices narrower than a channel, is read from ChanD).
 struct ChanF {
     float su, sv;
     int32_t j0, nb;
-    float w[4];
+    float w0, w1;
+    float nuc_hi, nuc_lo;
 };
 
 // Per channel, exact FP64 values (64 B): s_k = fl(nu_k gu) as the cell rule
@@ -58,24 +62,22 @@ struct SrcDev {
     int64_t rec_off;        // first row record of this window
 };
 
-// Per (row, chunk) record written by the mixed path's FP64 pre-pass (48 B).
-//   t0          frac(tau nu_c0 / c), turns, nu_c0 = first channel of the chunk
-//   dhi, dlo    D = frac(tau step / c) split so that lane * dhi is exact
-//               (dhi has at most 19 significant bits), dlo = D - dhi
-//   sre, sim    exp(2 pi i frac(32 D)): the lane-to-lane stride of the
-//               per-lane recurrence
-//   u, v        fl32 of the (folded) uvw, metres
-//   rowf        row index | (fold << 31)
-//   W[4]        the row's weights; for windows with at most two pols W[3]
-//               instead holds (as int bits) the uv cell shared by every
-//               channel of the chunk, -1 if that cell is off the grid, or
-//               CELL_MIXED if the chunk's channels fall in different cells
-// For windows without a linear axis, dhi/dlo carry the bits of tau (FP64).
+// Per-row record written by the mixed path's FP64 pre-pass (64 B), in
+// processing order.
+//   tau_hi + tau_lo  the delay tau (metres) as a float-float pair, so that
+//                    tau * nu_k / c is formed to ~1e-14 relative in FP32
+//   u, v             fl32 of the (folded) uvw, metres
+//   rowf             row index | (fold << 31)
+//   W[4]             the row's weights
+//   cell[c]          for channel chunks c < REC_CELLS: the uv cell shared by
+//                    every channel of the chunk, -1 if that cell is off the
+//                    grid, CELL_MIXED if the chunk spans several cells
+constexpr int REC_CELLS = 7;
 struct __align__(16) RowRec {
-    float t0, dhi, dlo, sre;
-    float sim, u, v;
+    float tau_hi, tau_lo, u, v;
     uint32_t rowf;
     float W[4];
+    int32_t cell[REC_CELLS];
 };
 
 // One unit of stacking work: rows [q0, q1) (in processing order) of window

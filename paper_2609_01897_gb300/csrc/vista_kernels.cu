@@ -9,8 +9,8 @@
 
 namespace vista {
 
-// Debug export: the same seed/recurrence/cell code as stack_mixed, writing
-// the phasor and the cell of every (row, channel) of one window.
+// Debug export: the same phasor and cell code as stack_mixed, writing the
+// phasor and the cell of every (row, channel) of one window.
 template <int NS>
 __global__ void debug_mixed(RunArgs a, int src, double *ph_out, int32_t *cell_out)
 {
@@ -22,31 +22,19 @@ __global__ void debug_mixed(RunArgs a, int src, double *ph_out, int32_t *cell_ou
     const int chunk = (int)(task / nrow);
     const int64_t i = task % nrow;
     const int c0 = S.k_lo + chunk * 32 * NS;
-    const RowRec rec = a.recs[S.rec_off + (int64_t)chunk * nrow + i];
+    const RowRec rec = a.recs[S.rec_off + i];
     const int64_t row = (int64_t)(rec.rowf & 0x7fffffffu);
     const bool fold = (rec.rowf >> 31) != 0;
-    const bool linear = S.linear != 0;
-    float2 ph = make_float2(1.f, 0.f);
-    double tau = 0.0;
-    if (linear)
-        ph = lane_seed(rec, lane);
-    else
-        tau = __hiloint2double(__float_as_int(rec.dhi), __float_as_int(rec.dlo));
-    const float2 stp = make_float2(rec.sre, rec.sim);
 #pragma unroll
     for (int q = 0; q < NS; ++q) {
         const int k = c0 + q * 32 + lane;
         if (k < S.k_hi) {
             const ChanD *cd = a.chd + S.chan_off + (k - S.k_lo);
             const ChanF cf = a.chf[S.chan_off + (k - S.k_lo)];
-            if (!linear) {
-                double t = tau * (cd->nu * (1.0 / C_LIGHT));
-                t -= floor(t);
-                ph = turns_to_phasor((float)t);
-            }
+            const float2 ph = shift_phasor(rec.tau_hi, rec.tau_lo, cf.nuc_hi, cf.nuc_lo);
             // same cell path as the stacking kernel: the chunk's shared cell
             // from the pre-pass when there is one, else per channel
-            const int cinfo = S.npol <= 2 ? __float_as_int(rec.W[3]) : CELL_MIXED;
+            const int cinfo = chunk < REC_CELLS ? rec.cell[chunk] : CELL_MIXED;
             int iu, iv;
             if (cinfo != CELL_MIXED) {
                 iu = cinfo < 0 ? -1 : cinfo % a.g.nu;
@@ -66,7 +54,6 @@ __global__ void debug_mixed(RunArgs a, int src, double *ph_out, int32_t *cell_ou
                 cell_out[2 * o + 1] = ok ? iv : -1;
             }
         }
-        if (linear) ph = cmul(ph, stp);
     }
 }
 

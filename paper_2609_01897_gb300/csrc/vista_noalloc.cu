@@ -129,10 +129,12 @@ extern "C" int vista_stack_noalloc(const vista_cube_desc *c, const vista_source_
         f.sv = (float)d.sv;
         f.j0 = d.j0;
         f.nb = d.nb;
-        for (int b = 0; b < VISTA_MAX_BINS; ++b) {
-            d.w[b] = w[(size_t)k * VISTA_MAX_BINS + b];
-            f.w[b] = (float)d.w[b];
-        }
+        for (int b = 0; b < VISTA_MAX_BINS; ++b) d.w[b] = w[(size_t)k * VISTA_MAX_BINS + b];
+        f.w0 = (float)d.w[0];
+        f.w1 = (float)d.w[1];
+        const double nuc = d.nu / C_LIGHT;
+        f.nuc_hi = (float)nuc;
+        f.nuc_lo = (float)(nuc - (double)f.nuc_hi);
         if (std::fabs(d.nu) > fbest) {
             fbest = std::fabs(d.nu);
             key_ch = k;
@@ -172,7 +174,7 @@ extern "C" int vista_stack_noalloc(const vista_cube_desc *c, const vista_source_
     const size_t o_chd = o;
     o += al256(sizeof(ChanD) * (size_t)nin);
     const size_t o_rec = o;
-    o += al256(sizeof(RowRec) * (size_t)nrow * (size_t)nchunk);
+    o += al256(sizeof(RowRec) * (size_t)nrow);
     const size_t o_hist = o;
     o += al256(4 * (size_t)nstripe);
     const size_t o_qs = o;

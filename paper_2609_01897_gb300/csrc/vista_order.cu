@@ -221,55 +221,35 @@ __global__ void __launch_bounds__(256) k_records(RunArgs a)
     const bool fold = a.g.fold && (v < 0.0 || (v == 0.0 && u < 0.0));
     const double tau = u * S.l + v * S.m + wz * S.n1;
     RowRec rec;
+    split_ff(tau, rec.tau_hi, rec.tau_lo);
     rec.u = (float)(fold ? -u : u);
     rec.v = (float)(fold ? -v : v);
     rec.rowf = (uint32_t)r | (fold ? 0x80000000u : 0u);
 #pragma unroll
     for (int k = 0; k < 4; ++k) rec.W[k] = k < S.npol ? S.wts[r * S.npol + k] : 0.0f;
-    if (S.linear) {
-        double D = tau * S.step_c;
-        D -= floor(D);
-        const double Dhi = floor(D * 524288.0) * (1.0 / 524288.0);
-        rec.dhi = (float)Dhi;
-        rec.dlo = (float)(D - Dhi);
-        double D32 = 32.0 * D;
-        D32 -= floor(D32);
-        const float2 st = turns_to_phasor((float)D32);
-        rec.sre = st.x;
-        rec.sim = st.y;
-    } else {
-        rec.dhi = __int_as_float(__double2hiint(tau));
-        rec.dlo = __int_as_float(__double2loint(tau));
-        rec.sre = 1.0f;
-        rec.sim = 0.0f;
-    }
+    // The cell index is monotone in frequency along a row, so equal cells at a
+    // chunk's two end channels hold for every channel between them.
     const ChanD *cd = a.chd + S.chan_off;
     const ChanF *cf = a.chf + S.chan_off;
     const int nin = S.k_hi - S.k_lo;
-    RowRec *out = a.recs + S.rec_off + q;
-    for (int c = 0; c < S.nchunk; ++c) {
-        double t = tau * (cd[c * a.cw].nu * (1.0 / C_LIGHT));
-        t -= floor(t);
-        rec.t0 = (float)t;
-        if (S.npol <= 2) {
-            // The cell index is monotone in frequency along a row, so equal
-            // cells at the chunk's two end channels hold for every channel
-            // between them.
+#pragma unroll
+    for (int c = 0; c < REC_CELLS; ++c) {
+        int info = CELL_MIXED;
+        if (c < S.nchunk) {
             const int e0 = c * a.cw, e1 = min(nin, (c + 1) * a.cw) - 1;
             const float fu0 = axis_floor(rec.u, cf[e0].su, uvw, fold, &cd[e0].su);
             const float fu1 = axis_floor(rec.u, cf[e1].su, uvw, fold, &cd[e1].su);
             const float fv0 = axis_floor(rec.v, cf[e0].sv, uvw + 1, fold, &cd[e0].sv);
             const float fv1 = axis_floor(rec.v, cf[e1].sv, uvw + 1, fold, &cd[e1].sv);
-            int info = CELL_MIXED;
             if (fu0 == fu1 && fv0 == fv1) {
                 const float hu = (float)(a.g.nu >> 1), hv = (float)(a.g.nv >> 1);
                 const bool in = fu0 >= -hu && fu0 < hu && fv0 >= -hv && fv0 < hv;
                 info = in ? ((int)fv0 + (a.g.nv >> 1)) * a.g.nu + ((int)fu0 + (a.g.nu >> 1)) : -1;
             }
-            rec.W[3] = __int_as_float(info);
         }
-        out[(int64_t)c * S.nrow] = rec;
+        rec.cell[c] = info;
     }
+    a.recs[S.rec_off + q] = rec;
 }
 
 cudaError_t launch_prepare(const RunArgs &a, cudaStream_t st)

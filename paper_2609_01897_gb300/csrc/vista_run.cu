@@ -64,10 +64,12 @@ int plan_source(vista_stack *h, const SrcHost &s, double gu, double gv, Plan &pl
         f.sv = (float)d.sv;
         f.j0 = d.j0;
         f.nb = d.nb;
-        for (int b = 0; b < VISTA_MAX_BINS; ++b) {
-            d.w[b] = w[(size_t)k * VISTA_MAX_BINS + b];
-            f.w[b] = (float)d.w[b];
-        }
+        for (int b = 0; b < VISTA_MAX_BINS; ++b) d.w[b] = w[(size_t)k * VISTA_MAX_BINS + b];
+        f.w0 = (float)d.w[0];
+        f.w1 = (float)d.w[1];
+        const double nuc = d.nu / C_LIGHT;   // nu_k / c as a float-float pair
+        f.nuc_hi = (float)nuc;
+        f.nuc_lo = (float)(nuc - (double)f.nuc_hi);
         if (std::fabs(d.nu) > fbest) {
             fbest = std::fabs(d.nu);
             pl.key_ch = k;
@@ -298,7 +300,7 @@ extern "C" int vista_run(vista_stack *h)
             d.key_su = (float)(s.freqs[(size_t)pl.key_ch] * gu);
             d.key_sv = (float)(s.freqs[(size_t)pl.key_ch] * gv);
             d.rec_off = rec_total;
-            if (!fp64) rec_total += (int64_t)d.nchunk * d.nrow;
+            if (!fp64) rec_total += d.nrow;
             {
                 int64_t nread = 0, npm = 0;
                 for (const ChanF &f : pl.chf) nread += f.nb > 0;

@@ -73,7 +73,7 @@ __global__ void __launch_bounds__(256) stack_mixed(RunArgs a)
         const Item item = a.so.items[it];
         if (lane == 0) {
             const SrcDev &S = a.srcs[item.w];
-            const RowRec *src = a.recs + S.rec_off + (int64_t)item.chunk * S.nrow + item.q0;
+            const RowRec *src = a.recs + S.rec_off + item.q0;
             const uint32_t bytes = (uint32_t)(item.q1 - item.q0) * (uint32_t)sizeof(RowRec);
             fence_proxy_async();
             mbar_expect_tx(&bars[s], bytes);
@@ -109,7 +109,6 @@ __global__ void __launch_bounds__(256) stack_mixed(RunArgs a)
         int64_t vstride;
         float vscale;
         int k_lo, k_hi, chan_off;
-        bool linear;
         int plane[P];
         {
             const SrcDev &G = a.srcs[item.w];
@@ -121,7 +120,6 @@ __global__ void __launch_bounds__(256) stack_mixed(RunArgs a)
             k_lo = G.k_lo;
             k_hi = G.k_hi;
             chan_off = G.chan_off;
-            linear = G.linear != 0;
             const int c0g = G.k_lo + item.chunk * 32 * NS;
             vis = reinterpret_cast<const char *>(G.vis) +
                   (int64_t)(c0g + lane - G.kbase) * P * (int64_t)VisLoad<P, VT>::kBytes;
@@ -132,21 +130,25 @@ __global__ void __launch_bounds__(256) stack_mixed(RunArgs a)
         const int c0 = k_lo + item.chunk * 32 * NS;
         const bool pack2 = (P == 2) && plane[0] >= 0 && plane[1] == plane[0] + 1 && !(plane[0] & 1) && !(npol_c & 1);
 
-        // per channel slot: fl32(s_k) and whether the channel has a rest bin
-        float su[NS], sv[NS];
+        // per channel slot: fl32(s_k), nu_k / c as float-float, and whether the
+        // channel has a rest bin
+        float su[NS], sv[NS], nh[NS], nl[NS];
         bool act[NS];
 #pragma unroll
         for (int q = 0; q < NS; ++q) {
             const int k = c0 + q * 32 + lane;
             act[q] = false;
-            su[q] = sv[q] = 0.f;
+            su[q] = sv[q] = nh[q] = nl[q] = 0.f;
             if (k < k_hi) {
                 const ChanF cf = a.chf[chan_off + (k - k_lo)];
                 su[q] = cf.su;
                 sv[q] = cf.sv;
+                nh[q] = cf.nuc_hi;
+                nl[q] = cf.nuc_lo;
                 act[q] = cf.nb > 0;
             }
         }
+        const int cslot = item.chunk < REC_CELLS ? item.chunk : -1;
         int cell[NS];
         float4 acc[NS][P];
         uint32_t cnt[NS][P];
@@ -189,7 +191,7 @@ __global__ void __launch_bounds__(256) stack_mixed(RunArgs a)
                 const ChanF cf = a.chf[st.chf];
                 const size_t base = ((size_t)st.cell * nrest + cf.j0) * npol_c;
                 for (int b = 0; b < cf.nb; ++b) {
-                    const float ww = cf.w[b];
+                    const float ww = b == 0 ? cf.w0 : b == 1 ? cf.w1 : (float)a.chd[st.chf].w[b];
                     const size_t e2 = base + (size_t)b * npol_c;
 #pragma unroll
                     for (int p = 0; p < P; ++p) {
@@ -252,19 +254,13 @@ __global__ void __launch_bounds__(256) stack_mixed(RunArgs a)
                 const uint32_t rowf = rec.rowf;
                 const int64_t row = (int64_t)(rowf & 0x7fffffffu);
                 const bool fold = (rowf >> 31) != 0;
-                float2 ph = make_float2(1.f, 0.f);
-                if (linear) ph = lane_seed(rec, lane);
-                // the chunk's shared cell, if the pre-pass found one (<= 2 pols)
-                const int cinfo = P <= 2 ? __float_as_int(rec.W[3]) : CELL_MIXED;
+                const float th = rec.tau_hi, tl = rec.tau_lo;
+                // the chunk's shared cell, if the pre-pass found one
+                const int cinfo = cslot >= 0 ? rec.cell[cslot] : CELL_MIXED;
 #pragma unroll
                 for (int q = 0; q < NS; ++q) {
                     const int k = c0 + q * 32 + lane;
-                    if (!linear && k < k_hi) {
-                        const double tau = __hiloint2double(__float_as_int(rec.dhi), __float_as_int(rec.dlo));
-                        double t = tau * (a.chd[chan_off + (k - k_lo)].nu * (1.0 / C_LIGHT));
-                        t -= floor(t);
-                        ph = turns_to_phasor((float)t);
-                    }
+                    const float2 ph = shift_phasor(th, tl, nh[q], nl[q]);
                     int cid = cell[q];
                     if (act[q]) {
                         if (cinfo != CELL_MIXED) {
@@ -312,7 +308,6 @@ __global__ void __launch_bounds__(256) stack_mixed(RunArgs a)
                             }
                         }
                     }
-                    if (linear && q + 1 < NS) ph = cmul(ph, make_float2(rec.sre, rec.sim));
                 }
             }
         }
