@@ -269,8 +269,8 @@ int vista_debug_order(vista_stack *h, int32_t src, int32_t *dst);
  *   count   caller's device array [nv][nu][nrest][npol] uint32, added to.
  *
  * Returns after the work has finished.  E_RANGE when the window needs more
- * scratch than the array holds (about 90 bytes per row: a 64-byte row
- * record plus the row ordering, i.e. up to ~90 000 rows).  The first call on a device looks up
+ * scratch than the array holds (about 75 bytes per row: a 48-byte row
+ * record plus the row ordering, i.e. up to ~110 000 rows).  The first call on a device looks up
  * the array's device address, so make that first call before any stream
  * capture.  All calls share the array: calls whose device work overlaps
  * (other host threads, other streams) race on it and must not be made;

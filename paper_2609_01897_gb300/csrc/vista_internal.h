@@ -62,7 +62,7 @@ struct SrcDev {
     int64_t rec_off;        // first row record of this window
 };
 
-// Per-row record written by the mixed path's FP64 pre-pass (64 B), in
+// Per-row record written by the mixed path's FP64 pre-pass (48 B), in
 // processing order.
 //   tau_hi + tau_lo  the delay tau (metres) as a float-float pair, so that
 //                    tau * nu_k / c is formed to ~1e-14 relative in FP32
@@ -72,7 +72,7 @@ struct SrcDev {
 //   cell[c]          for channel chunks c < REC_CELLS: the uv cell shared by
 //                    every channel of the chunk, -1 if that cell is off the
 //                    grid, CELL_MIXED if the chunk spans several cells
-constexpr int REC_CELLS = 7;
+constexpr int REC_CELLS = 3;
 struct __align__(16) RowRec {
     float tau_hi, tau_lo, u, v;
     uint32_t rowf;
