@@ -21,12 +21,7 @@
 namespace vista {
 
 constexpr int RB_MAX = 256;     // largest item (rows) the shared-memory buffers hold
-// Blocks of at most 4 warps; with one channel per lane at least 5 resident
-// blocks per SM (a 102-register budget, 20 warps per SM), with more channels
-// per lane 3 (170 registers).
-constexpr int KMAX_THREADS = 128;
-template <int NS>
-constexpr int kmin_blocks() { return NS == 1 ? 5 : 3; }
+constexpr int KMAX_THREADS = 256;   // blocks of at most 8 warps
 constexpr int STAGE_CAP = 96;   // staged runs per warp
 
 // One finished run of one channel slot.
@@ -45,7 +40,7 @@ __host__ __device__ constexpr size_t warp_smem_bytes(int rb)
 }
 
 template <int P, int VT, int NS, int D>
-__global__ void __launch_bounds__(KMAX_THREADS, kmin_blocks<NS>()) stack_mixed(RunArgs a)
+__global__ void __launch_bounds__(KMAX_THREADS) stack_mixed(RunArgs a)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
