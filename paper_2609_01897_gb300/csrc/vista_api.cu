@@ -451,6 +451,7 @@ extern "C" int vista_close(vista_stack *h)
     h->b_chf.release();
     h->b_chd.release();
     h->b_recs.release();
+    h->b_cells.release();
     h->b_off.release();
     h->b_stage.release();
     h->b_unpack.release();

@@ -79,34 +79,16 @@ __device__ __forceinline__ float2 cmul(float2 a, float2 b)
     return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
 }
 
-// exp(2 pi i t) for t in turns, for |t| < 2^21.
-//
-// Own evaluation (textbook quadrant reduction + Taylor series): x = 4t is
-// split into the nearest integer q (quadrant) and r in [-1/2, 1/2]
-// (exact: Sterbenz), theta = r pi/2 in [-pi/4, pi/4], then
-//   sin theta = theta (1 - theta^2/3! + theta^4/5! - theta^6/7! + theta^8/9!)
-//   cos theta = 1 - theta^2/2! + theta^4/4! - theta^6/6! + theta^8/8!
-// whose truncation errors on |theta| <= pi/4 are below 2e-9 and 3e-8, and
-// finally exp(i (q pi/2 + theta)) by rotating (cos, sin) q quarter turns.
-// The phase error is a few 1e-8 rad, far inside the 1e-5 rad budget.
+// exp(2 pi i t) for a reduced turn count |t| <= 1/2 (|2 pi t| <= pi).
+// CUDA's __sincosf has an absolute error of at most 2^-21.41 on [-pi, pi]
+// (CUDA C Programming Guide, intrinsic functions), i.e. a phase error below
+// 5e-7 rad, inside the 1e-5 rad budget, in two special-function-unit
+// instructions.
 __device__ __forceinline__ float2 turns_to_phasor(float t)
 {
-    const float x = 4.0f * t;                 // exact
-    const float q = rintf(x);
-    const float r = __fsub_rn(x, q);          // exact, |r| <= 1/2
-    const float th = r * 1.57079632679489662f;
-    const float t2 = th * th;
-    float s = __fmaf_rn(t2, 2.75573192e-06f, -1.98412698e-04f);   // 1/9!, -1/7!
-    s = __fmaf_rn(t2, s, 8.33333333e-03f);                          // 1/5!
-    s = __fmaf_rn(t2, s, -1.66666667e-01f);                         // -1/3!
-    s = __fmaf_rn(t2 * th, s, th);
-    float c = __fmaf_rn(t2, 2.48015873e-05f, -1.38888889e-03f);    // 1/8!, -1/6!
-    c = __fmaf_rn(t2, c, 4.16666667e-02f);                          // 1/4!
-    c = __fmaf_rn(t2, c, -0.5f);
-    c = __fmaf_rn(t2, c, 1.0f);
-    const int qi = ((int)q) & 3;
-    const float cs = (qi & 1) ? s : c, sn = (qi & 1) ? c : s;
-    return make_float2((qi == 1 || qi == 2) ? -cs : cs, (qi >= 2) ? -sn : sn);
+    float s, c;
+    __sincosf(__fmul_rn(t, 6.28318530717958648f), &s, &c);
+    return make_float2(c, s);
 }
 
 // exp(+2 pi i tau nu_k / c) from tau and nu_k / c given as float-float
@@ -171,6 +153,31 @@ __device__ __forceinline__ int axis_cell64(double c, double s, int n)
     double h = (double)(n >> 1);
     if (!(x >= -h && x < h)) return -1;
     return (int)floor(x) + (n >> 1);
+}
+
+// The cell iv * nu + iu of channel `cd` of one row by the FP64 rule, -1 off
+// the grid (the fall-back of CC_MIXED chunks; out of line, rarely run).
+static __device__ __noinline__ int cell_exact(const double *uvw, int64_t row, bool fold, const ChanD *cd, int nu,
+                                              int nv)
+{
+    double u = uvw[3 * row], v = uvw[3 * row + 1];
+    if (fold) {
+        u = -u;
+        v = -v;
+    }
+    const int iu = axis_cell64(u, cd->su, nu), iv = axis_cell64(v, cd->sv, nv);
+    return (iu >= 0 && iv >= 0) ? iv * nu + iu : -1;
+}
+
+// Cell of chunk-local channel kk from a chunk-cell entry that is neither
+// CC_NOCHANGE nor CC_MIXED.
+__device__ __forceinline__ int chunk_cell_step(int2 cc, int kk, int nu)
+{
+    const uint32_t m = (uint32_t)cc.y;
+    int c = cc.x;
+    if (kk >= (int)(m & 0xffu)) c += (m & 0x10000u) ? -1 : 1;
+    if (kk >= (int)((m >> 8) & 0xffu)) c += (m & 0x20000u) ? -nu : nu;
+    return c;
 }
 
 // ----------------------------------------------------------- vis loaders
@@ -270,6 +277,61 @@ struct VisLoad<P, VISTA_VIS_BF16X2> {
             v[1] = cvt(q.y, scale);
             v[2] = cvt(q.z, scale);
             v[3] = cvt(q.w, scale);
+        }
+    }
+};
+
+// ---- asynchronous copies of one lane's visibilities into shared memory ----
+
+__device__ __forceinline__ void cp_async_16(uint32_t dst, const void *src)
+{
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_8(uint32_t dst, const void *src)
+{
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(dst), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_4(uint32_t dst, const void *src)
+{
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(dst), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
+// One lane's P values of one (row, channel): kLaneBytes bytes, naturally
+// aligned (a multiple of the element size), copied by cp.async in 16-, 8- or
+// 4-byte pieces and decoded from shared memory.
+template <int P, int VT>
+struct VisAsync {
+    static constexpr int kLaneBytes = P * VisLoad<P, VT>::kBytes;
+    static __device__ __forceinline__ void copy(uint32_t dst, const void *src)
+    {
+        const char *s = reinterpret_cast<const char *>(src);
+        if constexpr (kLaneBytes % 16 == 0) {
+#pragma unroll
+            for (int i = 0; i < kLaneBytes / 16; ++i) cp_async_16(dst + 16 * i, s + 16 * i);
+        } else if constexpr (kLaneBytes == 8) {
+            cp_async_8(dst, s);
+        } else {
+            static_assert(kLaneBytes == 4, "lane bytes");
+            cp_async_4(dst, s);
+        }
+    }
+    static __device__ __forceinline__ void decode(const void *sm, float scale, float2 (&v)[P])
+    {
+        if constexpr (VT == VISTA_VIS_C64) {
+            const float2 *q = reinterpret_cast<const float2 *>(sm);
+#pragma unroll
+            for (int i = 0; i < P; ++i) v[i] = q[i];
+        } else if constexpr (VT == VISTA_VIS_C128) {
+            const double2 *q = reinterpret_cast<const double2 *>(sm);
+#pragma unroll
+            for (int i = 0; i < P; ++i) v[i] = make_float2((float)q[i].x, (float)q[i].y);
+        } else {
+            const uint32_t *q = reinterpret_cast<const uint32_t *>(sm);
+#pragma unroll
+            for (int i = 0; i < P; ++i) v[i] = VisLoad<P, VT>::cvt(q[i], scale);
         }
     }
 };

@@ -70,7 +70,7 @@ struct vista_stack {
     vista::DevStats *stats = nullptr;
     uint64_t host_nvis = 0;   // visibilities read, counted from the channel tables at each run
     int32_t *err = nullptr;
-    vista::DevBuf b_srcs, b_chf, b_chd, b_recs, b_off, b_stage, b_unpack, b_sort;
+    vista::DevBuf b_srcs, b_chf, b_chd, b_recs, b_cells, b_off, b_stage, b_unpack, b_sort;
     std::vector<vista::ClassRun> classes;
     vista::LaunchCfg cfg{64, 1, 4, 1, 2};
     // stripe geometry of the row ordering (depends on the cube only)

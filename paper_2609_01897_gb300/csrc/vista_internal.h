@@ -10,7 +10,6 @@ namespace vista {
 
 constexpr double C_LIGHT = 299792458.0;   // m/s
 constexpr int MAX_LOCAL_KEYS = 4096;      // cell keys inside one stripe (shared-memory histogram)
-constexpr int CELL_MIXED = -2;            // a chunk's channels fall in more than one uv cell
 
 // Cube geometry as the kernels see it.
 struct CubeGeom {
@@ -60,25 +59,35 @@ struct SrcDev {
     int32_t pad;
     float key_su, key_sv;   // fl32(s_k) at the row-ordering reference channel
     int64_t rec_off;        // first row record of this window
+    int64_t cell_off;       // first chunk-cell entry of this window ([chunk][row] inside)
 };
 
-// Per-row record written by the mixed path's FP64 pre-pass (48 B), in
+// Per-row record written by the mixed path's FP64 pre-pass (32 B), in
 // processing order.
 //   tau_hi + tau_lo  the delay tau (metres) as a float-float pair, so that
 //                    tau * nu_k / c is formed to ~1e-14 relative in FP32
-//   u, v             fl32 of the (folded) uvw, metres
 //   rowf             row index | (fold << 31)
-//   W[4]             the row's weights
-//   cell[c]          for channel chunks c < REC_CELLS: the uv cell shared by
-//                    every channel of the chunk, -1 if that cell is off the
-//                    grid, CELL_MIXED if the chunk spans several cells
-constexpr int REC_CELLS = 3;
+//   W[4]             the row's weights, negated for a folded row (the sign
+//                    conjugates the shifted visibility; |W| is the weight)
 struct __align__(16) RowRec {
-    float tau_hi, tau_lo, u, v;
+    float tau_hi, tau_lo;
     uint32_t rowf;
     float W[4];
-    int32_t cell[REC_CELLS];
+    uint32_t pad;
 };
+
+// uv cells of one (row, channel chunk), written by the pre-pass (8 B):
+//   x  the cell iv * nu + iu at the chunk's first channel, -1 off the grid
+//   y  CC_NOCHANGE: every channel of the chunk shares x;
+//      CC_MIXED: the chunk needs the per-channel FP64 rule;
+//      else bits 0-7 / 8-15: chunk-local channel at which iu / iv steps
+//      (255 = never), bit 16 / 17: that step is -1 (else +1).
+// The cell index of a row is monotone in frequency along each axis, so a
+// chunk whose end channels differ by at most one cell per axis, both ends on
+// the grid, steps at most once per axis; every other chunk is CC_MIXED
+// (or, off the grid at both ends of one axis, x = -1 with CC_NOCHANGE).
+constexpr int32_t CC_NOCHANGE = 0x0000ffff;
+constexpr int32_t CC_MIXED = -1;
 
 // One unit of stacking work: rows [q0, q1) (in processing order) of window
 // w, channel chunk c.
@@ -129,6 +138,7 @@ struct RunArgs {
     const ChanF *chf;
     const ChanD *chd;
     RowRec *recs;
+    int2 *ccells;               // chunk cells (+ 2 entries of padding for the bulk copies)
     const int64_t *row_off;     // [nsrc+1] cumulative rows
     int64_t nrows_total;
     CubeGeom g;

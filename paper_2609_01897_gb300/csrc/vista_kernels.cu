@@ -23,26 +23,25 @@ __global__ void debug_mixed(RunArgs a, int src, double *ph_out, int32_t *cell_ou
     const int64_t i = task % nrow;
     const int c0 = S.k_lo + chunk * 32 * NS;
     const RowRec rec = a.recs[S.rec_off + i];
+    const int2 cc = a.ccells[S.cell_off + (int64_t)chunk * nrow + i];
     const int64_t row = (int64_t)(rec.rowf & 0x7fffffffu);
     const bool fold = (rec.rowf >> 31) != 0;
 #pragma unroll
     for (int q = 0; q < NS; ++q) {
-        const int k = c0 + q * 32 + lane;
+        const int kk = q * 32 + lane, k = c0 + kk;
         if (k < S.k_hi) {
             const ChanD *cd = a.chd + S.chan_off + (k - S.k_lo);
             const ChanF cf = a.chf[S.chan_off + (k - S.k_lo)];
             const float2 ph = shift_phasor(rec.tau_hi, rec.tau_lo, cf.nuc_hi, cf.nuc_lo);
-            // same cell path as the stacking kernel: the chunk's shared cell
-            // from the pre-pass when there is one, else per channel
-            const int cinfo = chunk < REC_CELLS ? rec.cell[chunk] : CELL_MIXED;
-            int iu, iv;
-            if (cinfo != CELL_MIXED) {
-                iu = cinfo < 0 ? -1 : cinfo % a.g.nu;
-                iv = cinfo < 0 ? -1 : cinfo / a.g.nu;
-            } else {
-                iu = axis_cell(rec.u, cf.su, S.uvw + 3 * row, fold, &cd->su, a.g.nu);
-                iv = axis_cell(rec.v, cf.sv, S.uvw + 3 * row + 1, fold, &cd->sv, a.g.nv);
-            }
+            // same cell path as the stacking kernel
+            int cid;
+            if (cc.y == CC_NOCHANGE)
+                cid = cc.x;
+            else if (cc.y != CC_MIXED)
+                cid = chunk_cell_step(cc, kk, a.g.nu);
+            else
+                cid = cell_exact(S.uvw, row, fold, cd, a.g.nu, a.g.nv);
+            const int iu = cid < 0 ? -1 : cid % a.g.nu, iv = cid < 0 ? -1 : cid / a.g.nu;
             const int64_t o = row * S.nchan + k;
             if (ph_out) {
                 ph_out[2 * o] = (double)ph.x;

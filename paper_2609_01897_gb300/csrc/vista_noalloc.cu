@@ -175,6 +175,8 @@ extern "C" int vista_stack_noalloc(const vista_cube_desc *c, const vista_source_
     o += al256(sizeof(ChanD) * (size_t)nin);
     const size_t o_rec = o;
     o += al256(sizeof(RowRec) * (size_t)nrow);
+    const size_t o_cells = o;
+    o += al256(sizeof(int2) * ((size_t)nrow * (size_t)nchunk + 2));
     const size_t o_hist = o;
     o += al256(4 * (size_t)nstripe);
     const size_t o_qs = o;
@@ -229,6 +231,7 @@ extern "C" int vista_stack_noalloc(const vista_cube_desc *c, const vista_source_
     d.key_su = (float)(s->freqs[key_ch] * gu);
     d.key_sv = (float)(s->freqs[key_ch] * gv);
     d.rec_off = 0;
+    d.cell_off = 0;
     const int64_t roff[2] = {0, nrow};
 
     // tables into scratch; counters and the error word start at zero
@@ -247,6 +250,7 @@ extern "C" int vista_stack_noalloc(const vista_cube_desc *c, const vista_source_
     a.chf = (const ChanF *)(b + o_chf);
     a.chd = (const ChanD *)(b + o_chd);
     a.recs = (RowRec *)(b + o_rec);
+    a.ccells = (int2 *)(b + o_cells);
     a.row_off = (const int64_t *)(b + o_off);
     a.nrows_total = nrow;
     a.g = CubeGeom{c->nu, c->nv, c->nrest, c->npol, gu, gv, c->hermitian_fold, 0};

@@ -12,9 +12,9 @@
 //                  stripe-major order (item = rows of one bucket x one chunk)
 //   k_scatter      rows grouped by bucket
 //   k_bucket_sort  one block per bucket: counting sort by local cell key
-//   k_records      FP64 delay, phase seeds and recurrence stride of every
-//                  (row, chunk), written in processing order (paper Eq. 2 and
-//                  the phasor recurrence of Sec. 3.2)
+//   k_records      per row, in processing order: the FP64 delay of Eq. 2 as
+//                  a float-float pair and the (fold-signed) weights; per
+//                  (row, channel chunk): the chunk's uv cells
 #include "vista_device.cuh"
 
 namespace vista {
@@ -208,6 +208,23 @@ __global__ void __launch_bounds__(256) k_bucket_sort(RunArgs a)
     }
 }
 
+// First chunk-local channel in (lo, hi] whose floor(coord * s) differs from
+// f_lo (the cell is monotone in frequency; hi is known to differ).
+__device__ int axis_step(float c32, const ChanF *cf, const ChanD *cd, int e0, int lo, int hi, const double *coord64,
+                         bool neg, bool v_axis, float f_lo)
+{
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        const float f = v_axis ? axis_floor(c32, cf[e0 + mid].sv, coord64, neg, &cd[e0 + mid].sv)
+                               : axis_floor(c32, cf[e0 + mid].su, coord64, neg, &cd[e0 + mid].su);
+        if (f == f_lo)
+            lo = mid;
+        else
+            hi = mid;
+    }
+    return hi;
+}
+
 __global__ void __launch_bounds__(256) k_records(RunArgs a)
 {
     const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -222,34 +239,53 @@ __global__ void __launch_bounds__(256) k_records(RunArgs a)
     const double tau = u * S.l + v * S.m + wz * S.n1;
     RowRec rec;
     split_ff(tau, rec.tau_hi, rec.tau_lo);
-    rec.u = (float)(fold ? -u : u);
-    rec.v = (float)(fold ? -v : v);
     rec.rowf = (uint32_t)r | (fold ? 0x80000000u : 0u);
 #pragma unroll
-    for (int k = 0; k < 4; ++k) rec.W[k] = k < S.npol ? S.wts[r * S.npol + k] : 0.0f;
-    // The cell index is monotone in frequency along a row, so equal cells at a
-    // chunk's two end channels hold for every channel between them.
+    for (int k = 0; k < 4; ++k) {
+        const float wk = k < S.npol ? S.wts[r * S.npol + k] : 0.0f;
+        rec.W[k] = fold ? -wk : wk;
+    }
+    rec.pad = 0;
+    a.recs[S.rec_off + q] = rec;
+
+    // Chunk cells.  The cell index is monotone in frequency along each axis,
+    // so the cells at a chunk's two end channels bound every channel between.
+    const float uf = (float)(fold ? -u : u), vf = (float)(fold ? -v : v);
     const ChanD *cd = a.chd + S.chan_off;
     const ChanF *cf = a.chf + S.chan_off;
     const int nin = S.k_hi - S.k_lo;
-#pragma unroll
-    for (int c = 0; c < REC_CELLS; ++c) {
-        int info = CELL_MIXED;
-        if (c < S.nchunk) {
-            const int e0 = c * a.cw, e1 = min(nin, (c + 1) * a.cw) - 1;
-            const float fu0 = axis_floor(rec.u, cf[e0].su, uvw, fold, &cd[e0].su);
-            const float fu1 = axis_floor(rec.u, cf[e1].su, uvw, fold, &cd[e1].su);
-            const float fv0 = axis_floor(rec.v, cf[e0].sv, uvw + 1, fold, &cd[e0].sv);
-            const float fv1 = axis_floor(rec.v, cf[e1].sv, uvw + 1, fold, &cd[e1].sv);
-            if (fu0 == fu1 && fv0 == fv1) {
-                const float hu = (float)(a.g.nu >> 1), hv = (float)(a.g.nv >> 1);
-                const bool in = fu0 >= -hu && fu0 < hu && fv0 >= -hv && fv0 < hv;
-                info = in ? ((int)fv0 + (a.g.nv >> 1)) * a.g.nu + ((int)fu0 + (a.g.nu >> 1)) : -1;
+    const float hu = (float)(a.g.nu >> 1), hv = (float)(a.g.nv >> 1);
+    int2 *out = a.ccells + S.cell_off + q;
+    for (int c = 0; c < S.nchunk; ++c) {
+        const int e0 = c * a.cw, last = min(nin, e0 + a.cw) - 1 - e0;
+        const float fu0 = axis_floor(uf, cf[e0].su, uvw, fold, &cd[e0].su);
+        const float fu1 = axis_floor(uf, cf[e0 + last].su, uvw, fold, &cd[e0 + last].su);
+        const float fv0 = axis_floor(vf, cf[e0].sv, uvw + 1, fold, &cd[e0].sv);
+        const float fv1 = axis_floor(vf, cf[e0 + last].sv, uvw + 1, fold, &cd[e0 + last].sv);
+        // both ends off the grid on the same side of one axis: off throughout
+        const bool offu = (fu0 < -hu && fu1 < -hu) || (fu0 >= hu && fu1 >= hu);
+        const bool offv = (fv0 < -hv && fv1 < -hv) || (fv0 >= hv && fv1 >= hv);
+        const bool in = fu0 >= -hu && fu0 < hu && fu1 >= -hu && fu1 < hu && fv0 >= -hv && fv0 < hv &&
+                        fv1 >= -hv && fv1 < hv;
+        int2 cc;
+        if (offu || offv) {
+            cc = make_int2(-1, CC_NOCHANGE);
+        } else if (!in || fabsf(fu1 - fu0) > 1.0f || fabsf(fv1 - fv0) > 1.0f) {
+            cc = make_int2(-1, CC_MIXED);
+        } else {
+            uint32_t m = CC_NOCHANGE;
+            if (fu1 != fu0) {
+                const int b = axis_step(uf, cf, cd, e0, 0, last, uvw, fold, false, fu0);
+                m = (m & ~0xffu) | (uint32_t)b | (fu1 < fu0 ? 0x10000u : 0u);
             }
+            if (fv1 != fv0) {
+                const int b = axis_step(vf, cf, cd, e0, 0, last, uvw + 1, fold, true, fv0);
+                m = (m & ~0xff00u) | ((uint32_t)b << 8) | (fv1 < fv0 ? 0x20000u : 0u);
+            }
+            cc = make_int2(((int)fv0 + (a.g.nv >> 1)) * a.g.nu + ((int)fu0 + (a.g.nu >> 1)), (int)m);
         }
-        rec.cell[c] = info;
+        out[(int64_t)c * S.nrow] = cc;
     }
-    a.recs[S.rec_off + q] = rec;
 }
 
 cudaError_t launch_prepare(const RunArgs &a, cudaStream_t st)

@@ -224,7 +224,7 @@ extern "C" int vista_run(vista_stack *h)
     std::vector<size_t> cls_src0(classes.size()), cls_off0(classes.size());
     std::vector<SortLayout> layouts(classes.size());
     size_t sort_bytes = 0;
-    int64_t rec_total = 0;
+    int64_t rec_total = 0, cell_total = 0;
     uint64_t nvis_run = 0;
     size_t stage_pos = 0;
     const int span_copy = stage_bytes ? span_begin(h, 2) : -1;
@@ -300,7 +300,11 @@ extern "C" int vista_run(vista_stack *h)
             d.key_su = (float)(s.freqs[(size_t)pl.key_ch] * gu);
             d.key_sv = (float)(s.freqs[(size_t)pl.key_ch] * gv);
             d.rec_off = rec_total;
-            if (!fp64) rec_total += d.nrow;
+            d.cell_off = cell_total;
+            if (!fp64) {
+                rec_total += d.nrow;
+                cell_total += d.nrow * d.nchunk;
+            }
             {
                 int64_t nread = 0, npm = 0;
                 for (const ChanF &f : pl.chf) nread += f.nb > 0;
@@ -330,6 +334,9 @@ extern "C" int vista_run(vista_stack *h)
     if (!fp64) {
         if ((e = h->b_recs.ensure((size_t)(rec_total > 0 ? rec_total : 1) * sizeof(RowRec))) != cudaSuccess)
             return cuda_fail(h, e, "row record allocation");
+        // two entries of padding: a chunk-cell bulk copy may read one past the end
+        if ((e = h->b_cells.ensure((size_t)(cell_total + 2) * sizeof(int2))) != cudaSuccess)
+            return cuda_fail(h, e, "chunk cell allocation");
         if ((e = h->b_sort.ensure(sort_bytes > 0 ? sort_bytes : 256)) != cudaSuccess)
             return cuda_fail(h, e, "ordering buffer allocation");
     }
@@ -343,6 +350,7 @@ extern "C" int vista_run(vista_stack *h)
         a.chf = (const ChanF *)h->b_chf.p;
         a.chd = (const ChanD *)h->b_chd.p;
         a.recs = (RowRec *)h->b_recs.p;
+        a.ccells = (int2 *)h->b_cells.p;
         a.row_off = (const int64_t *)h->b_off.p + cls_off0[ci];
         a.g = g;
         a.cube = h->cube;

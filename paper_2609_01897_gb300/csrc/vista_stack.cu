@@ -2,66 +2,94 @@
 //
 // Persistent: every warp pops work items (one window, up to rows_per_item
 // rows in uv-cell order, a chunk of 32 x NS channels, lane = channel) from a
-// queue in stripe-major order.  Per warp, the FP64 row records of the next
-// item are fetched into shared memory by a TMA bulk copy (completing on an
-// mbarrier) while the current item is processed; inside an item the
-// visibility and flag loads run D rows ahead of the arithmetic.
+// queue in stripe-major order.  Per warp, the row records and chunk cells of
+// the next item are fetched into shared memory by TMA bulk copies
+// (completing on an mbarrier) while the current item is processed; inside an
+// item the visibility and flag loads run D rows ahead of the arithmetic.
 //
-// Per (row, channel): FP32 phasor from the record's FP64-reduced seed and
-// the lane recurrence (Sec. 3.2), guarded-FP32 uv cell that is bit-exact
-// against the FP64 cell rule, rest bins and Eq. 4 weights from the FP64
-// channel table.  Per lane, running sums over consecutive rows that share a
-// uv cell stay in registers.  When a lane's cell changes, its finished run
-// is appended to a per-warp staging area in shared memory (slots from a warp
-// ballot, no divergent branch); the warp drains the staging area together,
-// one lane per run, as float4 reductions per (cell, rest bin, pol) and one
-// count reduction per (cell, rest bin) (one u64 for a pol pair).
+// Per (row, channel): the FP32 phasor of Eq. 2 from the record's float-float
+// delay and the channel's float-float nu_k / c, the uv cell from the chunk's
+// cell entry (exact: computed by the pre-pass with the FP64 rule), rest bins
+// and Eq. 4 weights from the FP64 channel table.  Per lane, running sums
+// over consecutive rows that share a uv cell stay in registers.  When a
+// lane's cell changes, its finished run is appended to a per-warp staging
+// area in shared memory (slots from a warp ballot); the warp drains the
+// staging area together, one lane per run, as float4 reductions per (cell,
+// rest bin, pol) and one count reduction per (cell, rest bin) (one u64 for a
+// pol pair).  Runs off the grid only feed the dropped-visibility counter.
+#include <climits>
+
 #include "vista_device.cuh"
 
 namespace vista {
 
-constexpr int RB_MAX = 256;     // largest item (rows) the shared-memory buffers hold
+constexpr int RB_MAX = 256;         // largest item (rows) the shared-memory buffers hold
 constexpr int KMAX_THREADS = 256;   // blocks of at most 8 warps
-constexpr int STAGE_CAP = 96;   // staged runs per warp
+constexpr int STAGE_CAP = 96;       // staged runs per warp
+constexpr int NO_RUN = INT_MIN;     // lane holds no run
 
 // One finished run of one channel slot.
 template <int P>
 struct __align__(16) Staged {
-    int cell;         // iv * nu + iu
-    int chf;          // channel-table entry (rest bins and weights)
+    int cell;         // iv * nu + iu, -1 off the grid
+    int kk;           // chunk-local channel
     uint32_t cnt[P];
     float4 acc[P];    // sum W V'.re, sum W V'.im, sum W, sum W |V|^2
 };
 
-template <int P>
+// Rest bins of one channel of the current chunk, as the drain reads them.
+struct __align__(16) ChanS {
+    int32_t j0, nb;
+    float w0, w1;
+};
+
+// Chunk-cell entries per record slot: an item's rows plus the entries that
+// round its bulk copy out to 16-byte boundaries.
+__host__ __device__ constexpr int cc_slot_entries(int rb) { return (rb + 3) & ~1; }
+
+// Per-warp shared memory: two record slots, two chunk-cell slots, the
+// chunk's channel table, the D-row visibility ring, the staging area and two
+// mbarriers.
+template <int P, int VT, int NS, int D>
 __host__ __device__ constexpr size_t warp_smem_bytes(int rb)
 {
-    return 2 * (size_t)rb * sizeof(RowRec) + STAGE_CAP * sizeof(Staged<P>) + 2 * sizeof(uint64_t);
+    return 2 * (size_t)rb * sizeof(RowRec) + 2 * (size_t)cc_slot_entries(rb) * sizeof(int2) +
+           32 * NS * sizeof(ChanS) + (size_t)D * NS * 32 * VisAsync<P, VT>::kLaneBytes +
+           STAGE_CAP * sizeof(Staged<P>) + 2 * sizeof(uint64_t);
 }
 
 template <int P, int VT, int NS, int D>
 __global__ void __launch_bounds__(KMAX_THREADS) stack_mixed(RunArgs a)
 {
+    using VA = VisAsync<P, VT>;
+    constexpr int LB = VA::kLaneBytes;
     extern __shared__ __align__(16) unsigned char smem[];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    const int RB = a.so.rows_per_item;
-    unsigned char *wsm = smem + (size_t)wid * warp_smem_bytes<P>(RB);
+    const int RB = a.so.rows_per_item, CCS = cc_slot_entries(RB);
+    unsigned char *wsm = smem + (size_t)wid * warp_smem_bytes<P, VT, NS, D>(RB);
     RowRec *rbuf = reinterpret_cast<RowRec *>(wsm);
-    Staged<P> *stage = reinterpret_cast<Staged<P> *>(wsm + 2 * (size_t)RB * sizeof(RowRec));
-    uint64_t *bars = reinterpret_cast<uint64_t *>(wsm + 2 * (size_t)RB * sizeof(RowRec) +
-                                                  STAGE_CAP * sizeof(Staged<P>));
+    int2 *cbuf = reinterpret_cast<int2 *>(rbuf + 2 * RB);
+    ChanS *ctab = reinterpret_cast<ChanS *>(cbuf + 2 * CCS);
+    unsigned char *vring = reinterpret_cast<unsigned char *>(ctab + 32 * NS);
+    Staged<P> *stage = reinterpret_cast<Staged<P> *>(vring + (size_t)D * NS * 32 * LB);
+    uint64_t *bars = reinterpret_cast<uint64_t *>(stage + STAGE_CAP);
     if (lane == 0) {
         mbar_init(&bars[0], 1);
         mbar_init(&bars[1], 1);
         mbar_init_fence();
     }
     __syncwarp();
+    // this lane's ring entry of slot d, channel slot q
+    const uint32_t vring_lane = smem_addr(vring) + (uint32_t)lane * LB;
+    const unsigned char *vring_lane_p = vring + lane * LB;
 
     const uint32_t nitems = a.so.ctr[0];
-    const int npol_c = a.g.npol, nrest = a.g.nrest;
+    const int npol_c = a.g.npol, nrest = a.g.nrest, gnu = a.g.nu, gnv = a.g.nv;
     const unsigned lt_mask = (1u << lane) - 1u;
     float4 *cube4 = reinterpret_cast<float4 *>(a.cube);
-    uint32_t n_flag = 0, n_duv = 0, n_red = 0;
+    // visibilities read, stacked (unflagged, on the grid) and dropped off the
+    // grid; flagged = read - stacked - dropped
+    unsigned long long n_read = 0, n_ok = 0, n_duv = 0, n_red = 0;
     uint32_t phase = 0;   // bit s: parity of the next completion of slot s
 
     auto pop = [&]() -> uint32_t {
@@ -69,16 +97,21 @@ __global__ void __launch_bounds__(KMAX_THREADS) stack_mixed(RunArgs a)
         if (lane == 0) it = atomicAdd(&a.so.ctr[1], 1u);
         return __shfl_sync(0xffffffffu, it, 0);
     };
-    // Fetch the records of item `it` into slot s (lane 0 issues the copy).
+    // Fetch the records and chunk cells of item `it` into slot s (lane 0
+    // issues the copies).  The chunk-cell copy starts at an even entry.
     auto issue = [&](int s, uint32_t it) -> Item {
         const Item item = a.so.items[it];
         if (lane == 0) {
             const SrcDev &S = a.srcs[item.w];
-            const RowRec *src = a.recs + S.rec_off + item.q0;
-            const uint32_t bytes = (uint32_t)(item.q1 - item.q0) * (uint32_t)sizeof(RowRec);
+            const int n = item.q1 - item.q0;
+            const int64_t e0 = S.cell_off + (int64_t)item.chunk * S.nrow + item.q0;
+            const int64_t e0a = e0 & ~(int64_t)1;
+            const uint32_t ncc = (uint32_t)((e0 + n - e0a + 1) & ~(int64_t)1);
+            const uint32_t rbytes = (uint32_t)n * (uint32_t)sizeof(RowRec), cbytes = ncc * (uint32_t)sizeof(int2);
             fence_proxy_async();
-            mbar_expect_tx(&bars[s], bytes);
-            tma_load_1d(rbuf + (size_t)s * RB, src, bytes, &bars[s]);
+            mbar_expect_tx(&bars[s], rbytes + cbytes);
+            tma_load_1d(rbuf + (size_t)s * RB, a.recs + S.rec_off + item.q0, rbytes, &bars[s]);
+            tma_load_1d(cbuf + (size_t)s * CCS, a.ccells + e0a, cbytes, &bars[s]);
         }
         return item;
     };
@@ -104,58 +137,61 @@ __global__ void __launch_bounds__(KMAX_THREADS) stack_mixed(RunArgs a)
         // ---- one item ----
         // window fields in registers (the cube reductions could alias global
         // memory, so references into the table would be re-read)
-        const void *vis;
+        const unsigned char *vis;
         const uint8_t *flags;
         const double *uvw;
         int64_t vstride;
         float vscale;
-        int k_lo, k_hi, chan_off;
+        int k_hi, chf0;
         int plane[P];
+        const int2 *cb;
         {
             const SrcDev &G = a.srcs[item.w];
-            vis = G.vis;
-            flags = G.flags;
             uvw = G.uvw;
             vstride = G.vstride;
             vscale = G.vis_scale;
-            k_lo = G.k_lo;
             k_hi = G.k_hi;
-            chan_off = G.chan_off;
             const int c0g = G.k_lo + item.chunk * 32 * NS;
-            vis = reinterpret_cast<const char *>(G.vis) +
-                  (int64_t)(c0g + lane - G.kbase) * P * (int64_t)VisLoad<P, VT>::kBytes;
+            chf0 = G.chan_off + item.chunk * 32 * NS;
+            vis = reinterpret_cast<const unsigned char *>(G.vis) + (int64_t)(c0g + lane - G.kbase) * LB;
+            flags = G.flags;
             if (flags) flags += (int64_t)(c0g + lane - G.kbase) * P;
 #pragma unroll
             for (int p = 0; p < P; ++p) plane[p] = G.plane[p];
+            const int64_t e0 = G.cell_off + (int64_t)item.chunk * G.nrow + item.q0;
+            cb = cbuf + (size_t)cs * CCS + (e0 & 1);
+            k_hi -= c0g;   // chunk-local end
         }
-        const int c0 = k_lo + item.chunk * 32 * NS;
         const bool pack2 = (P == 2) && plane[0] >= 0 && plane[1] == plane[0] + 1 && !(plane[0] & 1) && !(npol_c & 1);
+        int npl = 0;
+#pragma unroll
+        for (int p = 0; p < P; ++p) npl += plane[p] >= 0;
+        const int n = item.q1 - item.q0;
 
-        // per channel slot: fl32(s_k), nu_k / c as float-float, and whether the
-        // channel has a rest bin
-        float su[NS], sv[NS], nh[NS], nl[NS];
+        // per channel slot: nu_k / c as float-float, whether the channel has
+        // a rest bin; the rest bins go to the warp's channel table
+        float nh[NS], nl[NS];
         bool act[NS];
 #pragma unroll
         for (int q = 0; q < NS; ++q) {
-            const int k = c0 + q * 32 + lane;
+            const int kk = q * 32 + lane;
             act[q] = false;
-            su[q] = sv[q] = nh[q] = nl[q] = 0.f;
-            if (k < k_hi) {
-                const ChanF cf = a.chf[chan_off + (k - k_lo)];
-                su[q] = cf.su;
-                sv[q] = cf.sv;
+            nh[q] = nl[q] = 0.f;
+            if (kk < k_hi) {
+                const ChanF cf = a.chf[chf0 + kk];
                 nh[q] = cf.nuc_hi;
                 nl[q] = cf.nuc_lo;
                 act[q] = cf.nb > 0;
+                ctab[kk] = ChanS{cf.j0, cf.nb, cf.w0, cf.w1};
             }
+            if (act[q]) n_read += (unsigned long long)n * (unsigned long long)npl;
         }
-        const int cslot = item.chunk < REC_CELLS ? item.chunk : -1;
         int cell[NS];
         float4 acc[NS][P];
         uint32_t cnt[NS][P];
 #pragma unroll
         for (int q = 0; q < NS; ++q) {
-            cell[q] = -1;
+            cell[q] = NO_RUN;
 #pragma unroll
             for (int p = 0; p < P; ++p) {
                 acc[q][p] = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -164,121 +200,143 @@ __global__ void __launch_bounds__(KMAX_THREADS) stack_mixed(RunArgs a)
         }
         int nstaged = 0;
 
-        // Stage lane runs that end here (`fl`): convergent, slots by ballot.
-        // The caller drains whenever fewer than 32 slots are free, so the
-        // index below stays inside the buffer; the check records a breach
-        // instead of writing out of bounds.
-        auto stage_runs = [&](int q, bool fl) {
-            const unsigned bal = __ballot_sync(0xffffffffu, fl);
-            const int slot = nstaged + __popc(bal & lt_mask);
-            if (fl && slot >= STAGE_CAP) atomicExch(a.err, 3);
-            if (fl && slot < STAGE_CAP) {
-                Staged<P> &st = stage[slot];
-                st.cell = cell[q];
-                st.chf = chan_off + (c0 + q * 32 + lane - k_lo);
-#pragma unroll
-                for (int p = 0; p < P; ++p) {
-                    st.cnt[p] = cnt[q][p];
-                    st.acc[p] = acc[q][p];
-                }
-            }
-            nstaged += __popc(bal);
-        };
         // All lanes write the staged runs to the cube, one run per lane.
         auto drain = [&]() {
             __syncwarp();
             for (int e = lane; e < nstaged; e += 32) {
-                const Staged<P> &st = stage[e];
-                const ChanF cf = a.chf[st.chf];
-                const size_t base = ((size_t)st.cell * nrest + cf.j0) * npol_c;
-                for (int b = 0; b < cf.nb; ++b) {
-                    const float ww = b == 0 ? cf.w0 : b == 1 ? cf.w1 : (float)a.chd[st.chf].w[b];
-                    const size_t e2 = base + (size_t)b * npol_c;
+                const Staged<P> st = stage[e];
+                uint32_t tot = 0;
 #pragma unroll
-                    for (int p = 0; p < P; ++p) {
-                        if (st.cnt[p] == 0) continue;
-                        const float4 v = st.acc[p];
-                        atomicAdd(cube4 + e2 + plane[p], make_float4(ww * v.x, ww * v.y, ww * v.z, ww * v.w));
-                        ++n_red;
-                        if (!pack2) {
-                            atomicAdd(a.count + e2 + plane[p], st.cnt[p]);
+                for (int p = 0; p < P; ++p) tot += plane[p] >= 0 ? st.cnt[p] : 0u;
+                if (st.cell < 0) {
+                    n_duv += tot;
+                } else {
+                    n_ok += tot;
+                    const ChanS ct = ctab[st.kk];
+                    const size_t base = ((size_t)st.cell * nrest + ct.j0) * npol_c;
+                    auto emit = [&](size_t e2, float ww) {
+#pragma unroll
+                        for (int p = 0; p < P; ++p) {
+                            if (plane[p] < 0 || st.cnt[p] == 0) continue;
+                            const float4 v = st.acc[p];
+                            atomicAdd(cube4 + e2 + plane[p], make_float4(ww * v.x, ww * v.y, ww * v.z, ww * v.w));
+                            ++n_red;
+                            if (!pack2) {
+                                atomicAdd(a.count + e2 + plane[p], st.cnt[p]);
+                                ++n_red;
+                            }
+                        }
+                        if (pack2 && (st.cnt[0] | st.cnt[P - 1])) {
+                            atomicAdd(reinterpret_cast<unsigned long long *>(a.count + e2 + plane[0]),
+                                      (unsigned long long)st.cnt[0] | ((unsigned long long)st.cnt[P - 1] << 32));
                             ++n_red;
                         }
-                    }
-                    if (pack2 && (st.cnt[0] | st.cnt[P - 1])) {
-                        atomicAdd(reinterpret_cast<unsigned long long *>(a.count + e2 + plane[0]),
-                                  (unsigned long long)st.cnt[0] | ((unsigned long long)st.cnt[P - 1] << 32));
-                        ++n_red;
-                    }
+                    };
+                    emit(base, ct.w0);
+                    if (ct.nb > 1) emit(base + (size_t)npol_c, ct.w1);
+                    // a third or fourth bin (lattices narrower than a channel)
+                    for (int b = 2; b < ct.nb; ++b)
+                        emit(base + (size_t)b * npol_c, (float)a.chd[chf0 + st.kk].w[b]);
                 }
             }
             __syncwarp();
             nstaged = 0;
         };
+        // Stage the lane runs that end here (`fl`): slots by ballot.  The
+        // staging area is drained whenever fewer than 32 slots are free, so
+        // the slot index stays inside it; the check records a breach instead
+        // of writing out of bounds.
+        auto stage_runs = [&](int q, bool fl) {
+            const unsigned bal = __ballot_sync(0xffffffffu, fl);
+            if (bal) {
+                const int slot = nstaged + __popc(bal & lt_mask);
+                if (fl) {
+                    if (slot < STAGE_CAP) {
+                        Staged<P> &st = stage[slot];
+                        st.cell = cell[q];
+                        st.kk = q * 32 + lane;
+#pragma unroll
+                        for (int p = 0; p < P; ++p) {
+                            st.cnt[p] = cnt[q][p];
+                            st.acc[p] = acc[q][p];
+                        }
+                    } else {
+                        atomicExch(a.err, 3);
+                    }
+                }
+                nstaged += __popc(bal);
+                if (nstaged > STAGE_CAP - 32) drain();
+            }
+        };
 
-        // visibility / flag ring, D rows ahead
-        const int n = item.q1 - item.q0;
-        float2 RV[D][NS][P];
+        // D-row ring: visibilities by cp.async into shared memory (one
+        // commit group per row), flags in registers
         uint32_t RF[D][NS];
+#pragma unroll
+        for (int d = 0; d < D; ++d)
+#pragma unroll
+            for (int q = 0; q < NS; ++q) RF[d][q] = 0;
         auto fetch = [&](int d, int i) {
-            const int64_t row = (int64_t)(rb[i].rowf & 0x7fffffffu);
-            const int64_t off = row * vstride;
+            const int64_t off = (int64_t)(rb[i].rowf & 0x7fffffffu) * vstride;
 #pragma unroll
             for (int q = 0; q < NS; ++q) {
-                RF[d][q] = 0;
                 if (act[q]) {
-                    VisLoad<P, VT>::load(vis, off + q * 32, vscale, RV[d][q]);
+                    VA::copy(vring_lane + (uint32_t)((d * NS + q) * 32 * LB), vis + (off + q * 32) * LB);
                     RF[d][q] = load_flags<P>(flags, off + q * 32);
                 }
             }
         };
 #pragma unroll
-        for (int d = 0; d < D; ++d)
+        for (int d = 0; d < D - 1; ++d) {
             if (d < n) fetch(d, d);
+            cp_async_commit();
+        }
 
         for (int i0 = 0; i0 < n; i0 += D) {
 #pragma unroll
             for (int d = 0; d < D; ++d) {
                 const int i = i0 + d;
                 if (i >= n) break;
+                if (i + D - 1 < n) fetch((d + D - 1) % D, i + D - 1);
+                cp_async_commit();
+                cp_async_wait<D - 1>();
                 float2 V[NS][P];
                 uint32_t F[NS];
 #pragma unroll
                 for (int q = 0; q < NS; ++q) {
                     F[q] = RF[d][q];
-#pragma unroll
-                    for (int p = 0; p < P; ++p) V[q][p] = RV[d][q][p];
+                    VA::decode(vring_lane_p + (size_t)(d * NS + q) * 32 * LB, vscale, V[q]);
                 }
-                if (i + D < n) fetch(d, i + D);
 
-                const RowRec &rec = rb[i];
-                const uint32_t rowf = rec.rowf;
-                const int64_t row = (int64_t)(rowf & 0x7fffffffu);
-                const bool fold = (rowf >> 31) != 0;
-                const float th = rec.tau_hi, tl = rec.tau_lo;
-                // the chunk's shared cell, if the pre-pass found one
-                const int cinfo = cslot >= 0 ? rec.cell[cslot] : CELL_MIXED;
+                const float4 r0 = *reinterpret_cast<const float4 *>(&rb[i]);   // tau_hi, tau_lo, rowf, W0
+                float W[P];
+                W[0] = r0.w;
+                if constexpr (P > 1) {
+                    const float4 r1 = *reinterpret_cast<const float4 *>(&rb[i].W[1]);
+                    W[1] = r1.x;
+                    if constexpr (P > 2) {
+                        W[2] = r1.y;
+                        W[3] = r1.z;
+                    }
+                }
+                const int2 cc = cb[i];
 #pragma unroll
                 for (int q = 0; q < NS; ++q) {
-                    const int k = c0 + q * 32 + lane;
-                    const float2 ph = shift_phasor(th, tl, nh[q], nl[q]);
+                    const float2 ph = shift_phasor(r0.x, r0.y, nh[q], nl[q]);
                     int cid = cell[q];
                     if (act[q]) {
-                        if (cinfo != CELL_MIXED) {
-                            cid = cinfo;
+                        if (cc.y == CC_NOCHANGE) {
+                            cid = cc.x;
+                        } else if (cc.y != CC_MIXED) {
+                            cid = chunk_cell_step(cc, q * 32 + lane, gnu);
                         } else {
-                            const ChanD *cd = a.chd + chan_off + (k - k_lo);
-                            const int iu = axis_cell(rec.u, su[q], uvw + 3 * row, fold, &cd->su, a.g.nu);
-                            const int iv = axis_cell(rec.v, sv[q], uvw + 3 * row + 1, fold, &cd->sv, a.g.nv);
-                            cid = (iu >= 0 && iv >= 0) ? iv * a.g.nu + iu : -1;
+                            const uint32_t rowf = __float_as_uint(r0.z);
+                            cid = cell_exact(uvw, (int64_t)(rowf & 0x7fffffffu), (rowf >> 31) != 0,
+                                             a.chd + chf0 + q * 32 + lane, gnu, gnv);
                         }
                     }
                     const bool newcell = cid != cell[q];
-                    uint32_t any = 0;
-#pragma unroll
-                    for (int p = 0; p < P; ++p) any |= cnt[q][p];
-                    stage_runs(q, newcell && cell[q] >= 0 && any != 0);
-                    if (nstaged > STAGE_CAP - 32) drain();
+                    stage_runs(q, newcell && cell[q] != NO_RUN);
                     if (newcell) {
                         cell[q] = cid;
 #pragma unroll
@@ -287,46 +345,35 @@ __global__ void __launch_bounds__(KMAX_THREADS) stack_mixed(RunArgs a)
                             cnt[q][p] = 0;
                         }
                     }
-                    if (act[q]) {
 #pragma unroll
-                        for (int p = 0; p < P; ++p) {
-                            // short predicated bodies instead of branches
-                            const bool pl = plane[p] >= 0;
-                            const bool f = ((F[q] >> (8 * p)) & 0xffu) != 0;
-                            const bool use = pl && !f && cid >= 0;
-                            n_flag += (pl && f) ? 1u : 0u;
-                            n_duv += (pl && !f && cid < 0) ? 1u : 0u;
-                            float2 vs = cmul(V[q][p], ph);
-                            vs.y = fold ? -vs.y : vs.y;
-                            const float W = rec.W[p];
-                            const float a2 = V[q][p].x * V[q][p].x + V[q][p].y * V[q][p].y;
-                            if (use) {
-                                acc[q][p].x += W * vs.x;
-                                acc[q][p].y += W * vs.y;
-                                acc[q][p].z += W;
-                                acc[q][p].w += W * a2;
-                                cnt[q][p] += 1;
-                            }
+                    for (int p = 0; p < P; ++p) {
+                        const bool ok = ((F[q] >> (8 * p)) & 0xffu) == 0;
+                        const float2 v = V[q][p];
+                        const float re = v.x * ph.x - v.y * ph.y;
+                        const float im = v.x * ph.y + v.y * ph.x;
+                        const float a2 = v.x * v.x + v.y * v.y;
+                        const float Ws = W[p], Wa = fabsf(Ws);   // the sign conjugates folded rows
+                        if (ok) {
+                            acc[q][p].x += Wa * re;
+                            acc[q][p].y += Ws * im;
+                            acc[q][p].z += Wa;
+                            acc[q][p].w += Wa * a2;
+                            cnt[q][p] += 1;
                         }
                     }
                 }
             }
         }
+        cp_async_wait<0>();
 #pragma unroll
-        for (int q = 0; q < NS; ++q) {
-            uint32_t any = 0;
-#pragma unroll
-            for (int p = 0; p < P; ++p) any |= cnt[q][p];
-            stage_runs(q, cell[q] >= 0 && any != 0);
-            if (nstaged > STAGE_CAP - 32) drain();
-        }
+        for (int q = 0; q < NS; ++q) stage_runs(q, cell[q] != NO_RUN);
         drain();
         s ^= 1;
     }
 
-    // counters (the visibilities read are counted on the host from the
+    // counters (the visibilities read are also counted on the host from the
     // channel tables): warp sum, one atomic per counter per warp
-    unsigned long long c3[3] = {n_flag, n_duv, n_red};
+    unsigned long long c3[3] = {n_read - n_ok - n_duv, n_duv, n_red};
 #pragma unroll
     for (int k = 0; k < 3; ++k)
 #pragma unroll
@@ -352,8 +399,8 @@ static int sm_count()
     return n;
 }
 
-template <int P, typename K>
-static cudaError_t launch_persistent(K kern, const RunArgs &a, int wpc, cudaStream_t st)
+template <int P, int VT, int NS, int D>
+static cudaError_t launch_persistent(const RunArgs &a, int wpc, cudaStream_t st)
 {
     const int rb = a.so.rows_per_item;
     if (rb < 1 || rb > RB_MAX) return cudaErrorInvalidValue;
@@ -364,9 +411,12 @@ static cudaError_t launch_persistent(K kern, const RunArgs &a, int wpc, cudaStre
         cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     }
     // fewer warps per block when their staging buffers would not fit
+    auto kern = stack_mixed<P, VT, NS, D>;
+    const size_t wsm = warp_smem_bytes<P, VT, NS, D>(rb);
     if (wpc * 32 > KMAX_THREADS) wpc = KMAX_THREADS / 32;
-    while (wpc > 1 && (size_t)wpc * warp_smem_bytes<P>(rb) > (size_t)smem_max) wpc >>= 1;
-    const size_t smem = (size_t)wpc * warp_smem_bytes<P>(rb);
+    while (wpc > 1 && (size_t)wpc * wsm > (size_t)smem_max) wpc >>= 1;
+    const size_t smem = (size_t)wpc * wsm;
+    if (smem > (size_t)smem_max) return cudaErrorInvalidValue;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     int per_sm = 0;
@@ -377,26 +427,22 @@ static cudaError_t launch_persistent(K kern, const RunArgs &a, int wpc, cudaStre
     return cudaGetLastError();
 }
 
-// Prefetch depth D (rows of visibilities in flight per warp): deeper rings
-// hide more HBM latency but cost registers; the common storage types get a
-// choice, the rest one depth per channels-per-lane.
+// Ring depth D (rows of visibilities in flight per warp): the ring lives in
+// shared memory, so depth costs only its flag registers and code size.  One
+// channel per lane takes D = 2, 4 or 8 (prefetch_rows), two take 2 or 4,
+// four take 2.
 template <int P, int VT>
 static cudaError_t launch_mixed_p(const RunArgs &a, int ns, int pf, int wpc, cudaStream_t st)
 {
-    constexpr bool choice = VT != VISTA_VIS_C128 && P <= 2;
     switch (ns) {
     case 1:
-        if constexpr (choice) {
-            if (pf >= 8) return launch_persistent<P>(stack_mixed<P, VT, 1, 8>, a, wpc, st);
-            if (pf >= 4) return launch_persistent<P>(stack_mixed<P, VT, 1, 4>, a, wpc, st);
-        }
-        return launch_persistent<P>(stack_mixed<P, VT, 1, 2>, a, wpc, st);
+        if (pf >= 8) return launch_persistent<P, VT, 1, 8>(a, wpc, st);
+        if (pf >= 4) return launch_persistent<P, VT, 1, 4>(a, wpc, st);
+        return launch_persistent<P, VT, 1, 2>(a, wpc, st);
     case 2:
-        if constexpr (choice) {
-            if (pf >= 4) return launch_persistent<P>(stack_mixed<P, VT, 2, 4>, a, wpc, st);
-        }
-        return launch_persistent<P>(stack_mixed<P, VT, 2, (P <= 2 ? 2 : 1)>, a, wpc, st);
-    case 4: return launch_persistent<P>(stack_mixed<P, VT, 4, 1>, a, wpc, st);
+        if (pf >= 4) return launch_persistent<P, VT, 2, 4>(a, wpc, st);
+        return launch_persistent<P, VT, 2, 2>(a, wpc, st);
+    case 4: return launch_persistent<P, VT, 4, 2>(a, wpc, st);
     default: return cudaErrorInvalidValue;
     }
 }
