@@ -61,6 +61,7 @@ struct SrcDev {
     int64_t rec_off;        // first row record of this window
     int64_t cell_off;       // first chunk-cell entry of this window ([chunk][row] inside)
 };
+static_assert(sizeof(SrcDev) % 16 == 0, "SrcDev is copied in 16-byte units");
 
 // Per-row record written by the mixed path's FP64 pre-pass (32 B), in
 // processing order.
@@ -90,10 +91,15 @@ constexpr int32_t CC_NOCHANGE = 0x0000ffff;
 constexpr int32_t CC_MIXED = -1;
 
 // One unit of stacking work: rows [q0, q1) (in processing order) of window
-// w, channel chunk c.
+// w, channel chunk c, with the table positions its bulk copies start at.
 struct __align__(16) Item {
     int32_t w, chunk, q0, q1;
+    int32_t chf0, nch;          // first channel-table entry of the chunk, channels in it
+    int64_t rec0;               // first row record
+    int64_t cell0;              // first chunk-cell entry
+    int64_t pad;
 };
+static_assert(sizeof(Item) == 48, "Item is copied in 16-byte units");
 
 // Counters (device), see vista_stats.
 struct DevStats {
@@ -115,10 +121,12 @@ struct LaunchCfg {
 //   key      [rows]             stripe << 13 | local cell key
 //   tmp      [rows]             (local key << 32) | row, bucket-grouped
 //   perm     [rows]             row of each processing position
+//   ioff     [nbuckets + 1]     first work item of each bucket (stripe-major)
 //   items    [max_items]        work list, stripe-major
 //   ctr      [2]                item count, queue head
 struct SortArgs {
     uint32_t *hist, *qstart, *slot, *key, *perm;
+    int64_t *ioff;
     unsigned long long *tmp;
     Item *items;
     uint32_t *ctr;

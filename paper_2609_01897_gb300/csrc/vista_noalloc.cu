@@ -181,6 +181,8 @@ extern "C" int vista_stack_noalloc(const vista_cube_desc *c, const vista_source_
     o += al256(4 * (size_t)nstripe);
     const size_t o_qs = o;
     o += al256(4 * (size_t)nstripe);
+    const size_t o_ioff = o;
+    o += al256(8 * ((size_t)nstripe + 1));
     const size_t o_slot = o;
     o += al256(4 * (size_t)nrow);
     const size_t o_key = o;
@@ -260,6 +262,7 @@ extern "C" int vista_stack_noalloc(const vista_cube_desc *c, const vista_source_
     a.err = (int32_t *)(b + o_err);
     a.so.hist = (uint32_t *)(b + o_hist);
     a.so.qstart = (uint32_t *)(b + o_qs);
+    a.so.ioff = (int64_t *)(b + o_ioff);
     a.so.slot = (uint32_t *)(b + o_slot);
     a.so.key = (uint32_t *)(b + o_key);
     a.so.perm = (uint32_t *)(b + o_perm);

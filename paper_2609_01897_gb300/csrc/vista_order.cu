@@ -8,8 +8,10 @@
 //   k_keys         cell of every row at the window's highest in-cube
 //                  frequency -> (stripe, local cell key); per-bucket arrival
 //                  slots with warp-aggregated atomics
-//   k_scan         one block: per-window bucket offsets, and the work list in
-//                  stripe-major order (item = rows of one bucket x one chunk)
+//   k_scan         one block: per-window bucket offsets, per-bucket work-list
+//                  offsets in stripe-major order (item = rows of one bucket x
+//                  one chunk)
+//   k_items        the work list, one thread per item
 //   k_scatter      rows grouped by bucket
 //   k_bucket_sort  one block per bucket: counting sort by local cell key
 //   k_records      per row, in processing order: the FP64 delay of Eq. 2 as
@@ -96,29 +98,49 @@ __global__ void __launch_bounds__(1024) k_scan(RunArgs a)
     int64_t pos = part[threadIdx.x] - local;
     const int64_t total = part[blockDim.x - 1];
     for (int64_t i = i0; i < i1; ++i) {
+        so.ioff[i] = pos;
         const int s = (int)(i / nw), w = (int)(i % nw);
         const int64_t n = so.hist[(size_t)w * ns + s];
-        const int64_t q = so.qstart[(size_t)w * ns + s];
-        const int nch = a.srcs[w].nchunk;
-        for (int64_t t = 0; t * R < n; ++t) {
-            for (int c = 0; c < nch; ++c) {
-                if (pos < so.max_items) {
-                    Item it;
-                    it.w = w;
-                    it.chunk = c;
-                    it.q0 = (int32_t)(q + t * R);
-                    it.q1 = (int32_t)min(q + n, q + (t + 1) * R);
-                    so.items[pos] = it;
-                }
-                ++pos;
-            }
-        }
+        pos += ((n + R - 1) / R) * a.srcs[w].nchunk;
     }
+    if (threadIdx.x == 0) so.ioff[nb] = total;
     if (threadIdx.x == 0) {
         if (total > so.max_items) atomicExch(a.err, 2);   // host sizing bug: never expected
         so.ctr[0] = (uint32_t)min(total, so.max_items);
         so.ctr[1] = 0u;
     }
+}
+
+// One thread per work item: bucket i (stripe-major) holds items
+// [ioff[i], ioff[i+1]), rows in groups of rows_per_item, each group split
+// into the window's channel chunks.
+__global__ void __launch_bounds__(256) k_items(RunArgs a)
+{
+    const SortArgs &so = a.so;
+    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t nb = (int64_t)a.nsrc * so.nstripe;
+    if (p >= so.ioff[nb] || p >= so.max_items) return;
+    const int i = find_owner(so.ioff, (int)nb, p);
+    const int nw = a.nsrc, R = so.rows_per_item;
+    const int st = i / nw, w = i % nw;
+    const SrcDev &S = a.srcs[w];
+    const int64_t local = p - so.ioff[i];
+    const int c = (int)(local % S.nchunk);
+    const int64_t t = local / S.nchunk;
+    const int64_t n = so.hist[(size_t)w * so.nstripe + st];
+    const int64_t q = so.qstart[(size_t)w * so.nstripe + st];
+    const int nin = S.k_hi - S.k_lo;
+    Item it;
+    it.w = w;
+    it.chunk = c;
+    it.q0 = (int32_t)(q + t * R);
+    it.q1 = (int32_t)min(q + n, q + (t + 1) * R);
+    it.chf0 = S.chan_off + c * a.cw;
+    it.nch = min(a.cw, nin - c * a.cw);
+    it.rec0 = S.rec_off + it.q0;
+    it.cell0 = S.cell_off + (int64_t)c * S.nrow + it.q0;
+    it.pad = 0;
+    so.items[p] = it;
 }
 
 __global__ void __launch_bounds__(256) k_scatter(RunArgs a)
@@ -296,6 +318,7 @@ cudaError_t launch_prepare(const RunArgs &a, cudaStream_t st)
     const unsigned rb = (unsigned)((a.nrows_total + 255) / 256);
     if (rb) k_keys<<<rb, 256, 0, st>>>(a);
     k_scan<<<1, 1024, 0, st>>>(a);
+    if (so.max_items > 0) k_items<<<(unsigned)((so.max_items + 255) / 256), 256, 0, st>>>(a);
     if (rb) k_scatter<<<rb, 256, 0, st>>>(a);
     const int64_t nbuckets = (int64_t)a.nsrc * so.nstripe;
     if (rb && nbuckets) k_bucket_sort<<<(unsigned)nbuckets, 256, 0, st>>>(a);

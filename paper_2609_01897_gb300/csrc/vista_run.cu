@@ -100,7 +100,7 @@ inline size_t al256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 // Layout of the shared ordering buffer for one class.
 struct SortLayout {
-    size_t hist, qstart, slot, key, perm, tmp, items, ctr, total;
+    size_t hist, qstart, ioff, slot, key, perm, tmp, items, ctr, total;
 };
 
 SortLayout sort_layout(int64_t rows, int64_t nbuckets, int64_t max_items)
@@ -111,6 +111,8 @@ SortLayout sort_layout(int64_t rows, int64_t nbuckets, int64_t max_items)
     o += al256(4 * (size_t)nbuckets);
     L.qstart = o;
     o += al256(4 * (size_t)nbuckets);
+    L.ioff = o;
+    o += al256(8 * ((size_t)nbuckets + 1));
     L.slot = o;
     o += al256(4 * (size_t)rows);
     L.key = o;
@@ -368,6 +370,7 @@ extern "C" int vista_run(vista_stack *h)
             char *b = (char *)h->b_sort.p;
             so.hist = (uint32_t *)(b + L.hist);
             so.qstart = (uint32_t *)(b + L.qstart);
+            so.ioff = (int64_t *)(b + L.ioff);
             so.slot = (uint32_t *)(b + L.slot);
             so.key = (uint32_t *)(b + L.key);
             so.perm = (uint32_t *)(b + L.perm);
@@ -383,7 +386,7 @@ extern "C" int vista_run(vista_stack *h)
             int sp = span_begin(h, 0);
             e = launch_prepare(a, h->stream);
             span_end(h, sp);
-            if (h->timing) h->tacc.launches += 5;
+            if (h->timing) h->tacc.launches += 6;
             if (e == cudaSuccess) {
                 sp = span_begin(h, 1);
                 e = launch_mixed(a, cr.key, cfg.warps_per_cta, cfg.prefetch_rows, h->stream);

@@ -1,22 +1,25 @@
 // The mixed-precision stacking kernel (sm_103a).
 //
-// Persistent: every warp pops work items (one window, up to rows_per_item
-// rows in uv-cell order, a chunk of 32 x NS channels, lane = channel) from a
-// queue in stripe-major order.  Per warp, the row records and chunk cells of
-// the next item are fetched into shared memory by TMA bulk copies
-// (completing on an mbarrier) while the current item is processed; inside an
-// item the visibility and flag loads run D rows ahead of the arithmetic.
+// Persistent: warp g of G takes work items g, g + G, g + 2G, ... of a list
+// in stripe-major order (item = one window, up to rows_per_item rows in
+// uv-cell order, a chunk of 32 x NS channels, lane = channel).  While a warp
+// processes an item, TMA bulk copies (one mbarrier per slot) bring the next
+// item's row records, chunk cells, window header, channel table and work-list
+// entries into the other shared-memory slot, so an item starts without a
+// global round trip.  Inside an item the visibilities of the next D - 1 rows
+// are in flight into a shared-memory ring (cp.async), their flags in
+// registers.
 //
 // Per (row, channel): the FP32 phasor of Eq. 2 from the record's float-float
 // delay and the channel's float-float nu_k / c, the uv cell from the chunk's
 // cell entry (exact: computed by the pre-pass with the FP64 rule), rest bins
 // and Eq. 4 weights from the FP64 channel table.  Per lane, running sums
 // over consecutive rows that share a uv cell stay in registers.  When a
-// lane's cell changes, its finished run is appended to a per-warp staging
-// area in shared memory (slots from a warp ballot); the warp drains the
-// staging area together, one lane per run, as float4 reductions per (cell,
-// rest bin, pol) and one count reduction per (cell, rest bin) (one u64 for a
-// pol pair).  Runs off the grid only feed the dropped-visibility counter.
+// lane's cell changes, its finished run goes to a per-warp circular staging
+// area in shared memory (slots from a warp ballot); every 32 staged runs the
+// warp drains them together, one lane per run, as float4 reductions per
+// (cell, rest bin, pol) and one count reduction per (cell, rest bin) (one
+// u64 for a pol pair).  Runs off the grid only feed the dropped counter.
 #include <climits>
 
 #include "vista_device.cuh"
@@ -25,7 +28,7 @@ namespace vista {
 
 constexpr int RB_MAX = 256;         // largest item (rows) the shared-memory buffers hold
 constexpr int KMAX_THREADS = 256;   // blocks of at most 8 warps
-constexpr int STAGE_CAP = 96;       // staged runs per warp
+constexpr int STAGE_CAP = 64;       // staged runs per warp (circular; a power of two)
 constexpr int NO_RUN = INT_MIN;     // lane holds no run
 
 // One finished run of one channel slot.
@@ -37,26 +40,45 @@ struct __align__(16) Staged {
     float4 acc[P];    // sum W V'.re, sum W V'.im, sum W, sum W |V|^2
 };
 
-// Rest bins of one channel of the current chunk, as the drain reads them.
-struct __align__(16) ChanS {
-    int32_t j0, nb;
-    float w0, w1;
-};
-
-// Chunk-cell entries per record slot: an item's rows plus the entries that
-// round its bulk copy out to 16-byte boundaries.
+// Chunk-cell entries per slot: an item's rows plus the entries that round
+// its bulk copy out to 16-byte boundaries.
 __host__ __device__ constexpr int cc_slot_entries(int rb) { return (rb + 3) & ~1; }
 
-// Per-warp shared memory: two record slots, two chunk-cell slots, the
-// chunk's channel table, the D-row visibility ring, the staging area and two
-// mbarriers.
+// One item slot in shared memory (filled by bulk copies).
+template <int NS>
+__host__ __device__ constexpr size_t slot_bytes(int rb)
+{
+    return 2 * sizeof(Item) + sizeof(SrcDev) + 32 * NS * sizeof(ChanF) + (size_t)rb * sizeof(RowRec) +
+           (size_t)cc_slot_entries(rb) * sizeof(int2);
+}
+
+// Per-warp shared memory: two item slots, the D-row visibility ring, the
+// staging area and two mbarriers.
 template <int P, int VT, int NS, int D>
 __host__ __device__ constexpr size_t warp_smem_bytes(int rb)
 {
-    return 2 * (size_t)rb * sizeof(RowRec) + 2 * (size_t)cc_slot_entries(rb) * sizeof(int2) +
-           32 * NS * sizeof(ChanS) + (size_t)D * NS * 32 * VisAsync<P, VT>::kLaneBytes +
+    return 2 * slot_bytes<NS>(rb) + (size_t)D * NS * 32 * VisAsync<P, VT>::kLaneBytes +
            STAGE_CAP * sizeof(Staged<P>) + 2 * sizeof(uint64_t);
 }
+
+// Views of one slot.
+template <int NS>
+struct Slot {
+    Item *self, *next;   // this item, the item after it (same warp)
+    SrcDev *hdr;
+    ChanF *chf;
+    RowRec *rec;
+    int2 *cells;
+    __device__ Slot(unsigned char *base, int rb)
+    {
+        self = reinterpret_cast<Item *>(base);
+        next = self + 1;
+        hdr = reinterpret_cast<SrcDev *>(next + 1);
+        chf = reinterpret_cast<ChanF *>(hdr + 1);
+        rec = reinterpret_cast<RowRec *>(chf + 32 * NS);
+        cells = reinterpret_cast<int2 *>(rec + rb);
+    }
+};
 
 template <int P, int VT, int NS, int D>
 __global__ void __launch_bounds__(KMAX_THREADS) stack_mixed(RunArgs a)
@@ -65,12 +87,10 @@ __global__ void __launch_bounds__(KMAX_THREADS) stack_mixed(RunArgs a)
     constexpr int LB = VA::kLaneBytes;
     extern __shared__ __align__(16) unsigned char smem[];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    const int RB = a.so.rows_per_item, CCS = cc_slot_entries(RB);
+    const int RB = a.so.rows_per_item;
     unsigned char *wsm = smem + (size_t)wid * warp_smem_bytes<P, VT, NS, D>(RB);
-    RowRec *rbuf = reinterpret_cast<RowRec *>(wsm);
-    int2 *cbuf = reinterpret_cast<int2 *>(rbuf + 2 * RB);
-    ChanS *ctab = reinterpret_cast<ChanS *>(cbuf + 2 * CCS);
-    unsigned char *vring = reinterpret_cast<unsigned char *>(ctab + 32 * NS);
+    auto slot_at = [&](int s) { return Slot<NS>(wsm + (size_t)s * slot_bytes<NS>(RB), RB); };
+    unsigned char *vring = wsm + 2 * slot_bytes<NS>(RB);
     Staged<P> *stage = reinterpret_cast<Staged<P> *>(vring + (size_t)D * NS * 32 * LB);
     uint64_t *bars = reinterpret_cast<uint64_t *>(stage + STAGE_CAP);
     if (lane == 0) {
@@ -79,11 +99,12 @@ __global__ void __launch_bounds__(KMAX_THREADS) stack_mixed(RunArgs a)
         mbar_init_fence();
     }
     __syncwarp();
-    // this lane's ring entry of slot d, channel slot q
     const uint32_t vring_lane = smem_addr(vring) + (uint32_t)lane * LB;
     const unsigned char *vring_lane_p = vring + lane * LB;
 
     const uint32_t nitems = a.so.ctr[0];
+    const uint32_t G = gridDim.x * (blockDim.x >> 5);
+    const uint32_t gw = blockIdx.x * (blockDim.x >> 5) + wid;
     const int npol_c = a.g.npol, nrest = a.g.nrest, gnu = a.g.nu, gnv = a.g.nv;
     const unsigned lt_mask = (1u << lane) - 1u;
     float4 *cube4 = reinterpret_cast<float4 *>(a.cube);
@@ -92,84 +113,82 @@ __global__ void __launch_bounds__(KMAX_THREADS) stack_mixed(RunArgs a)
     unsigned long long n_read = 0, n_ok = 0, n_duv = 0, n_red = 0;
     uint32_t phase = 0;   // bit s: parity of the next completion of slot s
 
-    auto pop = [&]() -> uint32_t {
-        uint32_t it = 0;
-        if (lane == 0) it = atomicAdd(&a.so.ctr[1], 1u);
-        return __shfl_sync(0xffffffffu, it, 0);
-    };
-    // Fetch the records and chunk cells of item `it` into slot s (lane 0
-    // issues the copies).  The chunk-cell copy starts at an even entry.
-    auto issue = [&](int s, uint32_t it) -> Item {
-        const Item item = a.so.items[it];
-        if (lane == 0) {
-            const SrcDev &S = a.srcs[item.w];
-            const int n = item.q1 - item.q0;
-            const int64_t e0 = S.cell_off + (int64_t)item.chunk * S.nrow + item.q0;
-            const int64_t e0a = e0 & ~(int64_t)1;
-            const uint32_t ncc = (uint32_t)((e0 + n - e0a + 1) & ~(int64_t)1);
-            const uint32_t rbytes = (uint32_t)n * (uint32_t)sizeof(RowRec), cbytes = ncc * (uint32_t)sizeof(int2);
-            fence_proxy_async();
-            mbar_expect_tx(&bars[s], rbytes + cbytes);
-            tma_load_1d(rbuf + (size_t)s * RB, a.recs + S.rec_off + item.q0, rbytes, &bars[s]);
-            tma_load_1d(cbuf + (size_t)s * CCS, a.ccells + e0a, cbytes, &bars[s]);
-        }
-        return item;
+    // Lane 0: bulk copies of item `it` (its entry `item`) into slot s,
+    // together with the entry of the warp's following item `itn`, if any.
+    auto issue = [&](int s, uint32_t it, const Item &item, uint32_t itn) {
+        const Slot<NS> S = slot_at(s);
+        const int n = item.q1 - item.q0;
+        const int64_t e0a = item.cell0 & ~(int64_t)1;
+        const uint32_t ncc = (uint32_t)((item.cell0 + n - e0a + 1) & ~(int64_t)1);
+        const uint32_t b_items = (uint32_t)sizeof(Item) * (itn < nitems ? 2u : 1u);
+        const uint32_t b_chf = (uint32_t)item.nch * (uint32_t)sizeof(ChanF);
+        const uint32_t b_rec = (uint32_t)n * (uint32_t)sizeof(RowRec), b_cc = ncc * (uint32_t)sizeof(int2);
+        fence_proxy_async();
+        mbar_expect_tx(&bars[s], b_items + (uint32_t)sizeof(SrcDev) + b_chf + b_rec + b_cc);
+        tma_load_1d(S.self, a.so.items + it, (uint32_t)sizeof(Item), &bars[s]);
+        if (itn < nitems) tma_load_1d(S.next, a.so.items + itn, (uint32_t)sizeof(Item), &bars[s]);
+        tma_load_1d(S.hdr, a.srcs + item.w, (uint32_t)sizeof(SrcDev), &bars[s]);
+        tma_load_1d(S.chf, a.chf + item.chf0, b_chf, &bars[s]);
+        tma_load_1d(S.rec, a.recs + item.rec0, b_rec, &bars[s]);
+        tma_load_1d(S.cells, a.ccells + e0a, b_cc, &bars[s]);
     };
 
-    uint32_t it_next = pop();
-    Item nxt{};
-    if (it_next < nitems) nxt = issue(0, it_next);
+    uint32_t it = gw;
+    if (lane == 0 && it < nitems) {
+        const Item first = a.so.items[it];
+        issue(0, it, first, it + G);
+    }
     int s = 0;
-    while (it_next < nitems) {
-        const Item item = nxt;
+    for (; it < nitems; it += G, s ^= 1) {
         const int cs = s;
         __syncwarp();
-        it_next = pop();
-        if (it_next < nitems) nxt = issue(cs ^ 1, it_next);
         if (!mbar_wait_bounded(&bars[cs], (phase >> cs) & 1u, a.err)) {
-            // give the other slot's copy a bounded chance to land, then stop
-            if (it_next < nitems) mbar_wait_bounded(&bars[cs ^ 1], (phase >> (cs ^ 1)) & 1u, a.err);
+            // the copy in flight gets one more bounded wait before the warp stops
+            mbar_wait_bounded(&bars[cs], (phase >> cs) & 1u, a.err);
             break;
         }
         phase ^= 1u << cs;
-        const RowRec *rb = rbuf + (size_t)cs * RB;
+        const Slot<NS> S = slot_at(cs);
+        // the next item's copies run while this one is processed
+        if (lane == 0 && it + G < nitems) issue(cs ^ 1, it + G, *S.next, it + 2 * G);
 
         // ---- one item ----
         // window fields in registers (the cube reductions could alias global
-        // memory, so references into the table would be re-read)
+        // memory, so reads through pointers would be repeated)
         const unsigned char *vis;
         const uint8_t *flags;
         const double *uvw;
         int64_t vstride;
         float vscale;
-        int k_hi, chf0;
+        int nch, chf0, n;
         int plane[P];
         const int2 *cb;
+        const RowRec *rb = S.rec;
+        const ChanF *ctab = S.chf;
         {
-            const SrcDev &G = a.srcs[item.w];
-            uvw = G.uvw;
-            vstride = G.vstride;
-            vscale = G.vis_scale;
-            k_hi = G.k_hi;
-            const int c0g = G.k_lo + item.chunk * 32 * NS;
-            chf0 = G.chan_off + item.chunk * 32 * NS;
-            vis = reinterpret_cast<const unsigned char *>(G.vis) + (int64_t)(c0g + lane - G.kbase) * LB;
-            flags = G.flags;
-            if (flags) flags += (int64_t)(c0g + lane - G.kbase) * P;
+            const SrcDev &H = *S.hdr;
+            const Item &I = *S.self;
+            uvw = H.uvw;
+            vstride = H.vstride;
+            vscale = H.vis_scale;
+            nch = I.nch;
+            chf0 = I.chf0;
+            n = I.q1 - I.q0;
+            const int c0g = H.k_lo + I.chunk * 32 * NS;
+            vis = reinterpret_cast<const unsigned char *>(H.vis) + (int64_t)(c0g + lane - H.kbase) * LB;
+            flags = H.flags;
+            if (flags) flags += (int64_t)(c0g + lane - H.kbase) * P;
 #pragma unroll
-            for (int p = 0; p < P; ++p) plane[p] = G.plane[p];
-            const int64_t e0 = G.cell_off + (int64_t)item.chunk * G.nrow + item.q0;
-            cb = cbuf + (size_t)cs * CCS + (e0 & 1);
-            k_hi -= c0g;   // chunk-local end
+            for (int p = 0; p < P; ++p) plane[p] = H.plane[p];
+            cb = S.cells + (I.cell0 & 1);
         }
         const bool pack2 = (P == 2) && plane[0] >= 0 && plane[1] == plane[0] + 1 && !(plane[0] & 1) && !(npol_c & 1);
         int npl = 0;
 #pragma unroll
         for (int p = 0; p < P; ++p) npl += plane[p] >= 0;
-        const int n = item.q1 - item.q0;
 
         // per channel slot: nu_k / c as float-float, whether the channel has
-        // a rest bin; the rest bins go to the warp's channel table
+        // a rest bin
         float nh[NS], nl[NS];
         bool act[NS];
 #pragma unroll
@@ -177,12 +196,10 @@ __global__ void __launch_bounds__(KMAX_THREADS) stack_mixed(RunArgs a)
             const int kk = q * 32 + lane;
             act[q] = false;
             nh[q] = nl[q] = 0.f;
-            if (kk < k_hi) {
-                const ChanF cf = a.chf[chf0 + kk];
-                nh[q] = cf.nuc_hi;
-                nl[q] = cf.nuc_lo;
-                act[q] = cf.nb > 0;
-                ctab[kk] = ChanS{cf.j0, cf.nb, cf.w0, cf.w1};
+            if (kk < nch) {
+                nh[q] = ctab[kk].nuc_hi;
+                nl[q] = ctab[kk].nuc_lo;
+                act[q] = ctab[kk].nb > 0;
             }
             if (act[q]) n_read += (unsigned long long)n * (unsigned long long)npl;
         }
@@ -198,13 +215,13 @@ __global__ void __launch_bounds__(KMAX_THREADS) stack_mixed(RunArgs a)
                 cnt[q][p] = 0;
             }
         }
-        int nstaged = 0;
+        uint32_t head = 0, count = 0;   // circular staging area
 
-        // All lanes write the staged runs to the cube, one run per lane.
+        // The warp writes min(count, 32) staged runs to the cube, one per lane.
         auto drain = [&]() {
             __syncwarp();
-            for (int e = lane; e < nstaged; e += 32) {
-                const Staged<P> st = stage[e];
+            if ((uint32_t)lane < count) {
+                const Staged<P> st = stage[(head + lane) & (STAGE_CAP - 1)];
                 uint32_t tot = 0;
 #pragma unroll
                 for (int p = 0; p < P; ++p) tot += plane[p] >= 0 ? st.cnt[p] : 0u;
@@ -212,7 +229,8 @@ __global__ void __launch_bounds__(KMAX_THREADS) stack_mixed(RunArgs a)
                     n_duv += tot;
                 } else {
                     n_ok += tot;
-                    const ChanS ct = ctab[st.kk];
+                    const ChanF &ct = ctab[st.kk];
+                    const int nb = ct.nb;
                     const size_t base = ((size_t)st.cell * nrest + ct.j0) * npol_c;
                     auto emit = [&](size_t e2, float ww) {
 #pragma unroll
@@ -233,39 +251,44 @@ __global__ void __launch_bounds__(KMAX_THREADS) stack_mixed(RunArgs a)
                         }
                     };
                     emit(base, ct.w0);
-                    if (ct.nb > 1) emit(base + (size_t)npol_c, ct.w1);
+                    if (nb > 1) emit(base + (size_t)npol_c, ct.w1);
                     // a third or fourth bin (lattices narrower than a channel)
-                    for (int b = 2; b < ct.nb; ++b)
-                        emit(base + (size_t)b * npol_c, (float)a.chd[chf0 + st.kk].w[b]);
+                    for (int b = 2; b < nb; ++b) emit(base + (size_t)b * npol_c, (float)a.chd[chf0 + st.kk].w[b]);
                 }
             }
             __syncwarp();
-            nstaged = 0;
+            const uint32_t k = count < 32u ? count : 32u;
+            head += k;
+            count -= k;
         };
-        // Stage the lane runs that end here (`fl`): slots by ballot.  The
-        // staging area is drained whenever fewer than 32 slots are free, so
-        // the slot index stays inside it; the check records a breach instead
-        // of writing out of bounds.
-        auto stage_runs = [&](int q, bool fl) {
-            const unsigned bal = __ballot_sync(0xffffffffu, fl);
-            if (bal) {
-                const int slot = nstaged + __popc(bal & lt_mask);
+        // A lane whose cell changes (`newcell`) stages its finished run
+        // (`fl`: it holds one) and starts a new one.  Before staging at most
+        // 31 runs wait, so the 32 new ones fit the 64 slots.
+        auto next_cell = [&](int q, int cid) {
+            const bool newcell = cid != cell[q];
+            if (__ballot_sync(0xffffffffu, newcell)) {
+                const bool fl = newcell && cell[q] != NO_RUN;
+                const unsigned bal = __ballot_sync(0xffffffffu, fl);
                 if (fl) {
-                    if (slot < STAGE_CAP) {
-                        Staged<P> &st = stage[slot];
-                        st.cell = cell[q];
-                        st.kk = q * 32 + lane;
+                    Staged<P> &st = stage[(head + count + __popc(bal & lt_mask)) & (STAGE_CAP - 1)];
+                    st.cell = cell[q];
+                    st.kk = q * 32 + lane;
 #pragma unroll
-                        for (int p = 0; p < P; ++p) {
-                            st.cnt[p] = cnt[q][p];
-                            st.acc[p] = acc[q][p];
-                        }
-                    } else {
-                        atomicExch(a.err, 3);
+                    for (int p = 0; p < P; ++p) {
+                        st.cnt[p] = cnt[q][p];
+                        st.acc[p] = acc[q][p];
                     }
                 }
-                nstaged += __popc(bal);
-                if (nstaged > STAGE_CAP - 32) drain();
+                count += __popc(bal);
+                if (count >= 32u) drain();
+                if (newcell) {
+                    cell[q] = cid;
+#pragma unroll
+                    for (int p = 0; p < P; ++p) {
+                        acc[q][p] = make_float4(0.f, 0.f, 0.f, 0.f);
+                        cnt[q][p] = 0;
+                    }
+                }
             }
         };
 
@@ -335,16 +358,7 @@ __global__ void __launch_bounds__(KMAX_THREADS) stack_mixed(RunArgs a)
                                              a.chd + chf0 + q * 32 + lane, gnu, gnv);
                         }
                     }
-                    const bool newcell = cid != cell[q];
-                    stage_runs(q, newcell && cell[q] != NO_RUN);
-                    if (newcell) {
-                        cell[q] = cid;
-#pragma unroll
-                        for (int p = 0; p < P; ++p) {
-                            acc[q][p] = make_float4(0.f, 0.f, 0.f, 0.f);
-                            cnt[q][p] = 0;
-                        }
-                    }
+                    next_cell(q, cid);
 #pragma unroll
                     for (int p = 0; p < P; ++p) {
                         const bool ok = ((F[q] >> (8 * p)) & 0xffu) == 0;
@@ -365,10 +379,10 @@ __global__ void __launch_bounds__(KMAX_THREADS) stack_mixed(RunArgs a)
             }
         }
         cp_async_wait<0>();
+        // the runs still open end with the item
 #pragma unroll
-        for (int q = 0; q < NS; ++q) stage_runs(q, cell[q] != NO_RUN);
-        drain();
-        s ^= 1;
+        for (int q = 0; q < NS; ++q) next_cell(q, NO_RUN);
+        while (count) drain();
     }
 
     // counters (the visibilities read are also counted on the host from the
