@@ -11,6 +11,19 @@ namespace vista {
 constexpr double C_LIGHT = 299792458.0;   // m/s
 constexpr int MAX_LOCAL_KEYS = 4096;      // cell keys inside one stripe (shared-memory histogram)
 
+// Channels per 4-byte word of flags (npol bytes per channel): the channel
+// ranges the mixed path reads start and end on multiples of this.
+__host__ __device__ inline int32_t flag_align_channels(int32_t npol) { return npol >= 4 ? 1 : 4 / npol; }
+
+// Flag rows of a window as the mixed path reads them: the flag array itself
+// when it starts on a 4-byte boundary and its rows are whole words, else a
+// copy of the channels read with the row pitch rounded up to a word.
+inline bool flags_direct(const void *flags, int32_t nchan, int32_t npol)
+{
+    return ((uintptr_t)flags % 4) == 0 && ((int64_t)nchan * npol) % 4 == 0;
+}
+inline int64_t flag_pitch(int32_t nin, int32_t npol) { return ((int64_t)nin * npol + 3) / 4 * 4; }
+
 // Cube geometry as the kernels see it.
 struct CubeGeom {
     int32_t nu, nv, nrest, npol;
@@ -42,7 +55,6 @@ struct SrcDev {
     const double *uvw;
     const void *vis;        // element (row, k, p) at (row * vstride + k - kbase) * npol + p
     const float *wts;
-    const uint8_t *flags;   // same indexing as vis
     int64_t nrow;
     int32_t nchan, npol;
     int32_t vis_type;
@@ -60,6 +72,12 @@ struct SrcDev {
     float key_su, key_sv;   // fl32(s_k) at the row-ordering reference channel
     int64_t rec_off;        // first row record of this window
     int64_t cell_off;       // first chunk-cell entry of this window ([chunk][row] inside)
+    // flag byte of (row r, channel k, pol p): fbase[r * fpitch + (k - fk0) * npol + p];
+    // fbase is 4-byte aligned and fpitch a multiple of 4 (null: no flags)
+    const uint8_t *fbase;
+    int64_t fpitch;
+    int32_t fk0;
+    int32_t pad3;
 };
 static_assert(sizeof(SrcDev) % 16 == 0, "SrcDev is copied in 16-byte units");
 
@@ -67,15 +85,16 @@ static_assert(sizeof(SrcDev) % 16 == 0, "SrcDev is copied in 16-byte units");
 // processing order.
 //   tau_hi + tau_lo  the delay tau (metres) as a float-float pair, so that
 //                    tau * nu_k / c is formed to ~1e-14 relative in FP32
-//   rowf             row index | (fold << 31)
-//   W[4]             the row's weights, negated for a folded row (the sign
-//                    conjugates the shifted visibility; |W| is the weight)
+//   W[4]             the row's weights (>= 0), negated for a folded row: the
+//                    sign conjugates the shifted visibility, |W| is the weight
+//                    (the sign bit of W[0] marks the fold, also for W = 0)
+//   row              the row index in the window's arrays
 struct __align__(16) RowRec {
     float tau_hi, tau_lo;
-    uint32_t rowf;
     float W[4];
-    uint32_t pad;
+    uint32_t row, pad;
 };
+static_assert(sizeof(RowRec) == 32, "RowRec is read as two 16-byte words");
 
 // uv cells of one (row, channel chunk), written by the pre-pass (8 B):
 //   x  the cell iv * nu + iu at the chunk's first channel, -1 off the grid
@@ -146,7 +165,7 @@ struct RunArgs {
     const ChanF *chf;
     const ChanD *chd;
     RowRec *recs;
-    int2 *ccells;               // chunk cells (+ 2 entries of padding for the bulk copies)
+    int2 *ccells;               // chunk cells (+ 4 entries of padding for the bulk copies)
     const int64_t *row_off;     // [nsrc+1] cumulative rows
     int64_t nrows_total;
     CubeGeom g;

@@ -24,8 +24,8 @@ __global__ void debug_mixed(RunArgs a, int src, double *ph_out, int32_t *cell_ou
     const int c0 = S.k_lo + chunk * 32 * NS;
     const RowRec rec = a.recs[S.rec_off + i];
     const int2 cc = a.ccells[S.cell_off + (int64_t)chunk * nrow + i];
-    const int64_t row = (int64_t)(rec.rowf & 0x7fffffffu);
-    const bool fold = (rec.rowf >> 31) != 0;
+    const int64_t row = rec.row;
+    const bool fold = signbit(rec.W[0]);
 #pragma unroll
     for (int q = 0; q < NS; ++q) {
         const int kk = q * 32 + lane, k = c0 + kk;
@@ -126,7 +126,7 @@ __global__ void __launch_bounds__(128) stack_fp64(RunArgs a, int only_src, doubl
                     const int q = S.plane[p];
                     if (q < 0) continue;
                     ++n_vis;
-                    if (S.flags && S.flags[vi + p]) {
+                    if (S.fbase && S.fbase[r * S.fpitch + (int64_t)(k - S.fk0) * npol + p]) {
                         ++n_flag;
                         continue;
                     }

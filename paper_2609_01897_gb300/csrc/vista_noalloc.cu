@@ -112,6 +112,12 @@ extern "C" int vista_stack_noalloc(const vista_cube_desc *c, const vista_source_
             hi = k + 1;
         }
     if (s->nrow == 0 || lo < 0) return VISTA_OK;   // nothing reaches the cube
+    {
+        // the range read starts and ends on whole words of flags (as vista_run)
+        const int32_t al = flag_align_channels(s->npol);
+        lo = lo / al * al;
+        hi = std::min(n, (hi + al - 1) / al * al);
+    }
     const double gu = 1.0 / (C_LIGHT * c->du), gv = 1.0 / (C_LIGHT * c->dv);
     const int32_t nin = hi - lo;
     std::vector<ChanF> chf((size_t)nin);
@@ -176,7 +182,9 @@ extern "C" int vista_stack_noalloc(const vista_cube_desc *c, const vista_source_
     const size_t o_rec = o;
     o += al256(sizeof(RowRec) * (size_t)nrow);
     const size_t o_cells = o;
-    o += al256(sizeof(int2) * ((size_t)nrow * (size_t)nchunk + 2));
+    o += al256(sizeof(int2) * ((size_t)nrow * (size_t)nchunk + 4));
+
+
     const size_t o_hist = o;
     o += al256(4 * (size_t)nstripe);
     const size_t o_qs = o;
@@ -199,6 +207,11 @@ extern "C" int vista_stack_noalloc(const vista_cube_desc *c, const vista_source_
     o += al256(sizeof(DevStats));
     const size_t o_err = o;
     o += 256;
+    // flags the kernel cannot read in words are copied with a word-aligned pitch
+    const bool repack = s->flags && !flags_direct(s->flags, n, s->npol);
+    const int64_t fpitch = repack ? flag_pitch(nin, s->npol) : (int64_t)n * s->npol;
+    const size_t o_flags = o;
+    if (repack) o += al256((size_t)nrow * (size_t)fpitch);
     if (o > NOALLOC_SCRATCH_BYTES)
         return fail(nullptr, VISTA_E_RANGE, "window needs %zu bytes of scratch; the no-allocation call has %zu", o,
                     NOALLOC_SCRATCH_BYTES);
@@ -212,7 +225,9 @@ extern "C" int vista_stack_noalloc(const vista_cube_desc *c, const vista_source_
     d.uvw = s->uvw;
     d.vis = s->vis;
     d.wts = s->weights;
-    d.flags = s->flags;
+    d.fbase = repack ? (const uint8_t *)(b + o_flags) : s->flags;
+    d.fpitch = fpitch;
+    d.fk0 = repack ? lo : 0;
     d.nrow = nrow;
     d.nchan = n;
     d.npol = s->npol;
@@ -241,6 +256,9 @@ extern "C" int vista_stack_noalloc(const vista_cube_desc *c, const vista_source_
     if (e == cudaSuccess) e = cudaMemcpyAsync(b + o_off, roff, sizeof roff, cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(b + o_chf, chf.data(), sizeof(ChanF) * chf.size(), cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(b + o_chd, chd.data(), sizeof(ChanD) * chd.size(), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess && repack)
+        e = cudaMemcpy2DAsync(b + o_flags, (size_t)fpitch, s->flags + (size_t)lo * s->npol, (size_t)n * s->npol,
+                              (size_t)nin * s->npol, (size_t)nrow, cudaMemcpyDeviceToDevice, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(b + o_stats, 0, sizeof(DevStats), st);
     if (e == cudaSuccess) e = cudaMemsetAsync(b + o_err, 0, sizeof(int32_t), st);
     if (e != cudaSuccess) return cuda_fail(nullptr, e, "scratch set-up");

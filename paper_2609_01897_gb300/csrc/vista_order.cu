@@ -261,13 +261,13 @@ __global__ void __launch_bounds__(256) k_records(RunArgs a)
     const double tau = u * S.l + v * S.m + wz * S.n1;
     RowRec rec;
     split_ff(tau, rec.tau_hi, rec.tau_lo);
-    rec.rowf = (uint32_t)r | (fold ? 0x80000000u : 0u);
+    rec.row = (uint32_t)r;
+    rec.pad = 0;
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
         const float wk = k < S.npol ? S.wts[r * S.npol + k] : 0.0f;
         rec.W[k] = fold ? -wk : wk;
     }
-    rec.pad = 0;
     a.recs[S.rec_off + q] = rec;
 
     // Chunk cells.  The cell index is monotone in frequency along each axis,

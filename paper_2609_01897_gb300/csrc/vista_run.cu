@@ -46,6 +46,14 @@ int plan_source(vista_stack *h, const SrcHost &s, double gu, double gv, Plan &pl
             hi = k + 1;
         }
     if (lo < 0) lo = hi = 0;
+    // The range read starts and ends on a multiple of a = 4 / gcd(npol, 4)
+    // channels (the added channels have no rest bin), so that a chunk's flag
+    // bytes are whole 4-byte words.
+    const int32_t al = flag_align_channels(s.d.npol);
+    if (hi > lo) {
+        lo = lo / al * al;
+        hi = std::min(n, (hi + al - 1) / al * al);
+    }
     pl.k_lo = lo;
     pl.k_hi = hi;
     pl.linear = linear_axis(s.freqs.data(), n, &pl.step);
@@ -205,16 +213,25 @@ extern "C" int vista_run(vista_stack *h)
     }
     if (chf.size() > (size_t)0x7fffffff) return fail(h, VISTA_E_RANGE, "too many channels in one run");
 
-    // 4. host-memory windows: staging layout (in-cube channels only)
+    // 4. staging layout: host-memory windows (the channels read only), and
+    //    the flags of device windows the mixed path cannot read in words
+    auto repack_flags = [&](const SrcHost &s) {
+        return !fp64 && s.d.mem == VISTA_MEM_DEVICE && s.d.flags && !flags_direct(s.d.flags, s.d.nchan, s.d.npol);
+    };
     size_t stage_bytes = 0;
     for (const ClassRun &cr : classes)
         for (int i : cr.members) {
             const SrcHost &s = h->pending[(size_t)i];
-            if (s.d.mem != VISTA_MEM_HOST) continue;
-            const size_t nr = (size_t)s.d.nrow, nin = (size_t)(plans[(size_t)i].k_hi - plans[(size_t)i].k_lo);
-            const size_t nvv = nr * nin * (size_t)s.d.npol;
-            stage_bytes += al256(nr * 24) + al256(nvv * vis_elem_bytes(s.d.vis_type)) +
-                           al256(nr * 4 * (size_t)s.d.npol) + (s.d.flags ? al256(nvv) : 0);
+            const size_t nr = (size_t)s.d.nrow;
+            const int32_t nin = plans[(size_t)i].k_hi - plans[(size_t)i].k_lo;
+            const size_t fbytes = s.d.flags ? al256(nr * (size_t)flag_pitch(nin, s.d.npol)) : 0;
+            if (s.d.mem == VISTA_MEM_HOST) {
+                const size_t nvv = nr * (size_t)nin * (size_t)s.d.npol;
+                stage_bytes += al256(nr * 24) + al256(nvv * vis_elem_bytes(s.d.vis_type)) +
+                               al256(nr * 4 * (size_t)s.d.npol) + fbytes;
+            } else if (repack_flags(s)) {
+                stage_bytes += fbytes;
+            }
         }
     if (stage_bytes) {
         e = h->b_stage.ensure(stage_bytes);
@@ -247,9 +264,11 @@ extern "C" int vista_run(vista_stack *h)
             d.uvw = s.d.uvw;
             d.vis = s.d.vis;
             d.wts = s.d.weights;
-            d.flags = s.d.flags;
             d.vstride = s.d.nchan;
             d.kbase = 0;
+            d.fbase = s.d.flags;
+            d.fpitch = (int64_t)s.d.nchan * s.d.npol;
+            d.fk0 = 0;
             if (s.d.mem == VISTA_MEM_HOST) {
                 const size_t nr = (size_t)s.d.nrow, P = (size_t)s.d.npol;
                 const size_t esz = vis_elem_bytes(s.d.vis_type);
@@ -262,9 +281,10 @@ extern "C" int vista_run(vista_stack *h)
                 char *p_w = base + stage_pos;
                 stage_pos += al256(nr * 4 * P);
                 char *p_f = nullptr;
+                const size_t fp = (size_t)flag_pitch(nin, s.d.npol);
                 if (s.d.flags) {
                     p_f = base + stage_pos;
-                    stage_pos += al256(nvv);
+                    stage_pos += al256(nr * fp);
                 }
                 const size_t row_in = (size_t)s.d.nchan * P, row_out = (size_t)nin * P;
                 e = cudaMemcpyAsync(p_uvw, s.d.uvw, nr * 24, cudaMemcpyHostToDevice, h->stream);
@@ -274,15 +294,28 @@ extern "C" int vista_run(vista_stack *h)
                 if (e == cudaSuccess)
                     e = cudaMemcpyAsync(p_w, s.d.weights, nr * 4 * P, cudaMemcpyHostToDevice, h->stream);
                 if (e == cudaSuccess && p_f)
-                    e = cudaMemcpy2DAsync(p_f, row_out, s.d.flags + (size_t)pl.k_lo * P, row_in, row_out, nr,
+                    e = cudaMemcpy2DAsync(p_f, fp, s.d.flags + (size_t)pl.k_lo * P, row_in, row_out, nr,
                                           cudaMemcpyHostToDevice, h->stream);
                 if (e != cudaSuccess) return cuda_fail(h, e, "host-to-device copy of a host-memory window");
                 d.uvw = (const double *)p_uvw;
                 d.vis = p_vis;
                 d.wts = (const float *)p_w;
-                d.flags = (const uint8_t *)p_f;
                 d.vstride = nin;
                 d.kbase = pl.k_lo;
+                d.fbase = (const uint8_t *)p_f;
+                d.fpitch = (int64_t)fp;
+                d.fk0 = pl.k_lo;
+            } else if (repack_flags(s)) {
+                const size_t nr = (size_t)s.d.nrow, P = (size_t)s.d.npol;
+                const size_t fp = (size_t)flag_pitch(nin, s.d.npol);
+                char *p_f = (char *)h->b_stage.p + stage_pos;
+                stage_pos += al256(nr * fp);
+                e = cudaMemcpy2DAsync(p_f, fp, s.d.flags + (size_t)pl.k_lo * P, (size_t)s.d.nchan * P,
+                                      (size_t)nin * P, nr, cudaMemcpyDeviceToDevice, h->stream);
+                if (e != cudaSuccess) return cuda_fail(h, e, "flag repacking copy");
+                d.fbase = (const uint8_t *)p_f;
+                d.fpitch = (int64_t)fp;
+                d.fk0 = pl.k_lo;
             }
             d.nrow = s.d.nrow;
             d.nchan = s.d.nchan;
@@ -336,8 +369,9 @@ extern "C" int vista_run(vista_stack *h)
     if (!fp64) {
         if ((e = h->b_recs.ensure((size_t)(rec_total > 0 ? rec_total : 1) * sizeof(RowRec))) != cudaSuccess)
             return cuda_fail(h, e, "row record allocation");
-        // two entries of padding: a chunk-cell bulk copy may read one past the end
-        if ((e = h->b_cells.ensure((size_t)(cell_total + 2) * sizeof(int2))) != cudaSuccess)
+        // padding: the bulk copy of an item's chunk cells starts and ends on
+        // 16-byte boundaries, up to one entry past the last
+        if ((e = h->b_cells.ensure((size_t)(cell_total + 4) * sizeof(int2))) != cudaSuccess)
             return cuda_fail(h, e, "chunk cell allocation");
         if ((e = h->b_sort.ensure(sort_bytes > 0 ? sort_bytes : 256)) != cudaSuccess)
             return cuda_fail(h, e, "ordering buffer allocation");

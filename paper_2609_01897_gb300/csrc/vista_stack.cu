@@ -6,9 +6,10 @@
 // processes an item, TMA bulk copies (one mbarrier per slot) bring the next
 // item's row records, chunk cells, window header, channel table and work-list
 // entries into the other shared-memory slot, so an item starts without a
-// global round trip.  Inside an item the visibilities of the next D - 1 rows
-// are in flight into a shared-memory ring (cp.async), their flags in
-// registers.
+// global round trip.  Inside an item the visibilities and flags of the next
+// D - 1 rows are in flight into a shared-memory ring (cp.async; a chunk's
+// flag bytes are whole 4-byte words, see flag_align_channels), so the row
+// loop waits on no synchronous global load.
 //
 // Per (row, channel): the FP32 phasor of Eq. 2 from the record's float-float
 // delay and the channel's float-float nu_k / c, the uv cell from the chunk's
@@ -31,6 +32,9 @@ constexpr int KMAX_THREADS = 256;   // blocks of at most 8 warps
 constexpr int STAGE_CAP = 64;       // staged runs per warp (circular; a power of two)
 constexpr int NO_RUN = INT_MIN;     // lane holds no run
 
+// What a window without flags reads as its flags (every row: pitch 0).
+__device__ __align__(16) uint8_t g_zero_flags[512];
+
 // One finished run of one channel slot.
 template <int P>
 struct __align__(16) Staged {
@@ -45,19 +49,19 @@ struct __align__(16) Staged {
 __host__ __device__ constexpr int cc_slot_entries(int rb) { return (rb + 3) & ~1; }
 
 // One item slot in shared memory (filled by bulk copies).
-template <int NS>
+template <int P, int NS>
 __host__ __device__ constexpr size_t slot_bytes(int rb)
 {
     return 2 * sizeof(Item) + sizeof(SrcDev) + 32 * NS * sizeof(ChanF) + (size_t)rb * sizeof(RowRec) +
            (size_t)cc_slot_entries(rb) * sizeof(int2);
 }
 
-// Per-warp shared memory: two item slots, the D-row visibility ring, the
-// staging area and two mbarriers.
+// Per-warp shared memory: two item slots, the D-row visibility and flag
+// rings, the staging area and two mbarriers.
 template <int P, int VT, int NS, int D>
 __host__ __device__ constexpr size_t warp_smem_bytes(int rb)
 {
-    return 2 * slot_bytes<NS>(rb) + (size_t)D * NS * 32 * VisAsync<P, VT>::kLaneBytes +
+    return 2 * slot_bytes<P, NS>(rb) + (size_t)D * NS * 32 * (VisAsync<P, VT>::kLaneBytes + P) +
            STAGE_CAP * sizeof(Staged<P>) + 2 * sizeof(uint64_t);
 }
 
@@ -83,15 +87,19 @@ struct Slot {
 template <int P, int VT, int NS, int D>
 __global__ void __launch_bounds__(KMAX_THREADS) stack_mixed(RunArgs a)
 {
+    static_assert(D >= 2 && (D & (D - 1)) == 0, "ring depth: a power of two");
     using VA = VisAsync<P, VT>;
     constexpr int LB = VA::kLaneBytes;
+    constexpr int FWD = 8 * NS * P;             // flag words of one (row, chunk)
+    constexpr int FPL = (FWD + 31) / 32;        // of which each lane copies up to FPL
     extern __shared__ __align__(16) unsigned char smem[];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const int RB = a.so.rows_per_item;
     unsigned char *wsm = smem + (size_t)wid * warp_smem_bytes<P, VT, NS, D>(RB);
-    auto slot_at = [&](int s) { return Slot<NS>(wsm + (size_t)s * slot_bytes<NS>(RB), RB); };
-    unsigned char *vring = wsm + 2 * slot_bytes<NS>(RB);
-    Staged<P> *stage = reinterpret_cast<Staged<P> *>(vring + (size_t)D * NS * 32 * LB);
+    auto slot_at = [&](int s) { return Slot<NS>(wsm + (size_t)s * slot_bytes<P, NS>(RB), RB); };
+    unsigned char *vring = wsm + 2 * slot_bytes<P, NS>(RB);
+    unsigned char *fring = vring + (size_t)D * NS * 32 * LB;
+    Staged<P> *stage = reinterpret_cast<Staged<P> *>(fring + (size_t)D * FWD * 4);
     uint64_t *bars = reinterpret_cast<uint64_t *>(stage + STAGE_CAP);
     if (lane == 0) {
         mbar_init(&bars[0], 1);
@@ -101,6 +109,7 @@ __global__ void __launch_bounds__(KMAX_THREADS) stack_mixed(RunArgs a)
     __syncwarp();
     const uint32_t vring_lane = smem_addr(vring) + (uint32_t)lane * LB;
     const unsigned char *vring_lane_p = vring + lane * LB;
+    const uint32_t fring_lane = smem_addr(vring) + (uint32_t)(D * NS * 32 * LB) + 4u * (uint32_t)lane;
 
     const uint32_t nitems = a.so.ctr[0];
     const uint32_t G = gridDim.x * (blockDim.x >> 5);
@@ -110,7 +119,22 @@ __global__ void __launch_bounds__(KMAX_THREADS) stack_mixed(RunArgs a)
     float4 *cube4 = reinterpret_cast<float4 *>(a.cube);
     // visibilities read, stacked (unflagged, on the grid) and dropped off the
     // grid; flagged = read - stacked - dropped
-    unsigned long long n_read = 0, n_ok = 0, n_duv = 0, n_red = 0;
+    uint32_t n_read = 0, n_ok = 0, n_duv = 0, n_red = 0;
+    // warp sums of the counters, one atomic per counter per warp (at the
+    // end, or early if a lane's count nears 2^32)
+    auto flush_counters = [&]() {
+        unsigned long long c3[3] = {(unsigned long long)n_read - n_ok - n_duv, n_duv, n_red};
+#pragma unroll
+        for (int k = 0; k < 3; ++k)
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) c3[k] += __shfl_xor_sync(0xffffffffu, c3[k], o);
+        if (lane == 0) {
+            if (c3[0]) atomicAdd(&a.stats->n_flagged, c3[0]);
+            if (c3[1]) atomicAdd(&a.stats->n_dropped_uv, c3[1]);
+            if (c3[2]) atomicAdd(&a.stats->n_reductions, c3[2]);
+        }
+        n_read = n_ok = n_duv = n_red = 0;
+    };
     uint32_t phase = 0;   // bit s: parity of the next completion of slot s
 
     // Lane 0: bulk copies of item `it` (its entry `item`) into slot s,
@@ -155,29 +179,37 @@ __global__ void __launch_bounds__(KMAX_THREADS) stack_mixed(RunArgs a)
         // ---- one item ----
         // window fields in registers (the cube reductions could alias global
         // memory, so reads through pointers would be repeated)
-        const unsigned char *vis;
-        const uint8_t *flags;
+        const RowRec *rb = S.rec;
+        const ChanF *ctab = S.chf;
+        const int2 *cb;
+        const unsigned char *vis0;   // the chunk's first channel of row 0
+        uint32_t vrow_bytes;         // visibility bytes per row
+        const uint8_t *fw0;          // this lane's first flag word of the chunk in row 0
+        uint32_t frow_bytes;         // flag bytes per row (0: no flags, all zero)
+        int nfw;                     // flag words of the chunk
         const double *uvw;
-        int64_t vstride;
         float vscale;
         int nch, chf0, n;
         int plane[P];
-        const int2 *cb;
-        const RowRec *rb = S.rec;
-        const ChanF *ctab = S.chf;
         {
             const SrcDev &H = *S.hdr;
             const Item &I = *S.self;
             uvw = H.uvw;
-            vstride = H.vstride;
             vscale = H.vis_scale;
             nch = I.nch;
             chf0 = I.chf0;
             n = I.q1 - I.q0;
-            const int c0g = H.k_lo + I.chunk * 32 * NS;
-            vis = reinterpret_cast<const unsigned char *>(H.vis) + (int64_t)(c0g + lane - H.kbase) * LB;
-            flags = H.flags;
-            if (flags) flags += (int64_t)(c0g + lane - H.kbase) * P;
+            const int64_t c0 = (int64_t)(H.k_lo + I.chunk * 32 * NS - H.kbase);
+            vis0 = reinterpret_cast<const unsigned char *>(H.vis) + c0 * LB;
+            vrow_bytes = (uint32_t)(H.vstride * LB);
+            if (H.fbase) {
+                fw0 = H.fbase + (int64_t)(H.k_lo + I.chunk * 32 * NS - H.fk0) * P + 4 * lane;
+                frow_bytes = (uint32_t)H.fpitch;
+            } else {
+                fw0 = g_zero_flags + 4 * lane;
+                frow_bytes = 0;
+            }
+            nfw = (I.nch * P + 3) / 4;
 #pragma unroll
             for (int p = 0; p < P; ++p) plane[p] = H.plane[p];
             cb = S.cells + (I.cell0 & 1);
@@ -188,31 +220,54 @@ __global__ void __launch_bounds__(KMAX_THREADS) stack_mixed(RunArgs a)
         for (int p = 0; p < P; ++p) npl += plane[p] >= 0;
 
         // per channel slot: nu_k / c as float-float, whether the channel has
-        // a rest bin
+        // a rest bin, and the lane's byte offsets (lanes past the chunk's last
+        // channel read that channel: always inside the row)
         float nh[NS], nl[NS];
         bool act[NS];
+        int kv[NS];
 #pragma unroll
         for (int q = 0; q < NS; ++q) {
-            const int kk = q * 32 + lane;
-            act[q] = false;
-            nh[q] = nl[q] = 0.f;
-            if (kk < nch) {
-                nh[q] = ctab[kk].nuc_hi;
-                nl[q] = ctab[kk].nuc_lo;
-                act[q] = ctab[kk].nb > 0;
-            }
-            if (act[q]) n_read += (unsigned long long)n * (unsigned long long)npl;
+            const int kk = q * 32 + lane, kc = min(kk, nch - 1);
+            nh[q] = ctab[kc].nuc_hi;
+            nl[q] = ctab[kc].nuc_lo;
+            act[q] = kk < nch && ctab[kc].nb > 0;
+            kv[q] = kc * LB;
+            if (act[q]) n_read += (uint32_t)(n * npl);
         }
+
+        // the cell of channel slot q in row i (NO_RUN for a lane without a
+        // channel); chunk entries are shared by the warp, so the branches are
+        // taken by all lanes alike
+        auto lane_cell = [&](int q, int2 cc, int i) -> int {
+            int cid;
+            if (__all_sync(0xffffffffu, cc.y == CC_NOCHANGE)) {
+                cid = cc.x;
+            } else if (__all_sync(0xffffffffu, cc.y != CC_MIXED)) {
+                cid = chunk_cell_step(cc, q * 32 + lane, gnu);
+            } else {
+                cid = NO_RUN;
+                if (act[q]) {
+                    const float4 r0 = *reinterpret_cast<const float4 *>(&rb[i]);
+                    cid = cell_exact(uvw, rb[i].row, signbit(r0.z), a.chd + chf0 + q * 32 + lane, gnu,
+                                     gnv);
+                }
+            }
+            return act[q] ? cid : NO_RUN;
+        };
+
         int cell[NS];
         float4 acc[NS][P];
         uint32_t cnt[NS][P];
+        {
+            const int2 cc0 = cb[0];
 #pragma unroll
-        for (int q = 0; q < NS; ++q) {
-            cell[q] = NO_RUN;
+            for (int q = 0; q < NS; ++q) {
+                cell[q] = lane_cell(q, cc0, 0);
 #pragma unroll
-            for (int p = 0; p < P; ++p) {
-                acc[q][p] = make_float4(0.f, 0.f, 0.f, 0.f);
-                cnt[q][p] = 0;
+                for (int p = 0; p < P; ++p) {
+                    acc[q][p] = make_float4(0.f, 0.f, 0.f, 0.f);
+                    cnt[q][p] = 0;
+                }
             }
         }
         uint32_t head = 0, count = 0;   // circular staging area
@@ -261,14 +316,13 @@ __global__ void __launch_bounds__(KMAX_THREADS) stack_mixed(RunArgs a)
             head += k;
             count -= k;
         };
-        // A lane whose cell changes (`newcell`) stages its finished run
-        // (`fl`: it holds one) and starts a new one.  Before staging at most
-        // 31 runs wait, so the 32 new ones fit the 64 slots.
+        // A lane whose cell changes stages its finished run and starts a new
+        // one.  Before staging at most 31 runs wait, so 32 new ones fit the
+        // 64 slots.
         auto next_cell = [&](int q, int cid) {
-            const bool newcell = cid != cell[q];
-            if (__ballot_sync(0xffffffffu, newcell)) {
-                const bool fl = newcell && cell[q] != NO_RUN;
-                const unsigned bal = __ballot_sync(0xffffffffu, fl);
+            const bool fl = cid != cell[q];
+            const unsigned bal = __ballot_sync(0xffffffffu, fl);
+            if (bal) {
                 if (fl) {
                     Staged<P> &st = stage[(head + count + __popc(bal & lt_mask)) & (STAGE_CAP - 1)];
                     st.cell = cell[q];
@@ -278,10 +332,6 @@ __global__ void __launch_bounds__(KMAX_THREADS) stack_mixed(RunArgs a)
                         st.cnt[p] = cnt[q][p];
                         st.acc[p] = acc[q][p];
                     }
-                }
-                count += __popc(bal);
-                if (count >= 32u) drain();
-                if (newcell) {
                     cell[q] = cid;
 #pragma unroll
                     for (int p = 0; p < P; ++p) {
@@ -289,114 +339,84 @@ __global__ void __launch_bounds__(KMAX_THREADS) stack_mixed(RunArgs a)
                         cnt[q][p] = 0;
                     }
                 }
+                count += __popc(bal);
+                if (count >= 32u) drain();
             }
         };
 
-        // D-row ring: visibilities by cp.async into shared memory (one
-        // commit group per row), flags in registers
-        uint32_t RF[D][NS];
-#pragma unroll
-        for (int d = 0; d < D; ++d)
-#pragma unroll
-            for (int q = 0; q < NS; ++q) RF[d][q] = 0;
+        // D-row rings of visibilities and flags, filled by cp.async (one
+        // commit group per row); row i sits in slot i mod D.  Lane j copies
+        // flag words j, j + 32, ... of the chunk (each inside the row).
         auto fetch = [&](int d, int i) {
-            const int64_t off = (int64_t)(rb[i].rowf & 0x7fffffffu) * vstride;
+            const uint32_t row = rb[i].row;
+            const unsigned char *vrow = vis0 + (uint64_t)row * vrow_bytes;
+#pragma unroll
+            for (int q = 0; q < NS; ++q)
+                VA::copy(vring_lane + (uint32_t)((d * NS + q) * 32 * LB), vrow + kv[q]);
+            const uint8_t *frow = fw0 + (uint64_t)row * frow_bytes;
+#pragma unroll
+            for (int t = 0; t < FPL; ++t)
+                if (lane + 32 * t < nfw) cp_async_4(fring_lane + (uint32_t)(d * FWD * 4 + 128 * t), frow + 128 * t);
+        };
+        auto body = [&](int i, int d) {
+            const float4 r0 = *reinterpret_cast<const float4 *>(&rb[i]);   // tau_hi, tau_lo, W0, W1
+            float W[P];
+            W[0] = r0.z;
+            if constexpr (P > 1) W[1] = r0.w;
+            if constexpr (P > 2) {
+                const float2 r1 = *reinterpret_cast<const float2 *>(&rb[i].W[2]);
+                W[2] = r1.x;
+                W[3] = r1.y;
+            }
+            const int2 cc = cb[i];
 #pragma unroll
             for (int q = 0; q < NS; ++q) {
-                if (act[q]) {
-                    VA::copy(vring_lane + (uint32_t)((d * NS + q) * 32 * LB), vis + (off + q * 32) * LB);
-                    RF[d][q] = load_flags<P>(flags, off + q * 32);
+                float2 V[P];
+                VA::decode(vring_lane_p + (size_t)(d * NS + q) * 32 * LB, vscale, V);
+                const uint32_t F = ld_flags_smem<P>(fring + d * FWD * 4 + (q * 32 + lane) * P);
+                const float2 ph = shift_phasor(r0.x, r0.y, nh[q], nl[q]);
+                next_cell(q, lane_cell(q, cc, i));
+#pragma unroll
+                for (int p = 0; p < P; ++p) {
+                    const bool ok = ((F >> (8 * p)) & 0xffu) == 0;
+                    const float2 v = V[p];
+                    const float re = v.x * ph.x - v.y * ph.y;
+                    const float im = v.x * ph.y + v.y * ph.x;
+                    const float a2 = v.x * v.x + v.y * v.y;
+                    const float Ws = W[p], Wa = fabsf(Ws);   // the sign conjugates folded rows
+                    acc[q][p].x = ok ? __fmaf_rn(Wa, re, acc[q][p].x) : acc[q][p].x;
+                    acc[q][p].y = ok ? __fmaf_rn(Ws, im, acc[q][p].y) : acc[q][p].y;
+                    acc[q][p].z = ok ? acc[q][p].z + Wa : acc[q][p].z;
+                    acc[q][p].w = ok ? __fmaf_rn(Wa, a2, acc[q][p].w) : acc[q][p].w;
+                    cnt[q][p] += ok ? 1u : 0u;
                 }
             }
         };
+
 #pragma unroll
         for (int d = 0; d < D - 1; ++d) {
-            if (d < n) fetch(d, d);
+            fetch(d, min(d, n - 1));
             cp_async_commit();
         }
-
-        for (int i0 = 0; i0 < n; i0 += D) {
-#pragma unroll
-            for (int d = 0; d < D; ++d) {
-                const int i = i0 + d;
-                if (i >= n) break;
-                if (i + D - 1 < n) fetch((d + D - 1) % D, i + D - 1);
-                cp_async_commit();
-                cp_async_wait<D - 1>();
-                float2 V[NS][P];
-                uint32_t F[NS];
-#pragma unroll
-                for (int q = 0; q < NS; ++q) {
-                    F[q] = RF[d][q];
-                    VA::decode(vring_lane_p + (size_t)(d * NS + q) * 32 * LB, vscale, V[q]);
-                }
-
-                const float4 r0 = *reinterpret_cast<const float4 *>(&rb[i]);   // tau_hi, tau_lo, rowf, W0
-                float W[P];
-                W[0] = r0.w;
-                if constexpr (P > 1) {
-                    const float4 r1 = *reinterpret_cast<const float4 *>(&rb[i].W[1]);
-                    W[1] = r1.x;
-                    if constexpr (P > 2) {
-                        W[2] = r1.y;
-                        W[3] = r1.z;
-                    }
-                }
-                const int2 cc = cb[i];
-#pragma unroll
-                for (int q = 0; q < NS; ++q) {
-                    const float2 ph = shift_phasor(r0.x, r0.y, nh[q], nl[q]);
-                    int cid = cell[q];
-                    if (act[q]) {
-                        if (cc.y == CC_NOCHANGE) {
-                            cid = cc.x;
-                        } else if (cc.y != CC_MIXED) {
-                            cid = chunk_cell_step(cc, q * 32 + lane, gnu);
-                        } else {
-                            const uint32_t rowf = __float_as_uint(r0.z);
-                            cid = cell_exact(uvw, (int64_t)(rowf & 0x7fffffffu), (rowf >> 31) != 0,
-                                             a.chd + chf0 + q * 32 + lane, gnu, gnv);
-                        }
-                    }
-                    next_cell(q, cid);
-#pragma unroll
-                    for (int p = 0; p < P; ++p) {
-                        const bool ok = ((F[q] >> (8 * p)) & 0xffu) == 0;
-                        const float2 v = V[q][p];
-                        const float re = v.x * ph.x - v.y * ph.y;
-                        const float im = v.x * ph.y + v.y * ph.x;
-                        const float a2 = v.x * v.x + v.y * v.y;
-                        const float Ws = W[p], Wa = fabsf(Ws);   // the sign conjugates folded rows
-                        if (ok) {
-                            acc[q][p].x += Wa * re;
-                            acc[q][p].y += Ws * im;
-                            acc[q][p].z += Wa;
-                            acc[q][p].w += Wa * a2;
-                            cnt[q][p] += 1;
-                        }
-                    }
-                }
-            }
+#pragma unroll 1
+        for (int i = 0; i < n; ++i) {
+            // rows past the item re-read its last row into a slot nobody reads
+            fetch((i + D - 1) & (D - 1), min(i + D - 1, n - 1));
+            cp_async_commit();
+            cp_async_wait<D - 1>();
+            body(i, i & (D - 1));
         }
         cp_async_wait<0>();
         // the runs still open end with the item
 #pragma unroll
         for (int q = 0; q < NS; ++q) next_cell(q, NO_RUN);
         while (count) drain();
+        if (__any_sync(0xffffffffu, (n_read | n_ok | n_duv | n_red) >= 0x40000000u)) flush_counters();
     }
 
     // counters (the visibilities read are also counted on the host from the
-    // channel tables): warp sum, one atomic per counter per warp
-    unsigned long long c3[3] = {n_read - n_ok - n_duv, n_duv, n_red};
-#pragma unroll
-    for (int k = 0; k < 3; ++k)
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) c3[k] += __shfl_xor_sync(0xffffffffu, c3[k], o);
-    if (lane == 0) {
-        if (c3[0]) atomicAdd(&a.stats->n_flagged, c3[0]);
-        if (c3[1]) atomicAdd(&a.stats->n_dropped_uv, c3[1]);
-        if (c3[2]) atomicAdd(&a.stats->n_reductions, c3[2]);
-    }
+    // channel tables)
+    flush_counters();
 }
 
 // --------------------------------------------------------------- launchers
