@@ -206,6 +206,19 @@ int vista_enable_timing(vista_stack *h, int on);
 /* Waits for the stream, then reports the totals since timing was enabled. */
 int vista_get_timing(vista_stack *h, vista_timing *out);
 
+/* CUDA-graph replay of a run's device work (on by default).  The device work
+ * of a run (flag repacking copies, the row-ordering pre-pass and the stacking
+ * launches: the paper's one batched launch per set of measurement sets,
+ * Sec. 3.3) is captured in a graph the second time an unchanged source set
+ * is run, and replayed, without host planning, while the set stays
+ * unchanged: the same arrays (pointers), shapes, frequencies, positions,
+ * redshifts, pol maps, tuning and lattice.  The contents of the arrays may
+ * change between runs.  Runs with host-memory sources, and runs while timing
+ * is enabled, are planned and launched directly.  on = 0 disables replay. */
+int vista_enable_graphs(vista_stack *h, int on);
+/* Number of runs replayed from a graph since the handle was opened. */
+int vista_graph_runs(vista_stack *h, uint64_t *out);
+
 /* Wait for the stream, free every device and host resource, and forget the
  * handle; any later call with it returns E_STATE. */
 int vista_close(vista_stack *h);

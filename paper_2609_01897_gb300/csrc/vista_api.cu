@@ -110,6 +110,19 @@ void span_end(vista_stack *h, int id)
     if (id >= 0) cudaEventRecord(h->spans[(size_t)id].b, h->stream);
 }
 
+uint64_t fnv1a(const void *p, size_t n, uint64_t h)
+{
+    const unsigned char *b = static_cast<const unsigned char *>(p);
+    for (size_t i = 0; i < n; ++i) h = (h ^ b[i]) * 1099511628211ull;
+    return h;
+}
+
+void drop_graph(vista_stack *h)
+{
+    if (h->gexec) cudaGraphExecDestroy(h->gexec);
+    h->gexec = nullptr;
+}
+
 size_t vis_elem_bytes(int vt)
 {
     switch (vt) {
@@ -232,6 +245,7 @@ extern "C" int vista_add_source(vista_stack *h, const vista_source_desc *s)
     SrcHost sh;
     sh.d = *s;
     sh.freqs.assign(s->freqs, s->freqs + s->nchan);
+    sh.freq_digest = fnv1a(sh.freqs.data(), sh.freqs.size() * sizeof(double));
     sh.pol_map.resize((size_t)s->npol);
     for (int p = 0; p < s->npol; ++p) {
         const int32_t q = s->pol_map ? s->pol_map[p] : p;
@@ -380,6 +394,8 @@ extern "C" int vista_set_tuning(vista_stack *h, const vista_tuning *t)
         c.prefetch_rows = t->prefetch_rows;
     }
     h->cfg = c;
+    drop_graph(h);
+    h->plan_valid = false;
     return VISTA_OK;
 }
 
@@ -430,6 +446,23 @@ extern "C" int vista_get_timing(vista_stack *h, vista_timing *out)
     return VISTA_OK;
 }
 
+extern "C" int vista_enable_graphs(vista_stack *h, int on)
+{
+    CHECK_HANDLE(h);
+    if (on != 0 && on != 1) return fail(h, VISTA_E_ARG, "on must be 0 or 1");
+    h->graphs = on != 0;
+    if (!h->graphs) drop_graph(h);
+    return VISTA_OK;
+}
+
+extern "C" int vista_graph_runs(vista_stack *h, uint64_t *out)
+{
+    CHECK_HANDLE(h);
+    if (!out) return fail(h, VISTA_E_ARG, "null output");
+    *out = h->graph_launches;
+    return VISTA_OK;
+}
+
 extern "C" int vista_close(vista_stack *h)
 {
     CHECK_HANDLE(h);
@@ -443,6 +476,8 @@ extern "C" int vista_close(vista_stack *h)
         cudaEventDestroy(s.b);
     }
     for (cudaEvent_t ev : h->ev_pool) cudaEventDestroy(ev);
+    drop_graph(h);
+    if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
     cudaFree(h->cube);
     cudaFree(h->count);
     cudaFree(h->stats);

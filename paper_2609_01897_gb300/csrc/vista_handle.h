@@ -40,6 +40,15 @@ struct SrcHost {
     vista_source_desc d;
     std::vector<double> freqs;
     std::vector<int32_t> pol_map;   // npol entries (identity filled in)
+    uint64_t freq_digest = 0;       // FNV-1a of the frequency bytes
+};
+
+// A device-to-device 2-D copy of a run's device pass (flag repacking).
+struct Copy2D {
+    void *dst;
+    size_t dpitch;
+    const void *src;
+    size_t spitch, width, height;
 };
 
 // One launch class of a run: windows that share the kernel instantiation.
@@ -72,7 +81,16 @@ struct vista_stack {
     int32_t *err = nullptr;
     vista::DevBuf b_srcs, b_chf, b_chd, b_recs, b_cells, b_off, b_stage, b_unpack, b_sort;
     std::vector<vista::ClassRun> classes;
-    vista::LaunchCfg cfg{64, 1, 4, 1, 2};
+    std::vector<vista::Copy2D> copies;   // device copies of the last planned run
+    vista::LaunchCfg cfg{48, 1, 4, 1, 4};
+    // CUDA-graph replay of the device pass while the source set is unchanged
+    bool graphs = true;
+    bool plan_valid = false;             // device tables hold the plan of `plan_sig`
+    std::vector<uint8_t> plan_sig;
+    uint64_t plan_nvis = 0;
+    cudaStream_t cap_stream = nullptr;   // capture stream (handle-owned)
+    cudaGraphExec_t gexec = nullptr;
+    uint64_t graph_launches = 0;
     // stripe geometry of the row ordering (depends on the cube only)
     int32_t stripe_rows = 1, nstripe = 1, ushift = 0, nuk = 1;
     std::string msg;
@@ -90,5 +108,7 @@ int cuda_fail(vista_stack *h, cudaError_t e, const char *what);
 int span_begin(vista_stack *h, int kind);
 void span_end(vista_stack *h, int id);
 size_t vis_elem_bytes(int vt);
+uint64_t fnv1a(const void *p, size_t n, uint64_t h = 1469598103934665603ull);
+void drop_graph(vista_stack *h);
 
 }  // namespace vista

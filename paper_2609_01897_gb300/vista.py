@@ -95,6 +95,8 @@ SIGNATURES = {
     "vista_debug_cells": (C.c_int, [_P, C.c_int32, _P]),
     "vista_debug_order": (C.c_int, [_P, C.c_int32, _P]),
     "vista_stack_noalloc": (C.c_int, [C.POINTER(CubeDesc), C.POINTER(SourceDesc), _P, _P]),
+    "vista_enable_graphs": (C.c_int, [_P, C.c_int]),
+    "vista_graph_runs": (C.c_int, [_P, C.POINTER(C.c_uint64)]),
 }
 
 _lib = None
@@ -253,6 +255,15 @@ class Stack:
         t = Timing()
         _check("vista_get_timing", lib().vista_get_timing(self.h, C.byref(t)), self.h)
         return t.as_dict()
+
+    def enable_graphs(self, on=True):
+        """Replay the device work of an unchanged source set from a CUDA graph (default on)."""
+        _check("vista_enable_graphs", lib().vista_enable_graphs(self.h, 1 if on else 0), self.h)
+
+    def graph_runs(self):
+        n = C.c_uint64(0)
+        _check("vista_graph_runs", lib().vista_graph_runs(self.h, C.byref(n)), self.h)
+        return int(n.value)
 
     def debug_phasors(self, src, nrow, nchan):
         out = torch.zeros((nrow, nchan, 2), dtype=torch.float64, device="cuda")
