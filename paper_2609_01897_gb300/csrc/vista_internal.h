@@ -167,6 +167,8 @@ struct RunArgs {
     RowRec *recs;
     int2 *ccells;               // chunk cells (+ 4 entries of padding for the bulk copies)
     const int64_t *row_off;     // [nsrc+1] cumulative rows
+    const int64_t *cell_cum;    // [nsrc+1] cumulative (row, chunk) entries (mixed path)
+    int64_t ncells_total;
     int64_t nrows_total;
     CubeGeom g;
     void *cube;                 // float4 (mixed) or double[4] (FP64) per entry

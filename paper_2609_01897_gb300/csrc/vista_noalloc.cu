@@ -174,7 +174,7 @@ extern "C" int vista_stack_noalloc(const vista_cube_desc *c, const vista_source_
     const size_t o_src = o;
     o += al256(sizeof(SrcDev));
     const size_t o_off = o;
-    o += al256(2 * sizeof(int64_t));
+    o += al256(4 * sizeof(int64_t));
     const size_t o_chf = o;
     o += al256(sizeof(ChanF) * (size_t)nin);
     const size_t o_chd = o;
@@ -249,7 +249,7 @@ extern "C" int vista_stack_noalloc(const vista_cube_desc *c, const vista_source_
     d.key_sv = (float)(s->freqs[key_ch] * gv);
     d.rec_off = 0;
     d.cell_off = 0;
-    const int64_t roff[2] = {0, nrow};
+    const int64_t roff[4] = {0, nrow, 0, nrow * nchunk};   // rows, then (row, chunk) entries
 
     // tables into scratch; counters and the error word start at zero
     e = cudaMemcpyAsync(b + o_src, &d, sizeof d, cudaMemcpyHostToDevice, st);
@@ -272,6 +272,8 @@ extern "C" int vista_stack_noalloc(const vista_cube_desc *c, const vista_source_
     a.recs = (RowRec *)(b + o_rec);
     a.ccells = (int2 *)(b + o_cells);
     a.row_off = (const int64_t *)(b + o_off);
+    a.cell_cum = a.row_off + 2;
+    a.ncells_total = nrow * nchunk;
     a.nrows_total = nrow;
     a.g = CubeGeom{c->nu, c->nv, c->nrest, c->npol, gu, gv, c->hermitian_fold, 0};
     a.cube = cube4;

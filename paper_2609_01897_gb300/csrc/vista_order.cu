@@ -15,8 +15,8 @@
 //   k_scatter      rows grouped by bucket
 //   k_bucket_sort  one block per bucket: counting sort by local cell key
 //   k_records      per row, in processing order: the FP64 delay of Eq. 2 as
-//                  a float-float pair and the (fold-signed) weights; per
-//                  (row, channel chunk): the chunk's uv cells
+//                  a float-float pair and the (fold-signed) weights
+//   k_cells        per (row, channel chunk): the chunk's uv cells
 #include "vista_device.cuh"
 
 namespace vista {
@@ -269,45 +269,58 @@ __global__ void __launch_bounds__(256) k_records(RunArgs a)
         rec.W[k] = fold ? -wk : wk;
     }
     a.recs[S.rec_off + q] = rec;
+}
 
-    // Chunk cells.  The cell index is monotone in frequency along each axis,
-    // so the cells at a chunk's two end channels bound every channel between.
+// Chunk cells: one thread per (row, channel chunk) entry, laid out [chunk][row]
+// per window (rows in processing order).  The cell index is monotone in
+// frequency along each axis, so the cells at a chunk's two end channels
+// bound every channel between.
+__global__ void __launch_bounds__(256) k_cells(RunArgs a)
+{
+    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= a.ncells_total) return;
+    const int w = find_owner(a.cell_cum, a.nsrc, p);
+    const SrcDev &S = a.srcs[w];
+    const int64_t loc = p - a.cell_cum[w];
+    const int c = (int)(loc / S.nrow);
+    const int64_t q = loc - (int64_t)c * S.nrow;
+    const int64_t r = a.so.perm[a.row_off[w] + q];
+    const double *uvw = S.uvw + 3 * r;
+    const double u = uvw[0], v = uvw[1];
+    const bool fold = a.g.fold && (v < 0.0 || (v == 0.0 && u < 0.0));
     const float uf = (float)(fold ? -u : u), vf = (float)(fold ? -v : v);
     const ChanD *cd = a.chd + S.chan_off;
     const ChanF *cf = a.chf + S.chan_off;
     const int nin = S.k_hi - S.k_lo;
     const float hu = (float)(a.g.nu >> 1), hv = (float)(a.g.nv >> 1);
-    int2 *out = a.ccells + S.cell_off + q;
-    for (int c = 0; c < S.nchunk; ++c) {
-        const int e0 = c * a.cw, last = min(nin, e0 + a.cw) - 1 - e0;
-        const float fu0 = axis_floor(uf, cf[e0].su, uvw, fold, &cd[e0].su);
-        const float fu1 = axis_floor(uf, cf[e0 + last].su, uvw, fold, &cd[e0 + last].su);
-        const float fv0 = axis_floor(vf, cf[e0].sv, uvw + 1, fold, &cd[e0].sv);
-        const float fv1 = axis_floor(vf, cf[e0 + last].sv, uvw + 1, fold, &cd[e0 + last].sv);
-        // both ends off the grid on the same side of one axis: off throughout
-        const bool offu = (fu0 < -hu && fu1 < -hu) || (fu0 >= hu && fu1 >= hu);
-        const bool offv = (fv0 < -hv && fv1 < -hv) || (fv0 >= hv && fv1 >= hv);
-        const bool in = fu0 >= -hu && fu0 < hu && fu1 >= -hu && fu1 < hu && fv0 >= -hv && fv0 < hv &&
-                        fv1 >= -hv && fv1 < hv;
-        int2 cc;
-        if (offu || offv) {
-            cc = make_int2(-1, CC_NOCHANGE);
-        } else if (!in || fabsf(fu1 - fu0) > 1.0f || fabsf(fv1 - fv0) > 1.0f) {
-            cc = make_int2(-1, CC_MIXED);
-        } else {
-            uint32_t m = CC_NOCHANGE;
-            if (fu1 != fu0) {
-                const int b = axis_step(uf, cf, cd, e0, 0, last, uvw, fold, false, fu0);
-                m = (m & ~0xffu) | (uint32_t)b | (fu1 < fu0 ? 0x10000u : 0u);
-            }
-            if (fv1 != fv0) {
-                const int b = axis_step(vf, cf, cd, e0, 0, last, uvw + 1, fold, true, fv0);
-                m = (m & ~0xff00u) | ((uint32_t)b << 8) | (fv1 < fv0 ? 0x20000u : 0u);
-            }
-            cc = make_int2(((int)fv0 + (a.g.nv >> 1)) * a.g.nu + ((int)fu0 + (a.g.nu >> 1)), (int)m);
+    const int e0 = c * a.cw, last = min(nin, e0 + a.cw) - 1 - e0;
+    const float fu0 = axis_floor(uf, cf[e0].su, uvw, fold, &cd[e0].su);
+    const float fu1 = axis_floor(uf, cf[e0 + last].su, uvw, fold, &cd[e0 + last].su);
+    const float fv0 = axis_floor(vf, cf[e0].sv, uvw + 1, fold, &cd[e0].sv);
+    const float fv1 = axis_floor(vf, cf[e0 + last].sv, uvw + 1, fold, &cd[e0 + last].sv);
+    // both ends off the grid on the same side of one axis: off throughout
+    const bool offu = (fu0 < -hu && fu1 < -hu) || (fu0 >= hu && fu1 >= hu);
+    const bool offv = (fv0 < -hv && fv1 < -hv) || (fv0 >= hv && fv1 >= hv);
+    const bool in = fu0 >= -hu && fu0 < hu && fu1 >= -hu && fu1 < hu && fv0 >= -hv && fv0 < hv &&
+                    fv1 >= -hv && fv1 < hv;
+    int2 cc;
+    if (offu || offv) {
+        cc = make_int2(-1, CC_NOCHANGE);
+    } else if (!in || fabsf(fu1 - fu0) > 1.0f || fabsf(fv1 - fv0) > 1.0f) {
+        cc = make_int2(-1, CC_MIXED);
+    } else {
+        uint32_t m = CC_NOCHANGE;
+        if (fu1 != fu0) {
+            const int b = axis_step(uf, cf, cd, e0, 0, last, uvw, fold, false, fu0);
+            m = (m & ~0xffu) | (uint32_t)b | (fu1 < fu0 ? 0x10000u : 0u);
         }
-        out[(int64_t)c * S.nrow] = cc;
+        if (fv1 != fv0) {
+            const int b = axis_step(vf, cf, cd, e0, 0, last, uvw + 1, fold, true, fv0);
+            m = (m & ~0xff00u) | ((uint32_t)b << 8) | (fv1 < fv0 ? 0x20000u : 0u);
+        }
+        cc = make_int2(((int)fv0 + (a.g.nv >> 1)) * a.g.nu + ((int)fu0 + (a.g.nu >> 1)), (int)m);
     }
+    a.ccells[S.cell_off + loc] = cc;
 }
 
 cudaError_t launch_prepare(const RunArgs &a, cudaStream_t st)
@@ -323,6 +336,7 @@ cudaError_t launch_prepare(const RunArgs &a, cudaStream_t st)
     const int64_t nbuckets = (int64_t)a.nsrc * so.nstripe;
     if (rb && nbuckets) k_bucket_sort<<<(unsigned)nbuckets, 256, 0, st>>>(a);
     if (rb) k_records<<<rb, 256, 0, st>>>(a);
+    if (a.ncells_total > 0) k_cells<<<(unsigned)((a.ncells_total + 255) / 256), 256, 0, st>>>(a);
     return cudaGetLastError();
 }
 

@@ -161,7 +161,7 @@ cudaError_t device_pass(vista_stack *h, cudaStream_t st)
             int sp = span_begin(h, 0);
             e = launch_prepare(a, st);
             span_end(h, sp);
-            if (h->timing) h->tacc.launches += 6;
+            if (h->timing) h->tacc.launches += 7;
             if (e == cudaSuccess) {
                 sp = span_begin(h, 1);
                 e = launch_mixed(a, cr.key, cfg.warps_per_cta, cfg.prefetch_rows, st);
@@ -358,7 +358,7 @@ extern "C" int vista_run(vista_stack *h)
         cls_src0[ci] = sdev.size();
         cls_off0[ci] = offs.size();
         const size_t m = cr.members.size();
-        std::vector<int64_t> roff(m + 1, 0);
+        std::vector<int64_t> roff(m + 1, 0), croff(m + 1, 0);
         int64_t max_items = 0;
         for (size_t t = 0; t < m; ++t) {
             const int i = cr.members[t];
@@ -451,10 +451,13 @@ extern "C" int vista_run(vista_stack *h)
                 nvis_run += (uint64_t)(d.nrow * nread * npm);
             }
             roff[t + 1] = roff[t] + d.nrow;
+            croff[t + 1] = croff[t] + (fp64 ? 0 : d.nrow * d.nchunk);
             max_items += (int64_t)d.nchunk * ((d.nrow + cfg.rows_per_item - 1) / cfg.rows_per_item + h->nstripe);
             sdev.push_back(d);
         }
         offs.insert(offs.end(), roff.begin(), roff.end());
+        offs.insert(offs.end(), croff.begin(), croff.end());
+        cr.args.ncells_total = croff[m];
         cr.args.nsrc = (int32_t)m;
         cr.args.cw = cw;
         cr.args.nrows_total = roff[m];
@@ -492,6 +495,7 @@ extern "C" int vista_run(vista_stack *h)
         a.recs = (RowRec *)h->b_recs.p;
         a.ccells = (int2 *)h->b_cells.p;
         a.row_off = (const int64_t *)h->b_off.p + cls_off0[ci];
+        a.cell_cum = a.row_off + cr.members.size() + 1;
         a.g = g;
         a.cube = h->cube;
         a.count = h->count;

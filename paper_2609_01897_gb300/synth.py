@@ -259,6 +259,90 @@ def wideband_hi(device="cpu", n_sources=24, src_ids=None) -> Workload:
     return Workload("wideband_hi", n, n, 2048, 2, du, du, nu_line, spws)
 
 
+CII_REST = 1900.537e9   # [CII] 158 um, Hz
+
+
+def batched(device="cpu", n_sources=2000, median_rows=20000, pool_gb=96.0, src_ids=None,
+            meta_only=False, du=None, seed_pool=True) -> Workload:
+    """Batched uneven stack: per source, rows lognormal(median 20k, sigma_ln 1),
+    1-4 windows of 1.875 GHz with 128/240/480/960/3840 channels in 84-950 GHz
+    (window 0 centred on [CII] 1900.537 GHz/(1+z) when that falls in the
+    band), 2 or 4 pols, z in [0.5, 4], flags 0-10 %; cube 256 x 256 x 1024 x 4
+    centred on [CII].  The total (~5e11 visibilities) cannot be resident:
+    every window's visibilities and flags are views at random offsets into
+    two device pools (pool_gb of complex64 noise and a flag pool of the same
+    element count in 11 segments with 0, 1, ..., 10 % flags; a window starts
+    in its source's segment), so every read is a real HBM read, while each
+    source's uvw and weights are its own.  Assumed: arrays of 10-50 antennas
+    within 0.25-5 km, 30 s integrations at dec -30, lat -23 (rows = the first
+    nrow of the baseline tracks), offsets within +-10", weights U[0.5, 1.5];
+    a window's rows are capped so that it fits the pool (the far lognormal
+    tail only)."""
+    cid = CONFIG_IDS["batched"]
+    nsrc_ids = range(n_sources) if src_ids is None else src_ids
+    choices = np.array([128, 240, 480, 960, 3840])
+    band_lo, band_hi, width = 84e9, 950e9, 1.875e9
+    pool_elems = max(1 << 20, int(pool_gb * 1e9 / 8) // 16 * 16)
+    plan = []
+    for s in nsrc_ids:
+        rng = np.random.default_rng(1000 * cid + s)
+        nrow = max(1, int(round(rng.lognormal(math.log(median_rows), 1.0))))
+        n_ant = int(rng.integers(10, 51))
+        radius = float(rng.uniform(250.0, 5000.0))
+        z = float(rng.uniform(0.5, 4.0))
+        npol = int(rng.choice([2, 4]))
+        flag_seg = int(rng.integers(0, 11))
+        l0 = float(rng.uniform(-10 * ARCSEC, 10 * ARCSEC))
+        m0 = float(rng.uniform(-10 * ARCSEC, 10 * ARCSEC))
+        ha0 = float(rng.uniform(-1.0, 1.0))
+        nspw = int(rng.integers(1, 5))
+        wins = []
+        nch_max = 0
+        for k in range(nspw):
+            nchan = int(rng.choice(choices))
+            fc = CII_REST / (1.0 + z)
+            if k > 0 or not (band_lo + 0.5 * width <= fc <= band_hi - 0.5 * width):
+                fc = float(rng.uniform(band_lo + 0.5 * width, band_hi - 0.5 * width))
+            df = width / nchan
+            wins.append(Spw(fc - 0.5 * (nchan - 1) * df, df, nchan))
+            nch_max = max(nch_max, nchan)
+        nrow = min(nrow, pool_elems // (nch_max * npol))
+        enu = array_enu(n_ant, radius, rng)
+        nbl = n_ant * (n_ant - 1) // 2
+        n_int = (nrow + nbl - 1) // nbl
+        uvw_np = uvw_tracks(enu, -23.0, -30.0, n_int, 30.0, ha0)[:nrow]
+        plan.append((s, nrow, npol, z, l0, m0, flag_seg, wins, uvw_np, rng))
+    spws = []
+    if meta_only:
+        for s, nrow, npol, z, l0, m0, flag_seg, wins, uvw_np, rng in plan:
+            for w in wins:
+                spws.append(SourceSpw(torch.as_tensor(uvw_np), w.freqs(), None, None, None, l0, m0, z,
+                                      source=s))
+    else:
+        g = _gen(1000 * cid + 999983, device)
+        pool = torch.empty(pool_elems, dtype=torch.complex64, device=device)
+        if seed_pool:
+            torch.view_as_real(pool).normal_(generator=g)
+        seg = pool_elems // 11 // 16 * 16
+        fpool = torch.empty(pool_elems, dtype=torch.uint8, device=device)
+        for k in range(11):
+            lo, hi = k * seg, (k + 1) * seg if k < 10 else pool_elems
+            fpool[lo:hi] = (torch.rand(hi - lo, generator=g, device=device) < 0.01 * k).to(torch.uint8)
+        for s, nrow, npol, z, l0, m0, flag_seg, wins, uvw_np, rng in plan:
+            uvw = torch.as_tensor(uvw_np, dtype=torch.float64, device=device)
+            wts = torch.as_tensor(rng.uniform(0.5, 1.5, size=(nrow, npol)), dtype=torch.float32, device=device)
+            for w in wins:
+                n = nrow * w.nchan * npol
+                off = int(rng.integers(0, (pool_elems - n) // 16 + 1)) * 16
+                vis = pool[off:off + n].view(nrow, w.nchan, npol)
+                foff = min(flag_seg * seg + int(rng.integers(0, seg // 16)) * 16, (pool_elems - n) // 16 * 16)
+                flags = fpool[foff:foff + n].view(nrow, w.nchan, npol)
+                spws.append(SourceSpw(uvw, w.freqs(), vis, wts, flags, l0, m0, z, source=s))
+    n = 256
+    du = _cube_du(spws, n) if du is None else du
+    return Workload("batched", n, n, 1024, 4, du, du, CII_REST, spws)
+
+
 def scaled(w: Workload, frac: float) -> Workload:
     """Same cube, only the first ceil(frac * nspw) windows (bounded samples)."""
     k = max(1, int(math.ceil(frac * len(w.spws))))
