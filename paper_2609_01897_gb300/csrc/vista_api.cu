@@ -31,21 +31,8 @@ bool is_fin(double x) { return std::isfinite(x); }
 int stripe_geometry(vista_stack *h)
 {
     const vista_cube_desc &d = h->desc;
-    const double row_bytes = (double)d.nu * d.nrest * d.npol * 20.0;
-    int S = (int)std::max(1.0, std::min((double)d.nv, std::floor(40e6 / row_bytes)));
-    int ushift = 0, nuk = d.nu;
-    while ((int64_t)S * nuk > MAX_LOCAL_KEYS) {
-        if (S > 1) {
-            S = std::max(1, MAX_LOCAL_KEYS / nuk);
-            if ((int64_t)S * nuk <= MAX_LOCAL_KEYS) break;
-            S = 1;
-        } else {
-            ++ushift;
-            nuk = (d.nu + (1 << ushift) - 1) >> ushift;
-        }
-    }
-    const int nst = (d.nv + S - 1) / S;
-    if (nst >= (1 << 19)) return VISTA_E_RANGE;
+    int S = 1, nst = 1, ushift = 0, nuk = 1;
+    if (!stripe_layout(d.nu, d.nv, d.nrest, d.npol, &S, &nst, &ushift, &nuk)) return VISTA_E_RANGE;
     h->stripe_rows = S;
     h->nstripe = nst;
     h->ushift = ushift;
@@ -175,15 +162,18 @@ extern "C" int vista_open_stack(const vista_cube_desc *d, vista_stack **out)
     }
     if (stripe_geometry(h) != VISTA_OK) {
         delete h;
-        return fail(nullptr, VISTA_E_RANGE, "cube too tall for the row ordering (nv / stripe >= 2^19)");
+        return fail(nullptr, VISTA_E_RANGE, "cube too tall for the row ordering");
     }
     cudaError_t e = cudaGetDevice(&h->device);
-    const size_t esz = d->precision == VISTA_PREC_FP64 ? 32 : 16;
+    const bool fp64c = d->precision == VISTA_PREC_FP64;
+    const size_t esz = fp64c ? 32 : 16;   // double[4] (FP64) or float4 (mixed, plus an FP64 master cube)
     if (e == cudaSuccess) e = cudaMalloc(&h->cube, (size_t)n * esz);
     if (e == cudaSuccess) e = cudaMalloc((void **)&h->count, (size_t)n * sizeof(uint32_t));
     if (e == cudaSuccess) e = cudaMalloc((void **)&h->stats, sizeof(DevStats));
     if (e == cudaSuccess) e = cudaMalloc((void **)&h->err, sizeof(int32_t));
     if (e == cudaSuccess) e = cudaMemsetAsync(h->cube, 0, (size_t)n * esz, h->stream);
+    if (e == cudaSuccess && !fp64c) e = cudaMalloc((void **)&h->cube_master, (size_t)n * 32);
+    if (e == cudaSuccess && !fp64c) e = cudaMemsetAsync(h->cube_master, 0, (size_t)n * 32, h->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(h->count, 0, (size_t)n * sizeof(uint32_t), h->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(h->stats, 0, sizeof(DevStats), h->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(h->err, 0, sizeof(int32_t), h->stream);
@@ -285,7 +275,8 @@ int read_common(vista_stack *h, void *sum_wv, void *sum_w, void *sum_wvv, uint32
     const int64_t n = h->nentries;
     const size_t fe = out_f64 ? 8 : 4;
     if (dst_dev) {
-        e = launch_unpack(h->cube, h->count, fp64, n, sum_wv, sum_w, sum_wvv, count, out_f64, h->stream);
+        e = launch_unpack(h->cube, h->cube_master, h->count, fp64, n, sum_wv, sum_w, sum_wvv, count, out_f64,
+                          h->stream);
         if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
         if (e != cudaSuccess) return cuda_fail(h, e, "cube unpack");
         return VISTA_OK;
@@ -300,7 +291,7 @@ int read_common(vista_stack *h, void *sum_wv, void *sum_w, void *sum_wvv, uint32
     char *d_w = sum_w ? p + b_wv : nullptr;
     char *d_vv = sum_wvv ? p + b_wv + b_w : nullptr;
     uint32_t *d_c = count ? (uint32_t *)(p + b_wv + b_w + b_vv) : nullptr;
-    e = launch_unpack(h->cube, h->count, fp64, n, d_wv, d_w, d_vv, d_c, out_f64, h->stream);
+    e = launch_unpack(h->cube, h->cube_master, h->count, fp64, n, d_wv, d_w, d_vv, d_c, out_f64, h->stream);
     if (e == cudaSuccess && sum_wv) e = cudaMemcpyAsync(sum_wv, d_wv, b_wv, cudaMemcpyDeviceToHost, h->stream);
     if (e == cudaSuccess && sum_w) e = cudaMemcpyAsync(sum_w, d_w, b_w, cudaMemcpyDeviceToHost, h->stream);
     if (e == cudaSuccess && sum_wvv) e = cudaMemcpyAsync(sum_wvv, d_vv, b_vv, cudaMemcpyDeviceToHost, h->stream);
@@ -331,6 +322,8 @@ extern "C" int vista_zero_cube(vista_stack *h)
     CHECK_HANDLE(h);
     const size_t esz = h->desc.precision == VISTA_PREC_FP64 ? 32 : 16;
     cudaError_t e = cudaMemsetAsync(h->cube, 0, (size_t)h->nentries * esz, h->stream);
+    if (e == cudaSuccess && h->cube_master)
+        e = cudaMemsetAsync(h->cube_master, 0, (size_t)h->nentries * 32, h->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(h->count, 0, (size_t)h->nentries * 4, h->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(h->stats, 0, sizeof(DevStats), h->stream);
     if (e != cudaSuccess) return cuda_fail(h, e, "cube zeroing");
@@ -479,6 +472,7 @@ extern "C" int vista_close(vista_stack *h)
     drop_graph(h);
     if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
     cudaFree(h->cube);
+    cudaFree(h->cube_master);
     cudaFree(h->count);
     cudaFree(h->stats);
     cudaFree(h->err);

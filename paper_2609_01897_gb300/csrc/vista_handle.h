@@ -74,6 +74,7 @@ struct vista_stack {
     double f0 = 0.0, df = 0.0;
     std::vector<vista::SrcHost> pending, last;
     void *cube = nullptr;
+    double *cube_master = nullptr;   // mixed: FP64 sums moved out of the float4 cube at checkpoints
     uint32_t *count = nullptr;
     int64_t nentries = 0;
     vista::DevStats *stats = nullptr;

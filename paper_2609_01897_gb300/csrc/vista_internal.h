@@ -10,6 +10,38 @@ namespace vista {
 
 constexpr double C_LIGHT = 299792458.0;   // m/s
 constexpr int MAX_LOCAL_KEYS = 4096;      // cell keys inside one stripe (shared-memory histogram)
+constexpr int MAX_STRIPES = 4096;         // stripes of the cube (shared-memory running counts)
+constexpr int SEG_ROWS = 2048;            // rows per segment of the row-order slot assignment
+
+// Row-ordering stripes of a cube: S iv rows per stripe (sized so that a
+// stripe's cube entries, ~20 B each, stay near 40 MB and resident in L2),
+// at most MAX_STRIPES stripes, and a local cell key (iv % S) * nuk + (iu >>
+// ushift) below MAX_LOCAL_KEYS.  Returns false if no such layout exists.
+inline bool stripe_layout(int nu, int nv, int nrest, int npol, int *S_out, int *nst_out, int *ushift_out,
+                          int *nuk_out)
+{
+    const double row_bytes = (double)nu * nrest * npol * 20.0;
+    const int minS = (nv + MAX_STRIPES - 1) / MAX_STRIPES;
+    if (minS > MAX_LOCAL_KEYS) return false;
+    double s0 = 40e6 / row_bytes;
+    s0 = s0 < 1.0 ? 1.0 : (s0 > nv ? nv : s0);
+    int S = (int)s0 < minS ? minS : (int)s0;
+    int ushift = 0, nuk = nu;
+    while ((int64_t)S * nuk > MAX_LOCAL_KEYS) {
+        if (S > minS) {
+            const int fit = MAX_LOCAL_KEYS / nuk;
+            S = fit < minS ? minS : (fit < S - 1 ? fit : S - 1);
+        } else {
+            ++ushift;
+            nuk = (nu + (1 << ushift) - 1) >> ushift;
+        }
+    }
+    *S_out = S;
+    *nst_out = (nv + S - 1) / S;
+    *ushift_out = ushift;
+    *nuk_out = nuk;
+    return true;
+}
 
 // Channels per 4-byte word of flags (npol bytes per channel): the channel
 // ranges the mixed path reads start and end on multiples of this.
@@ -141,11 +173,17 @@ struct LaunchCfg {
 //   tmp      [rows]             (local key << 32) | row, bucket-grouped
 //   perm     [rows]             row of each processing position
 //   ioff     [nbuckets + 1]     first work item of each bucket (stripe-major)
+//   segcnt   [nseg][nstripe]    rows of each (segment of SEG_ROWS rows, stripe), then
+//                               the segment's first slot in each bucket
+//   seg_off  [nwin + 1]         cumulative segments per window
 //   items    [max_items]        work list, stripe-major
 //   ctr      [2]                item count, queue head
 struct SortArgs {
     uint32_t *hist, *qstart, *slot, *key, *perm;
     int64_t *ioff;
+    uint32_t *segcnt;
+    const int64_t *seg_off;
+    int64_t nseg_total;
     unsigned long long *tmp;
     Item *items;
     uint32_t *ctr;
@@ -171,7 +209,10 @@ struct RunArgs {
     int64_t ncells_total;
     int64_t nrows_total;
     CubeGeom g;
-    void *cube;                 // float4 (mixed) or double[4] (FP64) per entry
+    void *cube;                 // per entry: FP64 double[4], or float4 (mixed)
+    double *cube_master;        // mixed with comp = 1: FP64 double[4] per entry, the sums moved
+                                // out of the float4 entries at checkpoints (value = master + float4)
+    int32_t comp;
     uint32_t *count;
     DevStats *stats;
     int32_t *err;
@@ -185,7 +226,7 @@ cudaError_t launch_prepare(const RunArgs &a, cudaStream_t st);
 // (chans_per_lane << 8) | npol, shared by every window of the class.
 cudaError_t launch_mixed(const RunArgs &a, int key, int warps_per_cta, int prefetch, cudaStream_t st);
 cudaError_t launch_fp64(const RunArgs &a, cudaStream_t st);
-cudaError_t launch_unpack(const void *cube, const uint32_t *count, int fp64, int64_t n,
+cudaError_t launch_unpack(const void *cube, const double *master, const uint32_t *count, int fp64, int64_t n,
                           void *sum_wv, void *sum_w, void *sum_wvv, uint32_t *cnt_out,
                           int out_f64, cudaStream_t st);
 cudaError_t launch_debug(const RunArgs &a, int ns, int src, int fp64, double *ph, int32_t *cells,

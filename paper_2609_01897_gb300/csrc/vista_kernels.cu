@@ -182,8 +182,8 @@ __global__ void __launch_bounds__(128) stack_fp64(RunArgs a, int only_src, doubl
 
 // ------------------------------------------------------------------ unpack
 
-__global__ void unpack_kernel(const void *cube, const uint32_t *count, int fp64, int64_t n, void *sum_wv,
-                              void *sum_w, void *sum_wvv, uint32_t *cnt_out, int out_f64)
+__global__ void unpack_kernel(const void *cube, const double *master, const uint32_t *count, int fp64, int64_t n,
+                              void *sum_wv, void *sum_w, void *sum_wvv, uint32_t *cnt_out, int out_f64)
 {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         double e[4];
@@ -194,11 +194,19 @@ __global__ void unpack_kernel(const void *cube, const uint32_t *count, int fp64,
             e[2] = c[2];
             e[3] = c[3];
         } else {
+            // the float4 sums since the last checkpoint plus the FP64 master sums
             const float4 c = reinterpret_cast<const float4 *>(cube)[i];
             e[0] = c.x;
             e[1] = c.y;
             e[2] = c.z;
             e[3] = c.w;
+            if (master) {
+                const double *m = master + 4 * i;
+                e[0] += m[0];
+                e[1] += m[1];
+                e[2] += m[2];
+                e[3] += m[3];
+            }
         }
         if (out_f64) {
             if (sum_wv) {
@@ -229,13 +237,14 @@ cudaError_t launch_fp64(const RunArgs &a, cudaStream_t st)
     return cudaGetLastError();
 }
 
-cudaError_t launch_unpack(const void *cube, const uint32_t *count, int fp64, int64_t n, void *sum_wv, void *sum_w,
-                          void *sum_wvv, uint32_t *cnt_out, int out_f64, cudaStream_t st)
+cudaError_t launch_unpack(const void *cube, const double *master, const uint32_t *count, int fp64, int64_t n,
+                          void *sum_wv, void *sum_w, void *sum_wvv, uint32_t *cnt_out, int out_f64, cudaStream_t st)
 {
     if (n == 0) return cudaSuccess;
     int64_t blocks = (n + 255) / 256;
     if (blocks > 152 * 16) blocks = 152 * 16;
-    unpack_kernel<<<(unsigned)blocks, 256, 0, st>>>(cube, count, fp64, n, sum_wv, sum_w, sum_wvv, cnt_out, out_f64);
+    unpack_kernel<<<(unsigned)blocks, 256, 0, st>>>(cube, master, count, fp64, n, sum_wv, sum_w, sum_wvv, cnt_out,
+                                                    out_f64);
     return cudaGetLastError();
 }
 

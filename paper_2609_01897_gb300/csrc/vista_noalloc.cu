@@ -150,20 +150,9 @@ extern "C" int vista_stack_noalloc(const vista_cube_desc *c, const vista_source_
     const bool linear = linear_axis(s->freqs, n, &step);
 
     // row-ordering stripes (as for a handle of the same cube)
-    const double row_bytes = (double)c->nu * c->nrest * c->npol * 20.0;
-    int S = (int)std::max(1.0, std::min((double)c->nv, std::floor(40e6 / row_bytes)));
-    int ushift = 0, nuk = c->nu;
-    while ((int64_t)S * nuk > MAX_LOCAL_KEYS) {
-        if (S > 1) {
-            S = std::max(1, MAX_LOCAL_KEYS / nuk);
-            if ((int64_t)S * nuk <= MAX_LOCAL_KEYS) break;
-            S = 1;
-        } else {
-            ++ushift;
-            nuk = (c->nu + (1 << ushift) - 1) >> ushift;
-        }
-    }
-    const int nstripe = (c->nv + S - 1) / S;
+    int S = 1, nstripe = 1, ushift = 0, nuk = 1;
+    if (!stripe_layout(c->nu, c->nv, c->nrest, c->npol, &S, &nstripe, &ushift, &nuk))
+        return fail(nullptr, VISTA_E_RANGE, "cube too tall for the row ordering");
     const int R = 64, cw = 32;
     const int nchunk = (nin + cw - 1) / cw;
     const int64_t nrow = s->nrow;
@@ -174,7 +163,7 @@ extern "C" int vista_stack_noalloc(const vista_cube_desc *c, const vista_source_
     const size_t o_src = o;
     o += al256(sizeof(SrcDev));
     const size_t o_off = o;
-    o += al256(4 * sizeof(int64_t));
+    o += al256(6 * sizeof(int64_t));
     const size_t o_chf = o;
     o += al256(sizeof(ChanF) * (size_t)nin);
     const size_t o_chd = o;
@@ -191,6 +180,8 @@ extern "C" int vista_stack_noalloc(const vista_cube_desc *c, const vista_source_
     o += al256(4 * (size_t)nstripe);
     const size_t o_ioff = o;
     o += al256(8 * ((size_t)nstripe + 1));
+    const size_t o_segcnt = o;
+    o += al256(4 * (size_t)((nrow + SEG_ROWS - 1) / SEG_ROWS) * (size_t)nstripe);
     const size_t o_slot = o;
     o += al256(4 * (size_t)nrow);
     const size_t o_key = o;
@@ -249,7 +240,9 @@ extern "C" int vista_stack_noalloc(const vista_cube_desc *c, const vista_source_
     d.key_sv = (float)(s->freqs[key_ch] * gv);
     d.rec_off = 0;
     d.cell_off = 0;
-    const int64_t roff[4] = {0, nrow, 0, nrow * nchunk};   // rows, then (row, chunk) entries
+    const int64_t nseg = (nrow + SEG_ROWS - 1) / SEG_ROWS;
+    // rows, (row, chunk) entries, row segments
+    const int64_t roff[6] = {0, nrow, 0, nrow * nchunk, 0, nseg};
 
     // tables into scratch; counters and the error word start at zero
     e = cudaMemcpyAsync(b + o_src, &d, sizeof d, cudaMemcpyHostToDevice, st);
@@ -273,16 +266,21 @@ extern "C" int vista_stack_noalloc(const vista_cube_desc *c, const vista_source_
     a.ccells = (int2 *)(b + o_cells);
     a.row_off = (const int64_t *)(b + o_off);
     a.cell_cum = a.row_off + 2;
+    a.so.seg_off = a.row_off + 4;
+    a.so.nseg_total = nseg;
     a.ncells_total = nrow * nchunk;
     a.nrows_total = nrow;
     a.g = CubeGeom{c->nu, c->nv, c->nrest, c->npol, gu, gv, c->hermitian_fold, 0};
     a.cube = cube4;
+    a.cube_master = nullptr;
+    a.comp = 0;   // the caller's cube: plain float4 sums
     a.count = count;
     a.stats = (DevStats *)(b + o_stats);
     a.err = (int32_t *)(b + o_err);
     a.so.hist = (uint32_t *)(b + o_hist);
     a.so.qstart = (uint32_t *)(b + o_qs);
     a.so.ioff = (int64_t *)(b + o_ioff);
+    a.so.segcnt = (uint32_t *)(b + o_segcnt);
     a.so.slot = (uint32_t *)(b + o_slot);
     a.so.key = (uint32_t *)(b + o_key);
     a.so.perm = (uint32_t *)(b + o_perm);

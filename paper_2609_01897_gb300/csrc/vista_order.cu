@@ -6,14 +6,17 @@
 // cube, sized to stay resident in L2) across all windows.
 //
 //   k_keys         cell of every row at the window's highest in-cube
-//                  frequency -> (stripe, local cell key); per-bucket arrival
-//                  slots with warp-aggregated atomics
+//                  frequency -> (stripe, local cell key); stripe counts per
+//                  segment of rows
+//   k_segscan      segment offsets inside each (window, stripe) bucket
+//   k_slots        each row's slot in its bucket, in row order
 //   k_scan         one block: per-window bucket offsets, per-bucket work-list
 //                  offsets in stripe-major order (item = rows of one bucket x
 //                  one chunk)
 //   k_items        the work list, one thread per item
 //   k_scatter      rows grouped by bucket
-//   k_bucket_sort  one block per bucket: counting sort by local cell key
+//   k_bucket_sort  one block per bucket: stable counting sort by local cell
+//                  key (the rows of one key stay in row order)
 //   k_records      per row, in processing order: the FP64 delay of Eq. 2 as
 //                  a float-float pair and the (fold-signed) weights
 //   k_cells        per (row, channel chunk): the chunk's uv cells
@@ -21,16 +24,49 @@
 
 namespace vista {
 
+// Row-order slots in (window, stripe) buckets, three passes over segments of
+// SEG_ROWS rows: keys and per-segment stripe counts, an exclusive scan of the
+// counts over each window's segments, then each segment's slots in row order
+// (ranks within a warp from a match, warps in turn against running counts in
+// shared memory).  Rows that share a bucket thus keep their row order.
+constexpr uint32_t NO_BUCKET = 0xffffffffu;
+
+struct SegRange {
+    int w;
+    int64_t g0, r0, r1;   // first global row of the window, rows [r0, r1) of the segment
+};
+__device__ __forceinline__ SegRange seg_range(const RunArgs &a, int64_t seg)
+{
+    SegRange sr;
+    sr.w = find_owner(a.so.seg_off, a.nsrc, seg);
+    sr.g0 = a.row_off[sr.w];
+    sr.r0 = (seg - a.so.seg_off[sr.w]) * SEG_ROWS;
+    const int64_t n = a.srcs[sr.w].nrow;
+    sr.r1 = sr.r0 + SEG_ROWS < n ? sr.r0 + SEG_ROWS : n;
+    return sr;
+}
+
+// Pass 1: the cell of every row at the window's highest in-cube frequency ->
+// (stripe, local cell key), and the stripe counts of the segment.
 __global__ void __launch_bounds__(256) k_keys(RunArgs a)
 {
-    const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (g >= a.nrows_total) return;
+    __shared__ uint32_t cnt[MAX_STRIPES];
     const SortArgs &so = a.so;
-    const int w = find_owner(a.row_off, a.nsrc, g);
-    const SrcDev &S = a.srcs[w];
-    const int64_t r = g - a.row_off[w];
-    uint32_t stripe = 0, L = 0, slot;
-    if (so.sorted) {
+    const int64_t seg = blockIdx.x;
+    const SegRange sr = seg_range(a, seg);
+    const SrcDev &S = a.srcs[sr.w];
+    if (!so.sorted) {
+        for (int64_t r = sr.r0 + threadIdx.x; r < sr.r1; r += blockDim.x) {
+            so.slot[sr.g0 + r] = (uint32_t)r;
+            so.key[sr.g0 + r] = 0u;
+        }
+        if (threadIdx.x == 0 && sr.r0 == 0) so.hist[sr.w] = (uint32_t)S.nrow;
+        return;
+    }
+    for (int k = threadIdx.x; k < so.nstripe; k += blockDim.x) cnt[k] = 0u;
+    __syncthreads();
+    for (int64_t r = sr.r0 + threadIdx.x; r < sr.r1; r += blockDim.x) {
+        uint32_t stripe = 0, L = 0;
         if (S.k_hi > S.k_lo) {
             double u = S.uvw[3 * r], v = S.uvw[3 * r + 1];
             if (a.g.fold && (v < 0.0 || (v == 0.0 && u < 0.0))) {
@@ -45,22 +81,62 @@ __global__ void __launch_bounds__(256) k_keys(RunArgs a)
             stripe = (uint32_t)(iv / so.stripe_rows);
             L = (uint32_t)((iv % so.stripe_rows) * so.nuk + (iu >> so.ushift));
         }
-        const uint32_t b = (uint32_t)w * so.nstripe + stripe;
-        const unsigned act = __activemask();
-        const unsigned peers = __match_any_sync(act, b);
-        const int lane = threadIdx.x & 31;
+        so.key[sr.g0 + r] = (stripe << 13) | L;
+        atomicAdd(&cnt[stripe], 1u);
+    }
+    __syncthreads();
+    for (int k = threadIdx.x; k < so.nstripe; k += blockDim.x) so.segcnt[seg * so.nstripe + k] = cnt[k];
+}
+
+// Pass 2: one thread per (window, stripe): the segments' first slots and the
+// bucket's row count.
+__global__ void __launch_bounds__(256) k_segscan(RunArgs a)
+{
+    const SortArgs &so = a.so;
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (!so.sorted || t >= (int64_t)a.nsrc * so.nstripe) return;
+    const int w = (int)(t / so.nstripe), k = (int)(t % so.nstripe);
+    uint32_t run = 0;
+    for (int64_t seg = so.seg_off[w]; seg < so.seg_off[w + 1]; ++seg) {
+        uint32_t *c = so.segcnt + seg * so.nstripe + k;
+        const uint32_t n = *c;
+        *c = run;
+        run += n;
+    }
+    so.hist[t] = run;
+}
+
+// Pass 3: each segment's slots in row order.
+__global__ void __launch_bounds__(256) k_slots(RunArgs a)
+{
+    __shared__ uint32_t run[MAX_STRIPES];
+    const SortArgs &so = a.so;
+    if (!so.sorted) return;
+    const int64_t seg = blockIdx.x;
+    const SegRange sr = seg_range(a, seg);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    for (int k = threadIdx.x; k < so.nstripe; k += blockDim.x) run[k] = so.segcnt[seg * so.nstripe + k];
+    __syncthreads();
+    for (int64_t c = sr.r0; c < sr.r1; c += blockDim.x) {
+        const int64_t r = c + threadIdx.x;
+        const uint32_t stripe = r < sr.r1 ? so.key[sr.g0 + r] >> 13 : NO_BUCKET;
+        const unsigned peers = __match_any_sync(0xffffffffu, stripe);
         const int leader = __ffs(peers) - 1;
         const uint32_t rank = __popc(peers & ((1u << lane) - 1u));
-        uint32_t base = 0;
-        if (lane == leader) base = atomicAdd(&so.hist[b], (uint32_t)__popc(peers));
-        base = __shfl_sync(peers, base, leader);
-        slot = base + rank;
-    } else {
-        slot = (uint32_t)r;
-        if (r == 0) so.hist[w] = (uint32_t)S.nrow;
+        uint32_t slot = 0;
+        for (int wi = 0; wi < nwarps; ++wi) {
+            if (warp == wi) {
+                uint32_t base = 0;
+                if (lane == leader && stripe != NO_BUCKET) {
+                    base = run[stripe];
+                    run[stripe] = base + (uint32_t)__popc(peers);
+                }
+                slot = __shfl_sync(peers, base, leader) + rank;
+            }
+            __syncthreads();
+        }
+        if (r < sr.r1) so.slot[sr.g0 + r] = slot;
     }
-    so.slot[g] = slot;
-    so.key[g] = (stripe << 13) | L;
 }
 
 // One block of 1024 threads.
@@ -170,7 +246,6 @@ __global__ void __launch_bounds__(256) k_bucket_sort(RunArgs a)
         return;
     }
     __shared__ uint32_t sh[MAX_LOCAL_KEYS];
-    __shared__ uint32_t start[MAX_LOCAL_KEYS];
     __shared__ uint32_t part[256];
     const int nk = so.stripe_rows * so.nuk;
     for (int i = threadIdx.x; i < nk; i += blockDim.x) sh[i] = 0;
@@ -194,39 +269,35 @@ __global__ void __launch_bounds__(256) k_bucket_sort(RunArgs a)
     for (int k = k0; k < k1; ++k) {
         const uint32_t c = sh[k];
         sh[k] = run;
-        start[k] = run;
         run += c;
     }
     __syncthreads();
-    for (uint32_t i = threadIdx.x; i < n; i += blockDim.x) {
-        const unsigned long long t = so.tmp[base + i];
-        const uint32_t pos = atomicAdd(&sh[(uint32_t)(t >> 32)], 1u);
-        so.perm[base + pos] = (uint32_t)t;
-    }
-    __syncthreads();
-    // Rows that share a cell key arrive in arbitrary (atomic) order; order
-    // each such group by row index.  Rows of one baseline are then
-    // consecutive in time, so at the other channels of the window the cell
-    // changes at most once inside the group instead of alternating.
-    // A warp per group: rank of each row = rows of the group with a smaller
-    // index (indices are distinct), written to tmp, then copied back.
+    // Stable scatter: the bucket's rows arrive in row order (k_keys), and
+    // keep it within each local key, so that rows of one baseline stay
+    // consecutive in time and, at the window's other channels, a group's
+    // cell changes at most once instead of alternating.
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
-    for (int k = warp; k < nk; k += nwarps) {
-        const uint32_t s0 = start[k], cnt = sh[k] - s0;
-        if (cnt < 2) continue;
-        const uint32_t *g = so.perm + base + s0;
-        for (uint32_t i = lane; i < cnt; i += 32) {
-            const uint32_t ri = g[i];
-            uint32_t rank = 0;
-            for (uint32_t j = 0; j < cnt; ++j) rank += g[j] < ri;
-            so.tmp[base + s0 + rank] = ri;
+    for (uint32_t c0 = 0; c0 < n; c0 += blockDim.x) {
+        const uint32_t i = c0 + threadIdx.x;
+        const bool valid = i < n;
+        const unsigned long long t = valid ? so.tmp[base + i] : 0ull;
+        const uint32_t L = valid ? (uint32_t)(t >> 32) : NO_BUCKET;
+        const unsigned peers = __match_any_sync(0xffffffffu, L);
+        const int leader = __ffs(peers) - 1;
+        const uint32_t rank = __popc(peers & ((1u << lane) - 1u));
+        uint32_t pos = 0;
+        for (int wi = 0; wi < nwarps; ++wi) {
+            if (warp == wi) {
+                uint32_t b0 = 0;
+                if (lane == leader && valid) {
+                    b0 = sh[L];
+                    sh[L] = b0 + (uint32_t)__popc(peers);
+                }
+                pos = __shfl_sync(peers, b0, leader) + rank;
+            }
+            __syncthreads();
         }
-    }
-    __syncthreads();
-    for (int k = warp; k < nk; k += nwarps) {
-        const uint32_t s0 = start[k], cnt = sh[k] - s0;
-        if (cnt < 2) continue;
-        for (uint32_t i = lane; i < cnt; i += 32) so.perm[base + s0 + i] = (uint32_t)so.tmp[base + s0 + i];
+        if (valid) so.perm[base + pos] = (uint32_t)t;
     }
 }
 
@@ -329,7 +400,12 @@ cudaError_t launch_prepare(const RunArgs &a, cudaStream_t st)
     cudaError_t e = cudaMemsetAsync(so.hist, 0, sizeof(uint32_t) * (size_t)a.nsrc * so.nstripe, st);
     if (e != cudaSuccess) return e;
     const unsigned rb = (unsigned)((a.nrows_total + 255) / 256);
-    if (rb) k_keys<<<rb, 256, 0, st>>>(a);
+    if (so.nseg_total > 0) {
+        k_keys<<<(unsigned)so.nseg_total, 256, 0, st>>>(a);
+        const int64_t nb = (int64_t)a.nsrc * so.nstripe;
+        k_segscan<<<(unsigned)((nb + 255) / 256), 256, 0, st>>>(a);
+        k_slots<<<(unsigned)so.nseg_total, 256, 0, st>>>(a);
+    }
     k_scan<<<1, 1024, 0, st>>>(a);
     if (so.max_items > 0) k_items<<<(unsigned)((so.max_items + 255) / 256), 256, 0, st>>>(a);
     if (rb) k_scatter<<<rb, 256, 0, st>>>(a);

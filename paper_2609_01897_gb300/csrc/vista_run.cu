@@ -108,10 +108,10 @@ inline size_t al256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 // Layout of the shared ordering buffer for one class.
 struct SortLayout {
-    size_t hist, qstart, ioff, slot, key, perm, tmp, items, ctr, total;
+    size_t hist, qstart, ioff, segcnt, slot, key, perm, tmp, items, ctr, total;
 };
 
-SortLayout sort_layout(int64_t rows, int64_t nbuckets, int64_t max_items)
+SortLayout sort_layout(int64_t rows, int64_t nbuckets, int64_t max_items, int64_t nseg, int nstripe)
 {
     SortLayout L{};
     size_t o = 0;
@@ -121,6 +121,8 @@ SortLayout sort_layout(int64_t rows, int64_t nbuckets, int64_t max_items)
     o += al256(4 * (size_t)nbuckets);
     L.ioff = o;
     o += al256(8 * ((size_t)nbuckets + 1));
+    L.segcnt = o;
+    o += al256(4 * (size_t)nseg * (size_t)nstripe);
     L.slot = o;
     o += al256(4 * (size_t)rows);
     L.key = o;
@@ -161,7 +163,7 @@ cudaError_t device_pass(vista_stack *h, cudaStream_t st)
             int sp = span_begin(h, 0);
             e = launch_prepare(a, st);
             span_end(h, sp);
-            if (h->timing) h->tacc.launches += 7;
+            if (h->timing) h->tacc.launches += 9;
             if (e == cudaSuccess) {
                 sp = span_begin(h, 1);
                 e = launch_mixed(a, cr.key, cfg.warps_per_cta, cfg.prefetch_rows, st);
@@ -358,7 +360,7 @@ extern "C" int vista_run(vista_stack *h)
         cls_src0[ci] = sdev.size();
         cls_off0[ci] = offs.size();
         const size_t m = cr.members.size();
-        std::vector<int64_t> roff(m + 1, 0), croff(m + 1, 0);
+        std::vector<int64_t> roff(m + 1, 0), croff(m + 1, 0), soff(m + 1, 0);
         int64_t max_items = 0;
         for (size_t t = 0; t < m; ++t) {
             const int i = cr.members[t];
@@ -452,17 +454,20 @@ extern "C" int vista_run(vista_stack *h)
             }
             roff[t + 1] = roff[t] + d.nrow;
             croff[t + 1] = croff[t] + (fp64 ? 0 : d.nrow * d.nchunk);
+            soff[t + 1] = soff[t] + (fp64 ? 0 : (d.nrow + SEG_ROWS - 1) / SEG_ROWS);
             max_items += (int64_t)d.nchunk * ((d.nrow + cfg.rows_per_item - 1) / cfg.rows_per_item + h->nstripe);
             sdev.push_back(d);
         }
         offs.insert(offs.end(), roff.begin(), roff.end());
         offs.insert(offs.end(), croff.begin(), croff.end());
+        offs.insert(offs.end(), soff.begin(), soff.end());
         cr.args.ncells_total = croff[m];
+        cr.args.so.nseg_total = soff[m];
         cr.args.nsrc = (int32_t)m;
         cr.args.cw = cw;
         cr.args.nrows_total = roff[m];
         const int nst = cfg.sort_rows ? h->nstripe : 1;
-        layouts[ci] = sort_layout(roff[m], (int64_t)m * nst, max_items);
+        layouts[ci] = sort_layout(roff[m], (int64_t)m * nst, max_items, soff[m], nst);
         cr.args.so.max_items = max_items;
         sort_bytes = std::max(sort_bytes, layouts[ci].total);
     }
@@ -496,8 +501,11 @@ extern "C" int vista_run(vista_stack *h)
         a.ccells = (int2 *)h->b_cells.p;
         a.row_off = (const int64_t *)h->b_off.p + cls_off0[ci];
         a.cell_cum = a.row_off + cr.members.size() + 1;
+        a.so.seg_off = a.cell_cum + cr.members.size() + 1;
         a.g = g;
         a.cube = h->cube;
+        a.cube_master = h->cube_master;
+        a.comp = h->cube_master ? 1 : 0;
         a.count = h->count;
         a.stats = h->stats;
         a.err = h->err;
@@ -508,6 +516,7 @@ extern "C" int vista_run(vista_stack *h)
             so.hist = (uint32_t *)(b + L.hist);
             so.qstart = (uint32_t *)(b + L.qstart);
             so.ioff = (int64_t *)(b + L.ioff);
+            so.segcnt = (uint32_t *)(b + L.segcnt);
             so.slot = (uint32_t *)(b + L.slot);
             so.key = (uint32_t *)(b + L.key);
             so.perm = (uint32_t *)(b + L.perm);

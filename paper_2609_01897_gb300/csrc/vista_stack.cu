@@ -30,6 +30,7 @@ namespace vista {
 constexpr int RB_MAX = 256;         // largest item (rows) the shared-memory buffers hold
 constexpr int KMAX_THREADS = 256;   // blocks of at most 8 warps
 constexpr int STAGE_CAP = 64;       // staged runs per warp (circular; a power of two)
+constexpr uint32_t CKPT_EVERY = 32;   // runs of a lane between FP64 checkpoints (a power of two)
 constexpr int NO_RUN = INT_MIN;     // lane holds no run
 
 // What a window without flags reads as its flags (every row: pitch 0).
@@ -115,11 +116,27 @@ __global__ void __launch_bounds__(KMAX_THREADS) stack_mixed(RunArgs a)
     const uint32_t G = gridDim.x * (blockDim.x >> 5);
     const uint32_t gw = blockIdx.x * (blockDim.x >> 5) + wid;
     const int npol_c = a.g.npol, nrest = a.g.nrest, gnu = a.g.nu, gnv = a.g.nv;
+    const bool comp = a.comp != 0;
     const unsigned lt_mask = (1u << lane) - 1u;
     float4 *cube4 = reinterpret_cast<float4 *>(a.cube);
     // visibilities read, stacked (unflagged, on the grid) and dropped off the
     // grid; flagged = read - stacked - dropped
     uint32_t n_read = 0, n_ok = 0, n_duv = 0, n_red = 0;
+    uint32_t n_runs = lane * 37u;   // drained runs of this lane (offset: lanes checkpoint at different times)
+    // the lane's pending checkpoint: FP32 sums taken out of the cube, to be
+    // added to the master entry ck_dst
+    float4 ck_took = make_float4(0.f, 0.f, 0.f, 0.f);
+    double *ck_dst = nullptr;
+    auto flush_ckpt = [&]() {
+        if (ck_dst) {
+            atomicAdd(ck_dst, (double)ck_took.x);
+            atomicAdd(ck_dst + 1, (double)ck_took.y);
+            atomicAdd(ck_dst + 2, (double)ck_took.z);
+            atomicAdd(ck_dst + 3, (double)ck_took.w);
+            n_red += 4;
+            ck_dst = nullptr;
+        }
+    };
     // warp sums of the counters, one atomic per counter per warp (at the
     // end, or early if a lane's count nears 2^32)
     auto flush_counters = [&]() {
@@ -272,7 +289,14 @@ __global__ void __launch_bounds__(KMAX_THREADS) stack_mixed(RunArgs a)
         }
         uint32_t head = 0, count = 0;   // circular staging area
 
-        // The warp writes min(count, 32) staged runs to the cube, one per lane.
+        // The warp writes min(count, 32) staged runs to the cube, one per lane:
+        // a float4 reduction per (cell, rest bin, pol) and the counts.  With
+        // checkpoints (comp), every CKPT_EVERY-th run of a lane also moves the
+        // FP32 sums of one entry it touched into the FP64 master cube (16-byte
+        // atomic exchange with zero; the FP64 reductions of the value taken
+        // wait for the lane's next checkpoint, so no drain waits on a returned
+        // value).  An entry's FP32 sum thus holds only the runs since its last
+        // checkpoint, about CKPT_EVERY x (entries per run).
         auto drain = [&]() {
             __syncwarp();
             if ((uint32_t)lane < count) {
@@ -287,7 +311,10 @@ __global__ void __launch_bounds__(KMAX_THREADS) stack_mixed(RunArgs a)
                     const ChanF &ct = ctab[st.kk];
                     const int nb = ct.nb;
                     const size_t base = ((size_t)st.cell * nrest + ct.j0) * npol_c;
-                    auto emit = [&](size_t e2, float ww) {
+                    const bool ckpt = comp && ((++n_runs & (CKPT_EVERY - 1)) == 0);
+                    for (int b = 0; b < nb; ++b) {
+                        const float ww = b == 0 ? ct.w0 : b == 1 ? ct.w1 : (float)a.chd[chf0 + st.kk].w[b];
+                        const size_t e2 = base + (size_t)b * npol_c;
 #pragma unroll
                         for (int p = 0; p < P; ++p) {
                             if (plane[p] < 0 || st.cnt[p] == 0) continue;
@@ -304,11 +331,23 @@ __global__ void __launch_bounds__(KMAX_THREADS) stack_mixed(RunArgs a)
                                       (unsigned long long)st.cnt[0] | ((unsigned long long)st.cnt[P - 1] << 32));
                             ++n_red;
                         }
-                    };
-                    emit(base, ct.w0);
-                    if (nb > 1) emit(base + (size_t)npol_c, ct.w1);
-                    // a third or fourth bin (lattices narrower than a channel)
-                    for (int b = 2; b < nb; ++b) emit(base + (size_t)b * npol_c, (float)a.chd[chf0 + st.kk].w[b]);
+                    }
+                    if (ckpt) {
+                        // one entry of this run (cycling through its bins and pols):
+                        // complete the lane's previous checkpoint, whose exchanged
+                        // value has long arrived, then exchange this entry's FP32
+                        // sums with zero; the value taken is added to the master
+                        // cube at the lane's next checkpoint (or at the end)
+                        const uint32_t pick = n_runs / CKPT_EVERY;
+                        const int b = (int)(pick / P) % (nb < 2 ? nb : 2), p = (int)(pick % P);
+                        if (plane[p] >= 0 && st.cnt[p] != 0) {
+                            flush_ckpt();
+                            const size_t e = base + (size_t)b * npol_c + plane[p];
+                            ck_took = atomicExch(cube4 + e, make_float4(0.f, 0.f, 0.f, 0.f));
+                            ck_dst = a.cube_master + 4 * e;
+                            ++n_red;
+                        }
+                    }
                 }
             }
             __syncwarp();
@@ -414,6 +453,7 @@ __global__ void __launch_bounds__(KMAX_THREADS) stack_mixed(RunArgs a)
         if (__any_sync(0xffffffffu, (n_read | n_ok | n_duv | n_red) >= 0x40000000u)) flush_counters();
     }
 
+    flush_ckpt();
     // counters (the visibilities read are also counted on the host from the
     // channel tables)
     flush_counters();
