@@ -47,6 +47,8 @@ def parse():
     p.add_argument("--e2e-steps", type=int, default=2, help="timed host-memory steps (0 = skip)")
     p.add_argument("--cpu-sample", type=int, default=2, help="windows timed in the oracle baseline (0 = skip)")
     p.add_argument("--tuning", default="", help="rows,chans_per_lane,warps,sort,prefetch")
+    p.add_argument("--autotune", type=int, default=0,
+                   help="autotune the launch shape first over this many candidates (0 = no)")
     return p.parse_args()
 
 
@@ -289,8 +291,14 @@ def run_ours(args):
 
     # mixed-precision path (the headline)
     st = open_stack(wl, V.PREC_MIXED, tuning)
+    if args.autotune > 0:
+        for s in wl.spws:
+            st.add_source(s.uvw, s.freqs, s.vis, s.weights, s.flags, l=s.l, m=s.m, z=s.z, pol_map=s.pol_map)
+        st.autotune(budget=args.autotune, reps=1)
+        st.run()                       # the queue the autotuner left in place: the first run
+    else:
+        one_step(st, wl)
     eff_tuning = st.tuning()
-    one_step(st, wl)
     f0, df = st.lattice()
     cnt = st.read_cube(which=("count",))["count"]
     touched = int((cnt > 0).sum())

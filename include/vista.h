@@ -137,13 +137,13 @@ typedef struct {
  *   rows_per_item   rows one warp walks through per work item (1..256; their
  *                   FP64 records are staged in shared memory).
  *   chans_per_lane  channels per lane in one item (item = 32 x this many
- *                   channels); also the FP32 phasor recurrence length
- *                   between FP64-derived seeds.
+ *                   channels; 1, 2 or 4).
  *   warps_per_cta   warps per block of the stacking kernel.
  *   sort_rows       1: order rows by uv cell before stacking (fewer
  *                   global reductions), 0: stack in input order.
- *   prefetch_rows   visibility rows each warp keeps in flight (2, 4 or 8;
- *                   used with one or two channels per lane and 1-2 pols). */
+ *   prefetch_rows   visibility rows each warp keeps in flight (2, 4 or 8
+ *                   with one channel per lane, 2 or 4 with two, 2 with
+ *                   four). */
 typedef struct {
     int32_t rows_per_item, chans_per_lane, warps_per_cta, sort_rows, prefetch_rows;
 } vista_tuning;
@@ -205,6 +205,18 @@ typedef struct {
 int vista_enable_timing(vista_stack *h, int on);
 /* Waits for the stream, then reports the totals since timing was enabled. */
 int vista_get_timing(vista_stack *h, vista_timing *out);
+
+/* Autotuner of the launch shape (mixed precision).  Times the queued source
+ * set under up to `budget` candidate shapes (0 = all of a fixed list: rows
+ * per item 32-96, one or two channels per lane, 2-8 warps per block, 2-8
+ * rows in flight; the current shape first), `reps` runs each (0 = 2), by
+ * the event-timed device work of vista_run(), and keeps the fastest as the
+ * handle's tuning (also returned in *best, which may be NULL).  The trial
+ * runs go into the cube, which is zeroed afterwards (with the counters), so
+ * call it before stacking anything worth keeping; the queue is left as it
+ * was.  The paper's own batching is fixed (Sec. 3.3); the shape is this
+ * library's. */
+int vista_autotune(vista_stack *h, int32_t budget, int32_t reps, vista_tuning *best);
 
 /* CUDA-graph replay of a run's device work (on by default).  The device work
  * of a run (flag repacking copies, the row-ordering pre-pass and the stacking

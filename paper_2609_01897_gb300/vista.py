@@ -96,6 +96,7 @@ SIGNATURES = {
     "vista_debug_order": (C.c_int, [_P, C.c_int32, _P]),
     "vista_stack_noalloc": (C.c_int, [C.POINTER(CubeDesc), C.POINTER(SourceDesc), _P, _P]),
     "vista_enable_graphs": (C.c_int, [_P, C.c_int]),
+    "vista_autotune": (C.c_int, [_P, C.c_int32, C.c_int32, C.POINTER(Tuning)]),
     "vista_graph_runs": (C.c_int, [_P, C.POINTER(C.c_uint64)]),
 }
 
@@ -255,6 +256,13 @@ class Stack:
         t = Timing()
         _check("vista_get_timing", lib().vista_get_timing(self.h, C.byref(t)), self.h)
         return t.as_dict()
+
+    def autotune(self, budget=0, reps=0):
+        """Time the queued windows under candidate launch shapes and keep the
+        fastest (the cube is zeroed afterwards; the queue is kept)."""
+        t = Tuning()
+        _check("vista_autotune", lib().vista_autotune(self.h, int(budget), int(reps), C.byref(t)), self.h)
+        return {k: int(getattr(t, k)) for k, _ in Tuning._fields_}
 
     def enable_graphs(self, on=True):
         """Replay the device work of an unchanged source set from a CUDA graph (default on)."""
