@@ -339,10 +339,14 @@ __global__ void __launch_bounds__(KMAX_THREADS) stack_mixed(RunArgs a)
                         // sums with zero; the value taken is added to the master
                         // cube at the lane's next checkpoint (or at the end)
                         const uint32_t pick = n_runs / CKPT_EVERY;
-                        const int b = (int)(pick / P) % (nb < 2 ? nb : 2), p = (int)(pick % P);
-                        if (plane[p] >= 0 && st.cnt[p] != 0) {
+                        const int b = (int)(pick / P) % (nb < 2 ? nb : 2), pp = (int)(pick % P);
+                        int pl = -1;
+#pragma unroll
+                        for (int p = 0; p < P; ++p)   // static indices (no local-memory copy)
+                            if (p == pp && plane[p] >= 0 && st.cnt[p] != 0) pl = plane[p];
+                        if (pl >= 0) {
                             flush_ckpt();
-                            const size_t e = base + (size_t)b * npol_c + plane[p];
+                            const size_t e = base + (size_t)b * npol_c + pl;
                             ck_took = atomicExch(cube4 + e, make_float4(0.f, 0.f, 0.f, 0.f));
                             ck_dst = a.cube_master + 4 * e;
                             ++n_red;
