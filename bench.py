@@ -387,12 +387,29 @@ def run_e2e(args, wl, tuning, n_vis, ws):
     from paper_2609_01897_gb300 import synth
     from paper_2609_01897_gb300 import vista as V
     host, h2d = [], 0
+    f0, df = None, None
     for s in wl.spws:
         hs = synth.SourceSpw(to_pinned(s.uvw), s.freqs, to_pinned(s.vis), to_pinned(s.weights),
                              to_pinned(s.flags), s.l, s.m, s.z, s.pol_map)
-        h2d += sum(t.numel() * t.element_size() for t in (hs.uvw, hs.vis, hs.weights, hs.flags)
-                   if t is not None)
         host.append(hs)
+    # bytes vista_run copies per step: uvw, weights, and the channels it reads
+    # (the in-cube range rounded out to whole flag words) of vis and flags
+    st0 = open_stack(wl, V.PREC_MIXED, tuning)
+    one_step(st0, wl)
+    f0, df = st0.lattice()
+    st0.close()
+    for s in wl.spws:
+        _, nb, _ = V.plan_channels(s.freqs, s.z, f0, df, wl.nrest, V.BIN_OVERLAP)
+        nrow, nch, npol = (int(x) for x in s.vis.shape)
+        ks = np.nonzero(nb > 0)[0]
+        if ks.size == 0 or nrow == 0:
+            continue
+        al = 1 if npol >= 4 else 4 // npol
+        lo, hi = int(ks[0]) // al * al, min(nch, (int(ks[-1]) + 1 + al - 1) // al * al)
+        nin = hi - lo
+        h2d += nrow * (24 + 4 * npol) + nrow * nin * npol * vis_bytes(s.vis)
+        if s.flags is not None:
+            h2d += nrow * ((nin * npol + 3) // 4 * 4)
     ste = open_stack(wl, V.PREC_MIXED, tuning)
     outs, t0 = None, 0.0
     for it in range(1 + args.e2e_steps):

@@ -65,9 +65,12 @@ typedef struct vista_stack vista_stack;   /* opaque handle */
  *              central_freq.  The lattice is fixed at the first run.
  *   central_freq  Hz, used only when rest_df == 0.
  *   bin_mode   VISTA_BIN_OVERLAP (Eqs. 3-4) or VISTA_BIN_NEAREST.
- *   precision  VISTA_PREC_MIXED: FP64 geometry, tables and phase seeds,
- *              FP32 per-visibility body, FP32 cube; VISTA_PREC_FP64: the
- *              plain form, FP64 throughout with an FP64 cube.
+ *   precision  VISTA_PREC_MIXED: FP64 geometry and tables (the delay of
+ *              each row kept as a float-float pair), FP32 per-visibility
+ *              body, an FP32 cube whose entries are moved into an FP64 master
+ *              cube at periodic checkpoints (so the sums stay within ~1e-6
+ *              relative at any stack depth); VISTA_PREC_FP64: the plain
+ *              form, FP64 throughout with an FP64 cube.
  *   hermitian_fold  1: rows with v < 0 (or v == 0, u < 0) are negated and
  *              their shifted visibility conjugated before binning.
  *   stream     cudaStream_t for all device work (NULL = legacy default stream). */
@@ -294,8 +297,10 @@ int vista_debug_order(vista_stack *h, int32_t src, int32_t *dst);
  *   count   caller's device array [nv][nu][nrest][npol] uint32, added to.
  *
  * Returns after the work has finished.  E_RANGE when the window needs more
- * scratch than the array holds (about 75 bytes per row: a 48-byte row
- * record plus the row ordering, i.e. up to ~110 000 rows).  The first call on a device looks up
+ * scratch than the array holds: about 52 bytes per row (a 32-byte row
+ * record and the row ordering) plus 9 bytes per row and 32-channel chunk
+ * (chunk cells, work list), plus the flags when they are not in whole
+ * words, i.e. ~95 000 rows of a 120-channel window.  The first call on a device looks up
  * the array's device address, so make that first call before any stream
  * capture.  All calls share the array: calls whose device work overlaps
  * (other host threads, other streams) race on it and must not be made;

@@ -394,15 +394,19 @@ extern "C" int vista_run(vista_stack *h)
                     stage_pos += al256(nr * fp);
                 }
                 const size_t row_in = (size_t)s.d.nchan * P, row_out = (size_t)nin * P;
+                // whole rows go as one contiguous copy, partial rows as a 2-D copy
+                auto copy_rows = [&](void *dst, size_t dpitch, const void *src, size_t spitch, size_t width) {
+                    if (width == spitch && width == dpitch)
+                        return cudaMemcpyAsync(dst, src, width * nr, cudaMemcpyHostToDevice, h->stream);
+                    return cudaMemcpy2DAsync(dst, dpitch, src, spitch, width, nr, cudaMemcpyHostToDevice, h->stream);
+                };
                 e = cudaMemcpyAsync(p_uvw, s.d.uvw, nr * 24, cudaMemcpyHostToDevice, h->stream);
                 if (e == cudaSuccess)
-                    e = cudaMemcpy2DAsync(p_vis, row_out * esz, (const char *)s.d.vis + (size_t)pl.k_lo * P * esz,
-                                          row_in * esz, row_out * esz, nr, cudaMemcpyHostToDevice, h->stream);
+                    e = copy_rows(p_vis, row_out * esz, (const char *)s.d.vis + (size_t)pl.k_lo * P * esz, row_in * esz,
+                                  row_out * esz);
                 if (e == cudaSuccess)
                     e = cudaMemcpyAsync(p_w, s.d.weights, nr * 4 * P, cudaMemcpyHostToDevice, h->stream);
-                if (e == cudaSuccess && p_f)
-                    e = cudaMemcpy2DAsync(p_f, fp, s.d.flags + (size_t)pl.k_lo * P, row_in, row_out, nr,
-                                          cudaMemcpyHostToDevice, h->stream);
+                if (e == cudaSuccess && p_f) e = copy_rows(p_f, fp, s.d.flags + (size_t)pl.k_lo * P, row_in, row_out);
                 if (e != cudaSuccess) return cuda_fail(h, e, "host-to-device copy of a host-memory window");
                 d.uvw = (const double *)p_uvw;
                 d.vis = p_vis;

@@ -45,6 +45,40 @@ struct __align__(16) Staged {
     float4 acc[P];    // sum W V'.re, sum W V'.im, sum W, sum W |V|^2
 };
 
+// A shared-memory channel-table entry as two 16-byte loads (a 32-byte stride
+// read in 4-byte pieces conflicts eight ways).
+__device__ __forceinline__ ChanF load_chanf(const ChanF *p)
+{
+    const int4 a = *reinterpret_cast<const int4 *>(p);
+    const float4 b = *reinterpret_cast<const float4 *>(reinterpret_cast<const char *>(p) + 16);
+    ChanF c;
+    c.su = __int_as_float(a.x);
+    c.sv = __int_as_float(a.y);
+    c.j0 = a.z;
+    c.nb = a.w;
+    c.w0 = b.x;
+    c.w1 = b.y;
+    c.nuc_hi = b.z;
+    c.nuc_lo = b.w;
+    return c;
+}
+
+// Weight of a third or fourth rest bin (lattices narrower than a channel;
+// out of line so that its FP64 conversion is not hoisted into every drain).
+static __device__ __noinline__ float far_bin_weight(const ChanD *cd, int b) { return (float)cd->w[b]; }
+
+// A float as a double, exactly, by moving its IEEE-754 fields (integer
+// instructions; the FP64 unit converts slowly).  Zero and subnormal inputs
+// give zero (below 1.2e-38), infinities and NaNs do not occur in the sums.
+__device__ __forceinline__ double widen(float x)
+{
+    const uint32_t b = __float_as_uint(x);
+    const uint32_t e = (b >> 23) & 0xffu;
+    if (e == 0u) return 0.0;
+    const uint32_t hi = (b & 0x80000000u) | ((e + 896u) << 20) | ((b & 0x7fffffu) >> 3);
+    return __hiloint2double((int)hi, (int)(b << 29));
+}
+
 // Chunk-cell entries per slot: an item's rows plus the entries that round
 // its bulk copy out to 16-byte boundaries.
 __host__ __device__ constexpr int cc_slot_entries(int rb) { return (rb + 3) & ~1; }
@@ -129,10 +163,10 @@ __global__ void __launch_bounds__(KMAX_THREADS) stack_mixed(RunArgs a)
     double *ck_dst = nullptr;
     auto flush_ckpt = [&]() {
         if (ck_dst) {
-            atomicAdd(ck_dst, (double)ck_took.x);
-            atomicAdd(ck_dst + 1, (double)ck_took.y);
-            atomicAdd(ck_dst + 2, (double)ck_took.z);
-            atomicAdd(ck_dst + 3, (double)ck_took.w);
+            atomicAdd(ck_dst, widen(ck_took.x));
+            atomicAdd(ck_dst + 1, widen(ck_took.y));
+            atomicAdd(ck_dst + 2, widen(ck_took.z));
+            atomicAdd(ck_dst + 3, widen(ck_took.w));
             n_red += 4;
             ck_dst = nullptr;
         }
@@ -245,9 +279,10 @@ __global__ void __launch_bounds__(KMAX_THREADS) stack_mixed(RunArgs a)
 #pragma unroll
         for (int q = 0; q < NS; ++q) {
             const int kk = q * 32 + lane, kc = min(kk, nch - 1);
-            nh[q] = ctab[kc].nuc_hi;
-            nl[q] = ctab[kc].nuc_lo;
-            act[q] = kk < nch && ctab[kc].nb > 0;
+            const ChanF cf = load_chanf(ctab + kc);
+            nh[q] = cf.nuc_hi;
+            nl[q] = cf.nuc_lo;
+            act[q] = kk < nch && cf.nb > 0;
             kv[q] = kc * LB;
             if (act[q]) n_read += (uint32_t)(n * npl);
         }
@@ -308,12 +343,12 @@ __global__ void __launch_bounds__(KMAX_THREADS) stack_mixed(RunArgs a)
                     n_duv += tot;
                 } else {
                     n_ok += tot;
-                    const ChanF &ct = ctab[st.kk];
+                    const ChanF ct = load_chanf(ctab + st.kk);
                     const int nb = ct.nb;
                     const size_t base = ((size_t)st.cell * nrest + ct.j0) * npol_c;
                     const bool ckpt = comp && ((++n_runs & (CKPT_EVERY - 1)) == 0);
                     for (int b = 0; b < nb; ++b) {
-                        const float ww = b == 0 ? ct.w0 : b == 1 ? ct.w1 : (float)a.chd[chf0 + st.kk].w[b];
+                        const float ww = b == 0 ? ct.w0 : b == 1 ? ct.w1 : far_bin_weight(a.chd + chf0 + st.kk, b);
                         const size_t e2 = base + (size_t)b * npol_c;
 #pragma unroll
                         for (int p = 0; p < P; ++p) {
