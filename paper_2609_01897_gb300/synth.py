@@ -239,7 +239,38 @@ def alma_compact(device="cpu", n_sources=64, src_ids=None, meta_only=False, du=N
     return Workload("alma_compact", n, n, 512, 2, du, du, nu_line, spws)
 
 
-def wideband_hi(device="cpu", n_sources=24, src_ids=None) -> Workload:
+CO10_9_REST = 1151.985452e9   # CO(10-9), Hz
+
+
+def mixed(device="cpu", n_sources=64, src_ids=None, meta_only=False, du=None) -> Workload:
+    """Precision workload: 64 sources, 43 antennas with baselines up to 16 km,
+    120 integrations, 4 windows x 960 channels in 340-356 GHz, 2 pols,
+    offsets up to 60" so that |tau nu / c| reaches ~5e3 turns (~3e4 rad).
+    Assumed: window centres 341/343/353/355 GHz, 1.875 GHz wide; z in [2, 3];
+    a CO(10-9) line (rest 1151.985 GHz, also the cube centre) with peak 2x
+    the continuum and FWHM 300 km/s; flux lognormal(mean 0.05 mJy, sigma_ln
+    1); 0.5 mJy noise; 1 % flags; 30 s integrations at dec -30, lat -23; cube
+    256 x 256 x 512 x 2.  The whole set (5.3e10 visibilities, 426 GB as
+    complex64) does not fit on one GPU: it is stacked in waves of sources
+    into one cube (runs are additive)."""
+    width, nchan = 1.875e9, 960
+    df = width / nchan
+    centres = (341e9, 343e9, 353e9, 355e9)
+    sig_ln = 1.0
+    mu_ln = math.log(5e-5) - 0.5 * sig_ln ** 2
+    spws = _make_sources(
+        CONFIG_IDS["mixed"], n_sources, n_ant=43, radius=8000.0, n_int=120, t_int=30.0, lat=-23.0, dec=-30.0,
+        spw_fn=lambda rng, z: [Spw(c - 0.5 * (nchan - 1) * df, df, nchan) for c in centres],
+        npol=2, flux_fn=lambda rng: rng.lognormal(mu_ln, sig_ln), fwhm=0.0, line_rest=CO10_9_REST,
+        line_peak_fn=lambda rng, f: 2.0 * f, line_fwhm=300.0, sigma=5e-4,
+        flag_fn=lambda rng: 0.01, offset_max=60 * ARCSEC, z_lo=2.0, z_hi=3.0, device=device,
+        src_ids=src_ids, meta_only=meta_only)
+    n = 256
+    du = _cube_du(spws, n) if du is None else du
+    return Workload("mixed", n, n, 512, 2, du, du, CO10_9_REST, spws)
+
+
+def wideband_hi(device="cpu", n_sources=24, src_ids=None, meta_only=False, du=None) -> Workload:
     """24 sources, 64 antennas within 8 km, 40 integrations, 856-1712 MHz in
     4096 channels, 2 pols, faint 21 cm line (rest 1420.405752 MHz, peak
     0.02 mJy, FWHM 200 km/s) under 2 mJy noise, z in [0.1, 0.5], cube
@@ -253,9 +284,9 @@ def wideband_hi(device="cpu", n_sources=24, src_ids=None) -> Workload:
         npol=2, flux_fn=lambda rng: 0.0, fwhm=0.0, line_rest=nu_line,
         line_peak_fn=lambda rng, f: 2e-5, line_fwhm=200.0, sigma=2e-3,
         flag_fn=lambda rng: 0.01, offset_max=10 * ARCSEC, z_lo=0.1, z_hi=0.5, device=device,
-        src_ids=src_ids)
+        src_ids=src_ids, meta_only=meta_only)
     n = 512
-    du = _cube_du(spws, n)
+    du = _cube_du(spws, n) if du is None else du
     return Workload("wideband_hi", n, n, 2048, 2, du, du, nu_line, spws)
 
 
