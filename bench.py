@@ -40,12 +40,16 @@ def parse():
     p.add_argument("--steps", type=int, default=10)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    p.add_argument("--config", default="alma_compact", choices=["alma_compact", "tiny", "wideband_hi", "batched"])
+    p.add_argument("--config", default="alma_compact", choices=["alma_compact", "tiny", "wideband_hi", "batched", "mixed"])
+    p.add_argument("--storage", default="c64", choices=["c64", "f16", "bf16"],
+                   help="visibility storage (16-bit: one power-of-two scale per window)")
     p.add_argument("--pool-gb", type=float, default=96.0, help="batched: device pool the windows alias (GB)")
     p.add_argument("--sources", type=int, default=0, help="sources per rank (0 = the workload's own)")
     p.add_argument("--fp64-steps", type=int, default=2, help="timed steps of the plain FP64 leg (0 = skip)")
     p.add_argument("--e2e-steps", type=int, default=2, help="timed host-memory steps (0 = skip)")
-    p.add_argument("--cpu-sample", type=int, default=2, help="windows timed in the oracle baseline (0 = skip)")
+    p.add_argument("--cpu-sample", type=int, default=40,
+                   help="windows timed once in the oracle baseline of our arm (0 = skip)")
+    p.add_argument("--ref-sample", type=int, default=8, help="windows per step of the reference (oracle) arm")
     p.add_argument("--tuning", default="", help="rows,chans_per_lane,warps,sort,prefetch")
     p.add_argument("--autotune", type=int, default=0,
                    help="autotune the launch shape first over this many candidates (0 = no)")
@@ -161,17 +165,55 @@ def measured_peaks():
 
 # ------------------------------------------------------------------ workload
 
+def in_cube_sources(meta, nrest):
+    """Rest lattice of a whole source set and the ids of the sources with a
+    channel inside it (computed by the library's host planner)."""
+    from paper_2609_01897_gb300 import vista as V
+    f0, df = V.plan_lattice([s.freqs for s in meta.spws], [s.z for s in meta.spws], nrest, meta.central_freq)
+    ids = set()
+    for s in meta.spws:
+        _, nb, _ = V.plan_channels(s.freqs, s.z, f0, df, nrest, V.BIN_OVERLAP)
+        if (nb > 0).any():
+            ids.add(s.source)
+    return f0, df, sorted(ids)
+
+
 def make_workload(args, rank, device):
     from paper_2609_01897_gb300 import synth
     if args.config == "tiny":
-        return synth.tiny(device)
-    n = args.sources or {"alma_compact": 64, "wideband_hi": 24, "batched": 2000}[args.config]
-    ids = range(rank * n, rank * n + n)
-    if args.config == "alma_compact":
-        return synth.alma_compact(device, n_sources=n, src_ids=ids)
-    if args.config == "batched":
-        return synth.batched(device, n_sources=n, src_ids=ids, pool_gb=args.pool_gb)
-    return synth.wideband_hi(device, n_sources=n, src_ids=ids)
+        wl = synth.tiny(device)
+    elif args.config == "mixed":
+        # the sources of a 64-source set whose windows reach the cube, on the
+        # lattice and cell size of the whole set (the rest never add a visibility)
+        n = args.sources or 64
+        meta = synth.mixed("cpu", n_sources=n, src_ids=range(rank * n, rank * n + n), meta_only=True)
+        f0, df, ids = in_cube_sources(meta, meta.nrest)
+        wl = synth.mixed(device, src_ids=ids, du=meta.du)
+        wl.rest_f0, wl.rest_df = f0, df
+    elif args.config == "wideband_hi":
+        # the complex-half variant holds 48 sources (drawn directly as 16-bit pairs)
+        n = args.sources or (24 if args.storage == "c64" else 48)
+        ids = range(rank * n, rank * n + n)
+        return synth.wideband_hi(device, n_sources=n, src_ids=ids, storage=args.storage)
+    else:
+        n = args.sources or {"alma_compact": 64, "batched": 2000}[args.config]
+        ids = range(rank * n, rank * n + n)
+        if args.config == "alma_compact":
+            wl = synth.alma_compact(device, n_sources=n, src_ids=ids)
+        else:
+            wl = synth.batched(device, n_sources=n, src_ids=ids, pool_gb=args.pool_gb)
+    if args.storage != "c64":
+        if args.config == "batched":
+            raise SystemExit("--storage applies to workloads with their own arrays (not the aliased pool)")
+        wl = synth.half_storage(wl, args.storage)
+    return wl
+
+
+def host_vis(s):
+    """A window's visibilities as complex numpy (16-bit storage dequantised)."""
+    if s.vis.dtype in (torch.float16, torch.bfloat16):
+        return torch.view_as_complex(s.vis.to(torch.float32).mul_(s.vis_scale)).cpu().numpy()
+    return s.vis.cpu().numpy()
 
 
 def vis_bytes(v):
@@ -203,7 +245,8 @@ def one_step(st, wl, host=None):
     The cube accumulates across steps (runs are additive)."""
     srcs = wl.spws if host is None else host
     for s in srcs:
-        st.add_source(s.uvw, s.freqs, s.vis, s.weights, s.flags, l=s.l, m=s.m, z=s.z, pol_map=s.pol_map)
+        st.add_source(s.uvw, s.freqs, s.vis, s.weights, s.flags, l=s.l, m=s.m, z=s.z, pol_map=s.pol_map,
+                      vis_scale=s.vis_scale)
     st.run()
 
 
@@ -211,8 +254,8 @@ def one_step(st, wl, host=None):
 
 def open_stack(wl, precision, tuning):
     from paper_2609_01897_gb300 import vista as V
-    st = V.Stack(wl.nu, wl.nv, wl.nrest, wl.npol, wl.du, wl.dv, central_freq=wl.central_freq,
-                 precision=precision)
+    st = V.Stack(wl.nu, wl.nv, wl.nrest, wl.npol, wl.du, wl.dv, rest_f0=wl.rest_f0, rest_df=wl.rest_df,
+                 central_freq=wl.central_freq, precision=precision)
     if tuning:
         st.set_tuning(*tuning)
     return st
@@ -267,7 +310,7 @@ def cpu_baseline(wl, f0, df, nsample):
     from oracle import oracle as O
     srcs = []
     for s in windows_in_cube(wl, f0, df, nsample):
-        srcs.append(O.Source(s.uvw.cpu().numpy(), s.freqs, s.vis.cpu().numpy(), s.weights.cpu().numpy(),
+        srcs.append(O.Source(s.uvw.cpu().numpy(), s.freqs, host_vis(s), s.weights.cpu().numpy(),
                              None if s.flags is None else s.flags.cpu().numpy(), s.l, s.m, s.z, s.pol_map))
     cube = O.make_cube(wl.nu, wl.nv, wl.nrest, wl.npol, wl.du, wl.dv, f0, df, 0, 0)
     nthreads = os.cpu_count() or 1
@@ -276,7 +319,7 @@ def cpu_baseline(wl, f0, df, nsample):
     dt = time.perf_counter() - t0
     n = int(out["stats"]["n_vis"])
     return {"value": n / dt, "unit": UNIT, "cores": nthreads, "kind": "oracle",
-            "sample": "%d of %d windows (%d visibilities), %.1f s" % (nsample, len(wl.spws), n, dt)}
+            "sample": "%d of %d windows (%d visibilities), %.1f s" % (len(srcs), len(wl.spws), n, dt)}
 
 
 def run_ours(args):
@@ -293,7 +336,8 @@ def run_ours(args):
     st = open_stack(wl, V.PREC_MIXED, tuning)
     if args.autotune > 0:
         for s in wl.spws:
-            st.add_source(s.uvw, s.freqs, s.vis, s.weights, s.flags, l=s.l, m=s.m, z=s.z, pol_map=s.pol_map)
+            st.add_source(s.uvw, s.freqs, s.vis, s.weights, s.flags, l=s.l, m=s.m, z=s.z, pol_map=s.pol_map,
+                          vis_scale=s.vis_scale)
         st.autotune(budget=args.autotune, reps=1)
         st.run()                       # the queue the autotuner left in place: the first run
     else:
@@ -390,7 +434,7 @@ def run_e2e(args, wl, tuning, n_vis, ws):
     f0, df = None, None
     for s in wl.spws:
         hs = synth.SourceSpw(to_pinned(s.uvw), s.freqs, to_pinned(s.vis), to_pinned(s.weights),
-                             to_pinned(s.flags), s.l, s.m, s.z, s.pol_map)
+                             to_pinned(s.flags), s.l, s.m, s.z, s.pol_map, s.source, s.vis_scale)
         host.append(hs)
     # bytes vista_run copies per step: uvw, weights, and the channels it reads
     # (the in-cube range rounded out to whole flag words) of vis and flags
@@ -400,7 +444,7 @@ def run_e2e(args, wl, tuning, n_vis, ws):
     st0.close()
     for s in wl.spws:
         _, nb, _ = V.plan_channels(s.freqs, s.z, f0, df, wl.nrest, V.BIN_OVERLAP)
-        nrow, nch, npol = (int(x) for x in s.vis.shape)
+        nrow, nch, npol = (int(x) for x in s.vis.shape[:3])
         ks = np.nonzero(nb > 0)[0]
         if ks.size == 0 or nrow == 0:
             continue
@@ -418,7 +462,8 @@ def run_e2e(args, wl, tuning, n_vis, ws):
             barrier(ws)
             t0 = time.perf_counter()
         one_step(ste, wl, host)
-        outs = ste.read_cube(device=False)
+        # the pinned result buffers are allocated once (first, untimed step)
+        outs = ste.read_cube(device=False, out=outs)
     dt = (time.perf_counter() - t0) / args.e2e_steps
     d2h = sum(v.numel() * v.element_size() for v in outs.values())
     ste.close()
@@ -433,9 +478,13 @@ def workload_name(wl):
                 "128-3840 ch, 2/4 pol c64, aliased into a device pool; cube %dx%dx%dx%d" % (
                     len(wl.spws), len({s.source for s in wl.spws}), wl.nv, wl.nu, wl.nrest, wl.npol))
     s0 = wl.spws[0]
-    return "%s: %d windows (%d sources), %d rows/window, %d ch x %d pol c64; cube %dx%dx%dx%d" % (
-        wl.name, len(wl.spws), len({s.source for s in wl.spws}), int(s0.vis.shape[0]), int(s0.vis.shape[1]),
-        int(s0.vis.shape[2]), wl.nv, wl.nu, wl.nrest, wl.npol)
+    storage = {torch.complex64: "c64", torch.float16: "FP16 pairs", torch.bfloat16: "BF16 pairs"}[s0.vis.dtype]
+    extra = ""
+    if wl.name.startswith("mixed"):
+        extra = " (the sources of 64 whose windows reach the cube; lattice and cell size of all 64)"
+    return "%s: %d windows (%d sources)%s, %d rows/window, %d ch x %d pol %s; cube %dx%dx%dx%d" % (
+        wl.name, len(wl.spws), len({s.source for s in wl.spws}), extra, int(s0.vis.shape[0]),
+        int(s0.vis.shape[1]), int(s0.vis.shape[2]), storage, wl.nv, wl.nu, wl.nrest, wl.npol)
 
 
 def st_tuning_str(t):
@@ -453,25 +502,30 @@ def run_reference(args):
         return
     from oracle import oracle as O
     dev = "cuda" if torch.cuda.is_available() else "cpu"
-    nsample = max(1, args.cpu_sample)
-    if args.config == "alma_compact":
+    nsample = max(1, args.ref_sample)
+    from paper_2609_01897_gb300 import synth
+    gen = {"alma_compact": synth.alma_compact, "mixed": synth.mixed, "wideband_hi": synth.wideband_hi}.get(args.config)
+    if gen is not None:
         # geometry and channel axes of every source (the lattice and the cell
         # size depend on all), visibilities only for the sampled windows
-        from paper_2609_01897_gb300 import synth
-        meta = synth.alma_compact("cpu", n_sources=64, meta_only=True)
+        n = args.sources or {"wideband_hi": 24 if args.storage == "c64" else 48}.get(args.config, 64)
+        meta = gen("cpu", n_sources=n, meta_only=True)
         f0, df = O.auto_lattice([s.freqs for s in meta.spws], [s.z for s in meta.spws], meta.nrest,
                                 meta.central_freq)
         picked = windows_in_cube(meta, f0, df, nsample)
         ids = sorted({s.source for s in picked})
-        wl = synth.alma_compact(dev, src_ids=ids, du=meta.du)
+        wl = gen(dev, n_sources=n, src_ids=ids, du=meta.du)
         keep = {(s.source, float(s.freqs[0])) for s in picked}
-        spws = [s for s in wl.spws if (s.source, float(s.freqs[0])) in keep]
+        wl.spws = [s for s in wl.spws if (s.source, float(s.freqs[0])) in keep]
+        if args.storage != "c64":
+            wl = synth.half_storage(wl, args.storage)
+        spws = wl.spws
     else:
         wl = make_workload(argparse.Namespace(**vars(args)), 0, dev)
         f0, df = O.auto_lattice([s.freqs for s in wl.spws], [s.z for s in wl.spws], wl.nrest,
                                 wl.central_freq)
         spws = windows_in_cube(wl, f0, df, nsample)
-    srcs = [O.Source(s.uvw.cpu().numpy(), s.freqs, s.vis.cpu().numpy(), s.weights.cpu().numpy(),
+    srcs = [O.Source(s.uvw.cpu().numpy(), s.freqs, host_vis(s), s.weights.cpu().numpy(),
                      None if s.flags is None else s.flags.cpu().numpy(), s.l, s.m, s.z, s.pol_map) for s in spws]
     cube = O.make_cube(wl.nu, wl.nv, wl.nrest, wl.npol, wl.du, wl.dv, f0, df, 0, 0)
     nthreads = os.cpu_count() or 1

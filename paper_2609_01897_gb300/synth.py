@@ -54,6 +54,7 @@ class SourceSpw:
     z: float
     pol_map: Optional[np.ndarray] = None
     source: int = 0
+    vis_scale: float = 1.0       # 16-bit storage: stored value x vis_scale = visibility
 
 
 @dataclass
@@ -162,7 +163,11 @@ def _cube_du(spws: List[SourceSpw], n: int) -> float:
 
 def _make_sources(cid: int, n_src: int, *, n_ant, radius, n_int, t_int, lat, dec, spw_fn,
                   npol, flux_fn, fwhm, line_rest, line_peak_fn, line_fwhm, sigma,
-                  flag_fn, offset_max, z_lo, z_hi, device, src_ids=None, meta_only=False) -> List[SourceSpw]:
+                  flag_fn, offset_max, z_lo, z_hi, device, src_ids=None, meta_only=False,
+                  storage="c64") -> List[SourceSpw]:
+    """storage "f16" / "bf16": each window is converted to 16-bit pairs right
+    after it is drawn (see half_pairs), so the complex form of the whole set
+    never exists at once."""
     out = []
     ids = range(n_src) if src_ids is None else src_ids
     for s in ids:
@@ -191,7 +196,10 @@ def _make_sources(cid: int, n_src: int, *, n_ant, radius, n_int, t_int, lat, dec
             v = v + noise
             wts = torch.full((uvw.shape[0], npol), 1.0 / sigma ** 2, dtype=torch.float32,
                              device=device)
-            out.append(SourceSpw(uvw, f, v, wts, flags, l0, m0, z, source=s))
+            scale = 1.0
+            if storage != "c64":
+                v, scale = half_pairs(v, storage)
+            out.append(SourceSpw(uvw, f, v, wts, flags, l0, m0, z, source=s, vis_scale=scale))
     return out
 
 
@@ -270,12 +278,41 @@ def mixed(device="cpu", n_sources=64, src_ids=None, meta_only=False, du=None) ->
     return Workload("mixed", n, n, 512, 2, du, du, CO10_9_REST, spws)
 
 
-def wideband_hi(device="cpu", n_sources=24, src_ids=None, meta_only=False, du=None) -> Workload:
+def half_pairs(vis: torch.Tensor, kind: str):
+    """One window's complex visibilities as 16-bit (re, im) pairs,
+    [nrow, nchan, npol, 2], with one power-of-two scale (exact in any
+    precision): FP16 maps the largest |component| below 2^15, BF16 below 1.
+    Returns (pairs, scale); pairs x scale = the stored visibility."""
+    if kind not in ("f16", "bf16"):
+        raise ValueError("kind is f16 or bf16")
+    dt = torch.float16 if kind == "f16" else torch.bfloat16
+    re_im = torch.view_as_real(vis)
+    amax = float(re_im.abs().max()) if re_im.numel() else 1.0
+    e = math.ceil(math.log2(amax)) if amax > 0 else 0
+    scale = 2.0 ** (e - 15) if kind == "f16" else 2.0 ** e
+    return (re_im / scale).to(dt).contiguous(), scale
+
+
+def half_storage(wl: Workload, kind: str) -> Workload:
+    """The workload with its visibilities stored as 16-bit pairs (half_pairs),
+    converted one window at a time, the complex originals dropped."""
+    out = []
+    for s in wl.spws:
+        q, scale = half_pairs(s.vis, kind)
+        out.append(SourceSpw(s.uvw, s.freqs, q, s.weights, s.flags, s.l, s.m, s.z, s.pol_map, s.source, scale))
+        s.vis = None
+    return Workload(wl.name + "-" + kind, wl.nu, wl.nv, wl.nrest, wl.npol, wl.du, wl.dv, wl.central_freq, out,
+                    rest_df=wl.rest_df, rest_f0=wl.rest_f0)
+
+
+def wideband_hi(device="cpu", n_sources=24, src_ids=None, meta_only=False, du=None, storage="c64") -> Workload:
     """24 sources, 64 antennas within 8 km, 40 integrations, 856-1712 MHz in
     4096 channels, 2 pols, faint 21 cm line (rest 1420.405752 MHz, peak
     0.02 mJy, FWHM 200 km/s) under 2 mJy noise, z in [0.1, 0.5], cube
     512 x 512 x 2048.  Assumed: MeerKAT-like latitude -30.7, dec -30,
-    no continuum, 8 s integrations, 1 % flags, offsets within +-10"."""
+    no continuum, 8 s integrations, 1 % flags, offsets within +-10".
+    The complex-half variant stacks 48 sources stored as 16-bit pairs
+    (storage "f16" / "bf16", drawn window by window)."""
     nu_line = 1420.405752e6
     df = (1712e6 - 856e6) / 4096
     spws = _make_sources(
@@ -284,7 +321,7 @@ def wideband_hi(device="cpu", n_sources=24, src_ids=None, meta_only=False, du=No
         npol=2, flux_fn=lambda rng: 0.0, fwhm=0.0, line_rest=nu_line,
         line_peak_fn=lambda rng, f: 2e-5, line_fwhm=200.0, sigma=2e-3,
         flag_fn=lambda rng: 0.01, offset_max=10 * ARCSEC, z_lo=0.1, z_hi=0.5, device=device,
-        src_ids=src_ids, meta_only=meta_only)
+        src_ids=src_ids, meta_only=meta_only, storage=storage)
     n = 512
     du = _cube_du(spws, n) if du is None else du
     return Workload("wideband_hi", n, n, 2048, 2, du, du, nu_line, spws)

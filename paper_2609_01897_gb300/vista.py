@@ -207,15 +207,27 @@ class Stack:
         self._pending = []
 
     # -- results
-    def read_cube(self, device=True, f64=False, which=("sum_wv", "sum_w", "sum_wvv", "count")):
+    def read_cube(self, device=True, f64=False, which=("sum_wv", "sum_w", "sum_wvv", "count"), out=None):
+        """The cube's sums (ΣwV as [..., 2]) and counts, on the device or in
+        pinned host memory.  `out` (a dict from an earlier call with the same
+        device / f64 / which) is filled in place instead of allocating: pinning
+        a host buffer of the cube's size costs more than the copy itself."""
         nv, nu, nrest, npol = self.shape
         dt = torch.float64 if f64 else torch.float32
-        kw = {"device": "cuda"} if device else {"pin_memory": torch.cuda.is_available()}
-        out = {}
-        out["sum_wv"] = torch.empty((nv, nu, nrest, npol, 2), dtype=dt, **kw) if "sum_wv" in which else None
-        out["sum_w"] = torch.empty((nv, nu, nrest, npol), dtype=dt, **kw) if "sum_w" in which else None
-        out["sum_wvv"] = torch.empty((nv, nu, nrest, npol), dtype=dt, **kw) if "sum_wvv" in which else None
-        out["count"] = torch.empty((nv, nu, nrest, npol), dtype=torch.int32, **kw) if "count" in which else None
+        shapes = {"sum_wv": ((nv, nu, nrest, npol, 2), dt), "sum_w": ((nv, nu, nrest, npol), dt),
+                  "sum_wvv": ((nv, nu, nrest, npol), dt), "count": ((nv, nu, nrest, npol), torch.int32)}
+        if out is not None:
+            for k in which:
+                t = out.get(k)
+                shp, tdt = shapes[k]
+                if (t is None or tuple(t.shape) != shp or t.dtype != tdt or t.is_cuda != bool(device)
+                        or not t.is_contiguous()):
+                    raise ValueError("out[%r] must be a contiguous %s tensor of shape %s on the %s" % (
+                        k, tdt, shp, "device" if device else "host"))
+            out = {k: (out[k] if k in which else None) for k in shapes}
+        else:
+            kw = {"device": "cuda"} if device else {"pin_memory": torch.cuda.is_available()}
+            out = {k: (torch.empty(shp, dtype=tdt, **kw) if k in which else None) for k, (shp, tdt) in shapes.items()}
         fn = lib().vista_read_cube_f64 if f64 else lib().vista_read_cube
         _check("vista_read_cube", fn(self.h, _ptr(out["sum_wv"]), _ptr(out["sum_w"]),
                                      _ptr(out["sum_wvv"]), _ptr(out["count"]), 1 if device else 0),

@@ -68,8 +68,10 @@ def test_batched_full_mixed_against_fp64(V):
             float(rel.flatten()[i]), i, int(d["count"].flatten()[i]), float(ref.flatten()[i]))
     for key in ("sum_w", "sum_wvv"):
         err = (m[key] - d[key]).abs()
+        print("batched full, %s: %s" % (key, worst(err, d[key].abs())))
         assert bool((err <= H.TOL_MIXED * d[key].abs() + 1e-300).all()), key + ": " + worst(err, d[key].abs())
     err = (m["sum_wv"] - d["sum_wv"]).abs().amax(dim=-1)
+    print("batched full, sum_wv: %s" % worst(err, scale))
     assert bool((err <= H.TOL_MIXED * scale + 1e-300).all()), "sum_wv: " + worst(err, scale)
     sm, sd = stats[V.PREC_MIXED], stats[V.PREC_FP64]
     for k in ("n_vis", "n_flagged", "n_dropped_uv", "n_stacked"):

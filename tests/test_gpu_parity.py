@@ -288,3 +288,24 @@ def test_all_flagged_and_empty(V, tiny):
     st.close()
     assert int(c["count"].sum()) == 0 and float(c["sum_w"].abs().sum()) == 0.0
     assert stats["n_flagged"] == stats["n_vis"] > 0 and stats["n_stacked"] == 0
+
+
+def test_host_readback_into_caller_buffers(V, tiny):
+    st = V.Stack(tiny.nu, tiny.nv, tiny.nrest, tiny.npol, tiny.du, tiny.dv, central_freq=tiny.central_freq)
+    try:
+        for s in tiny.spws:
+            st.add_source(s.uvw, s.freqs, s.vis, s.weights, s.flags, l=s.l, m=s.m, z=s.z)
+        st.run()
+        dev = {k: v.cpu() for k, v in st.read_cube(device=True).items()}
+        host = st.read_cube(device=False)
+        ptrs = {k: v.data_ptr() for k, v in host.items()}
+        for v in host.values():
+            v.zero_()
+        again = st.read_cube(device=False, out=host)
+        with pytest.raises(ValueError):
+            st.read_cube(device=False, out={"sum_w": host["sum_w"][:1]}, which=("sum_w",))
+    finally:
+        st.close()
+    for k in dev:
+        assert again[k].data_ptr() == ptrs[k]          # filled in place
+        assert torch.equal(again[k], dev[k]), k
