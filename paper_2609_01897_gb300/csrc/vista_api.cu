@@ -97,11 +97,20 @@ void span_end(vista_stack *h, int id)
     if (id >= 0) cudaEventRecord(h->spans[(size_t)id].b, h->stream);
 }
 
-uint64_t fnv1a(const void *p, size_t n, uint64_t h)
+uint64_t freq_digest(const double *f, size_t n)
 {
-    const unsigned char *b = static_cast<const unsigned char *>(p);
-    for (size_t i = 0; i < n; ++i) h = (h ^ b[i]) * 1099511628211ull;
-    return h;
+    // FNV-1a's xor-multiply step on whole 64-bit words, four independent
+    // lanes (no serial chain through every byte): each step is a bijection of
+    // the lane state, so a single changed word always changes the digest
+    uint64_t h[4] = {1469598103934665603ull, 0x9e3779b97f4a7c15ull, 0xc2b2ae3d27d4eb4full, 0x165667b19e3779f9ull};
+    for (size_t i = 0; i < n; ++i) {
+        uint64_t w;
+        std::memcpy(&w, f + i, sizeof w);
+        h[i & 3] = (h[i & 3] ^ w) * 1099511628211ull;
+    }
+    uint64_t d = n;
+    for (int k = 0; k < 4; ++k) d = (d ^ h[k] ^ (h[k] >> 29)) * 0xbf58476d1ce4e5b9ull;
+    return d;
 }
 
 void drop_graph(vista_stack *h)
@@ -235,7 +244,7 @@ extern "C" int vista_add_source(vista_stack *h, const vista_source_desc *s)
     SrcHost sh;
     sh.d = *s;
     sh.freqs.assign(s->freqs, s->freqs + s->nchan);
-    sh.freq_digest = fnv1a(sh.freqs.data(), sh.freqs.size() * sizeof(double));
+    sh.freq_digest = freq_digest(sh.freqs.data(), sh.freqs.size());
     sh.pol_map.resize((size_t)s->npol);
     for (int p = 0; p < s->npol; ++p) {
         const int32_t q = s->pol_map ? s->pol_map[p] : p;

@@ -40,7 +40,7 @@ struct SrcHost {
     vista_source_desc d;
     std::vector<double> freqs;
     std::vector<int32_t> pol_map;   // npol entries (identity filled in)
-    uint64_t freq_digest = 0;       // FNV-1a of the frequency bytes
+    uint64_t freq_digest = 0;       // digest of the frequencies (freq_digest())
 };
 
 // A device-to-device 2-D copy of a run's device pass (flag repacking).
@@ -109,7 +109,7 @@ int cuda_fail(vista_stack *h, cudaError_t e, const char *what);
 int span_begin(vista_stack *h, int kind);
 void span_end(vista_stack *h, int id);
 size_t vis_elem_bytes(int vt);
-uint64_t fnv1a(const void *p, size_t n, uint64_t h = 1469598103934665603ull);
+uint64_t freq_digest(const double *f, size_t n);   // change detection of a frequency axis
 void drop_graph(vista_stack *h);
 
 }  // namespace vista

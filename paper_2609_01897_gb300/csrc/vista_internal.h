@@ -221,7 +221,7 @@ struct RunArgs {
 
 // Kernel launchers (vista_kernels.cu).  Return a cudaError_t.
 // Row ordering, records and work list of one mixed class (several kernels).
-cudaError_t launch_prepare(const RunArgs &a, cudaStream_t st);
+cudaError_t launch_prepare(const RunArgs &a, cudaStream_t st, int *nlaunch = nullptr);   // kernels launched
 // Persistent stacking kernel of one mixed class; key = (vis_type << 16) |
 // (chans_per_lane << 8) | npol, shared by every window of the class.
 cudaError_t launch_mixed(const RunArgs &a, int key, int warps_per_cta, int prefetch, cudaStream_t st);

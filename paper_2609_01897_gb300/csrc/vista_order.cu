@@ -8,7 +8,8 @@
 //   k_keys         cell of every row at the window's highest in-cube
 //                  frequency -> (stripe, local cell key); stripe counts per
 //                  segment of rows
-//   k_segscan      segment offsets inside each (window, stripe) bucket
+//   k_segscan      segment offsets inside each (window, stripe) bucket (a
+//                  warp scan per bucket)
 //   k_slots        each row's slot in its bucket, in row order
 //   k_scan         one block: per-window bucket offsets, per-bucket work-list
 //                  offsets in stripe-major order (item = rows of one bucket x
@@ -16,10 +17,11 @@
 //   k_items        the work list, one thread per item
 //   k_scatter      rows grouped by bucket
 //   k_bucket_sort  one block per bucket: stable counting sort by local cell
-//                  key (the rows of one key stay in row order)
-//   k_records      per row, in processing order: the FP64 delay of Eq. 2 as
-//                  a float-float pair and the (fold-signed) weights
-//   k_cells        per (row, channel chunk): the chunk's uv cells
+//                  key (the rows of one key stay in row order), one
+//                  contiguous part of the bucket per warp
+//   k_rows         per row, in processing order: the FP64 delay of Eq. 2 as
+//                  a float-float pair, the (fold-signed) weights, and the
+//                  uv cells of each of the window's channel chunks
 #include "vista_device.cuh"
 
 namespace vista {
@@ -88,55 +90,98 @@ __global__ void __launch_bounds__(256) k_keys(RunArgs a)
     for (int k = threadIdx.x; k < so.nstripe; k += blockDim.x) so.segcnt[seg * so.nstripe + k] = cnt[k];
 }
 
-// Pass 2: one thread per (window, stripe): the segments' first slots and the
-// bucket's row count.
+// Pass 2: one warp per (window, stripe): the segments' first slots (an
+// exclusive scan of the counts over the window's segments, 32 at a time)
+// and the bucket's row count.
 __global__ void __launch_bounds__(256) k_segscan(RunArgs a)
 {
     const SortArgs &so = a.so;
-    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (!so.sorted || t >= (int64_t)a.nsrc * so.nstripe) return;
+    const int64_t t = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (!so.sorted || t >= (int64_t)a.nsrc * so.nstripe) return;   // whole warps
     const int w = (int)(t / so.nstripe), k = (int)(t % so.nstripe);
+    const int64_t s1 = so.seg_off[w + 1];
     uint32_t run = 0;
-    for (int64_t seg = so.seg_off[w]; seg < so.seg_off[w + 1]; ++seg) {
+    for (int64_t s0 = so.seg_off[w]; s0 < s1; s0 += 32) {
+        const int64_t seg = s0 + lane;
         uint32_t *c = so.segcnt + seg * so.nstripe + k;
-        const uint32_t n = *c;
-        *c = run;
-        run += n;
+        const uint32_t n = seg < s1 ? *c : 0u;
+        uint32_t incl = n;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += y;
+        }
+        if (seg < s1) *c = run + incl - n;
+        run += __shfl_sync(0xffffffffu, incl, 31);
     }
-    so.hist[t] = run;
+    if (lane == 0) so.hist[t] = run;
 }
 
-// Pass 3: each segment's slots in row order.
+// Pass 3: each segment's slots in row order.  Warp w of W takes the
+// contiguous w-th part of the segment, counts its stripes into its own
+// shared-memory row, the counts become offsets (the segment's first slots
+// plus the earlier warps' counts), and the warp assigns its rows in order.
+// Dynamic shared memory: W x nstripe words.
 __global__ void __launch_bounds__(256) k_slots(RunArgs a)
 {
-    __shared__ uint32_t run[MAX_STRIPES];
+    extern __shared__ uint32_t dsm[];
     const SortArgs &so = a.so;
     if (!so.sorted) return;
     const int64_t seg = blockIdx.x;
     const SegRange sr = seg_range(a, seg);
+    const int ns = so.nstripe;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
-    for (int k = threadIdx.x; k < so.nstripe; k += blockDim.x) run[k] = so.segcnt[seg * so.nstripe + k];
+    uint32_t *cnt = dsm + (size_t)warp * ns;
+    for (int i = threadIdx.x; i < nwarps * ns; i += blockDim.x) dsm[i] = 0u;
     __syncthreads();
-    for (int64_t c = sr.r0; c < sr.r1; c += blockDim.x) {
-        const int64_t r = c + threadIdx.x;
-        const uint32_t stripe = r < sr.r1 ? so.key[sr.g0 + r] >> 13 : NO_BUCKET;
+    const int64_t nr = sr.r1 - sr.r0;
+    const int64_t p0 = sr.r0 + nr * warp / nwarps, p1 = sr.r0 + nr * (warp + 1) / nwarps;
+    for (int64_t c = p0; c < p1; c += 32) {
+        const int64_t r = c + lane;
+        const uint32_t stripe = r < p1 ? so.key[sr.g0 + r] >> 13 : NO_BUCKET;
+        const unsigned peers = __match_any_sync(0xffffffffu, stripe);
+        if (stripe != NO_BUCKET && lane == __ffs(peers) - 1) cnt[stripe] += (uint32_t)__popc(peers);
+    }
+    __syncthreads();
+    for (int k = threadIdx.x; k < ns; k += blockDim.x) {
+        uint32_t run = so.segcnt[seg * ns + k];
+        for (int v = 0; v < nwarps; ++v) {
+            const uint32_t c = dsm[(size_t)v * ns + k];
+            dsm[(size_t)v * ns + k] = run;
+            run += c;
+        }
+    }
+    __syncthreads();
+    for (int64_t c = p0; c < p1; c += 32) {
+        const int64_t r = c + lane;
+        const uint32_t stripe = r < p1 ? so.key[sr.g0 + r] >> 13 : NO_BUCKET;
         const unsigned peers = __match_any_sync(0xffffffffu, stripe);
         const int leader = __ffs(peers) - 1;
-        const uint32_t rank = __popc(peers & ((1u << lane) - 1u));
-        uint32_t slot = 0;
-        for (int wi = 0; wi < nwarps; ++wi) {
-            if (warp == wi) {
-                uint32_t base = 0;
-                if (lane == leader && stripe != NO_BUCKET) {
-                    base = run[stripe];
-                    run[stripe] = base + (uint32_t)__popc(peers);
-                }
-                slot = __shfl_sync(peers, base, leader) + rank;
-            }
-            __syncthreads();
+        uint32_t b0 = 0;
+        if (stripe != NO_BUCKET && lane == leader) {
+            b0 = cnt[stripe];
+            cnt[stripe] = b0 + (uint32_t)__popc(peers);
         }
-        if (r < sr.r1) so.slot[sr.g0 + r] = slot;
+        const uint32_t slot = __shfl_sync(0xffffffffu, b0, leader) + (uint32_t)__popc(peers & ((1u << lane) - 1u));
+        if (r < p1) so.slot[sr.g0 + r] = slot;
     }
+}
+
+// Warps per block for a per-warp table of nk words in shared memory
+// (tables + extra tables of nk words kept within 96 KB).
+static int table_warps(int nk, int extra)
+{
+    int nw = (int)(96 * 1024 / (4 * (int64_t)(nk > 0 ? nk : 1))) - extra;
+    return nw < 1 ? 1 : (nw > 8 ? 8 : nw);
+}
+
+// Launch a kernel that takes dynamic shared memory above the 48 KB default.
+template <typename K>
+static cudaError_t allow_smem(K kern, size_t smem)
+{
+    if (smem <= 48 * 1024) return cudaSuccess;
+    return cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
 }
 
 // One block of 1024 threads.
@@ -232,9 +277,19 @@ __global__ void __launch_bounds__(256) k_scatter(RunArgs a)
     so.tmp[a.row_off[w] + q] = ((unsigned long long)L << 32) | r;
 }
 
-// One block per (window, stripe) bucket.
+// One block per (window, stripe) bucket: a stable counting sort of the
+// bucket's rows by local cell key.  The rows arrive in row order (k_slots)
+// and keep it within each key, so that rows of one baseline stay
+// consecutive in time and, at the window's other channels, a group's cell
+// changes at most once instead of alternating.  Warp w of W takes the
+// contiguous w-th part of the bucket: it counts its keys into its own
+// shared-memory row (no block barrier per 32 rows), the counts become
+// offsets (key-major, then warp), and the warp scatters its part in order.
+// Dynamic shared memory: (W + 1) x nk words.
 __global__ void __launch_bounds__(256) k_bucket_sort(RunArgs a)
 {
+    extern __shared__ uint32_t dsm[];
+    __shared__ uint32_t part[256];
     const SortArgs &so = a.so;
     const int64_t b = blockIdx.x;
     const int w = (int)(b / so.nstripe);
@@ -245,58 +300,70 @@ __global__ void __launch_bounds__(256) k_bucket_sort(RunArgs a)
         for (uint32_t i = threadIdx.x; i < n; i += blockDim.x) so.perm[base + i] = (uint32_t)so.tmp[base + i];
         return;
     }
-    __shared__ uint32_t sh[MAX_LOCAL_KEYS];
-    __shared__ uint32_t part[256];
     const int nk = so.stripe_rows * so.nuk;
-    for (int i = threadIdx.x; i < nk; i += blockDim.x) sh[i] = 0;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    uint32_t *cnt = dsm + (size_t)warp * nk;        // this warp's counts, then its offsets
+    uint32_t *tot = dsm + (size_t)nwarps * nk;      // per key: all warps' counts, then the key's start
+    for (int i = threadIdx.x; i < (nwarps + 1) * nk; i += blockDim.x) dsm[i] = 0u;
     __syncthreads();
-    for (uint32_t i = threadIdx.x; i < n; i += blockDim.x) atomicAdd(&sh[(uint32_t)(so.tmp[base + i] >> 32)], 1u);
+    const uint32_t r0 = (uint32_t)((uint64_t)n * warp / nwarps), r1 = (uint32_t)((uint64_t)n * (warp + 1) / nwarps);
+    for (uint32_t c0 = r0; c0 < r1; c0 += 32) {
+        const uint32_t i = c0 + lane;
+        const uint32_t L = i < r1 ? (uint32_t)(so.tmp[base + i] >> 32) : NO_BUCKET;
+        const unsigned peers = __match_any_sync(0xffffffffu, L);
+        if (L != NO_BUCKET && lane == __ffs(peers) - 1) cnt[L] += (uint32_t)__popc(peers);
+    }
     __syncthreads();
-    // exclusive scan of sh[0, nk): contiguous slices per thread
+    // per key: exclusive prefix over the warps, and the key's total
+    for (int k = threadIdx.x; k < nk; k += blockDim.x) {
+        uint32_t run = 0;
+        for (int v = 0; v < nwarps; ++v) {
+            const uint32_t c = dsm[(size_t)v * nk + k];
+            dsm[(size_t)v * nk + k] = run;
+            run += c;
+        }
+        tot[k] = run;
+    }
+    __syncthreads();
+    // exclusive scan of the totals over the keys: contiguous slices per thread
     const int per = (nk + blockDim.x - 1) / blockDim.x;
     const int k0 = min(nk, (int)threadIdx.x * per), k1 = min(nk, k0 + per);
     uint32_t loc = 0;
-    for (int k = k0; k < k1; ++k) loc += sh[k];
+    for (int k = k0; k < k1; ++k) loc += tot[k];
     part[threadIdx.x] = loc;
     __syncthreads();
     for (int off = 1; off < (int)blockDim.x; off <<= 1) {
-        uint32_t v = threadIdx.x >= (unsigned)off ? part[threadIdx.x - off] : 0u;
+        const uint32_t v = threadIdx.x >= (unsigned)off ? part[threadIdx.x - off] : 0u;
         __syncthreads();
         part[threadIdx.x] += v;
         __syncthreads();
     }
     uint32_t run = part[threadIdx.x] - loc;
     for (int k = k0; k < k1; ++k) {
-        const uint32_t c = sh[k];
-        sh[k] = run;
+        const uint32_t c = tot[k];
+        tot[k] = run;
         run += c;
     }
     __syncthreads();
-    // Stable scatter: the bucket's rows arrive in row order (k_keys), and
-    // keep it within each local key, so that rows of one baseline stay
-    // consecutive in time and, at the window's other channels, a group's
-    // cell changes at most once instead of alternating.
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
-    for (uint32_t c0 = 0; c0 < n; c0 += blockDim.x) {
-        const uint32_t i = c0 + threadIdx.x;
-        const bool valid = i < n;
+    for (int k = threadIdx.x; k < nk; k += blockDim.x) {
+        const uint32_t st = tot[k];
+        for (int v = 0; v < nwarps; ++v) dsm[(size_t)v * nk + k] += st;
+    }
+    __syncthreads();
+    // each warp scatters its part in row order
+    for (uint32_t c0 = r0; c0 < r1; c0 += 32) {
+        const uint32_t i = c0 + lane;
+        const bool valid = i < r1;
         const unsigned long long t = valid ? so.tmp[base + i] : 0ull;
         const uint32_t L = valid ? (uint32_t)(t >> 32) : NO_BUCKET;
         const unsigned peers = __match_any_sync(0xffffffffu, L);
         const int leader = __ffs(peers) - 1;
-        const uint32_t rank = __popc(peers & ((1u << lane) - 1u));
-        uint32_t pos = 0;
-        for (int wi = 0; wi < nwarps; ++wi) {
-            if (warp == wi) {
-                uint32_t b0 = 0;
-                if (lane == leader && valid) {
-                    b0 = sh[L];
-                    sh[L] = b0 + (uint32_t)__popc(peers);
-                }
-                pos = __shfl_sync(peers, b0, leader) + rank;
-            }
-            __syncthreads();
+        uint32_t b0 = 0;
+        if (valid && lane == leader) {
+            b0 = cnt[L];
+            cnt[L] = b0 + (uint32_t)__popc(peers);
         }
+        const uint32_t pos = __shfl_sync(0xffffffffu, b0, leader) + (uint32_t)__popc(peers & ((1u << lane) - 1u));
         if (valid) so.perm[base + pos] = (uint32_t)t;
     }
 }
@@ -318,7 +385,45 @@ __device__ int axis_step(float c32, const ChanF *cf, const ChanD *cd, int e0, in
     return hi;
 }
 
-__global__ void __launch_bounds__(256) k_records(RunArgs a)
+// The chunk-cell entry of chunk c of one row (coordinates uf, vf after the
+// fold; uvw the row's FP64 coordinates for the exact fall-backs).  The cell
+// index is monotone in frequency along each axis, so the cells at a chunk's
+// two end channels bound every channel between.
+__device__ int2 chunk_cell(const RunArgs &a, const SrcDev &S, const ChanF *cf, const ChanD *cd, int c, float uf,
+                           float vf, const double *uvw, bool fold)
+{
+    const int nin = S.k_hi - S.k_lo;
+    const float hu = (float)(a.g.nu >> 1), hv = (float)(a.g.nv >> 1);
+    const int e0 = c * a.cw, last = min(nin, e0 + a.cw) - 1 - e0;
+    const float fu0 = axis_floor(uf, cf[e0].su, uvw, fold, &cd[e0].su);
+    const float fu1 = axis_floor(uf, cf[e0 + last].su, uvw, fold, &cd[e0 + last].su);
+    const float fv0 = axis_floor(vf, cf[e0].sv, uvw + 1, fold, &cd[e0].sv);
+    const float fv1 = axis_floor(vf, cf[e0 + last].sv, uvw + 1, fold, &cd[e0 + last].sv);
+    // both ends off the grid on the same side of one axis: off throughout
+    const bool offu = (fu0 < -hu && fu1 < -hu) || (fu0 >= hu && fu1 >= hu);
+    const bool offv = (fv0 < -hv && fv1 < -hv) || (fv0 >= hv && fv1 >= hv);
+    const bool in = fu0 >= -hu && fu0 < hu && fu1 >= -hu && fu1 < hu && fv0 >= -hv && fv0 < hv &&
+                    fv1 >= -hv && fv1 < hv;
+    if (offu || offv) return make_int2(-1, CC_NOCHANGE);
+    if (!in || fabsf(fu1 - fu0) > 1.0f || fabsf(fv1 - fv0) > 1.0f) return make_int2(-1, CC_MIXED);
+    uint32_t m = CC_NOCHANGE;
+    if (fu1 != fu0) {
+        const int b = axis_step(uf, cf, cd, e0, 0, last, uvw, fold, false, fu0);
+        m = (m & ~0xffu) | (uint32_t)b | (fu1 < fu0 ? 0x10000u : 0u);
+    }
+    if (fv1 != fv0) {
+        const int b = axis_step(vf, cf, cd, e0, 0, last, uvw + 1, fold, true, fv0);
+        m = (m & ~0xff00u) | ((uint32_t)b << 8) | (fv1 < fv0 ? 0x20000u : 0u);
+    }
+    return make_int2(((int)fv0 + (a.g.nv >> 1)) * a.g.nu + ((int)fu0 + (a.g.nu >> 1)), (int)m);
+}
+
+// One thread per row, in processing order: the row record (the FP64 delay
+// of Eq. 2 as a float-float pair, the fold-signed weights, the row index)
+// and the chunk-cell entries of all the window's chunks, laid out
+// [chunk][row] per window so that an item's entries are contiguous.  The
+// row's coordinates are read once for both.
+__global__ void __launch_bounds__(256) k_rows(RunArgs a)
 {
     const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= a.nrows_total) return;
@@ -340,79 +445,57 @@ __global__ void __launch_bounds__(256) k_records(RunArgs a)
         rec.W[k] = fold ? -wk : wk;
     }
     a.recs[S.rec_off + q] = rec;
-}
 
-// Chunk cells: one thread per (row, channel chunk) entry, laid out [chunk][row]
-// per window (rows in processing order).  The cell index is monotone in
-// frequency along each axis, so the cells at a chunk's two end channels
-// bound every channel between.
-__global__ void __launch_bounds__(256) k_cells(RunArgs a)
-{
-    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= a.ncells_total) return;
-    const int w = find_owner(a.cell_cum, a.nsrc, p);
-    const SrcDev &S = a.srcs[w];
-    const int64_t loc = p - a.cell_cum[w];
-    const int c = (int)(loc / S.nrow);
-    const int64_t q = loc - (int64_t)c * S.nrow;
-    const int64_t r = a.so.perm[a.row_off[w] + q];
-    const double *uvw = S.uvw + 3 * r;
-    const double u = uvw[0], v = uvw[1];
-    const bool fold = a.g.fold && (v < 0.0 || (v == 0.0 && u < 0.0));
     const float uf = (float)(fold ? -u : u), vf = (float)(fold ? -v : v);
     const ChanD *cd = a.chd + S.chan_off;
     const ChanF *cf = a.chf + S.chan_off;
-    const int nin = S.k_hi - S.k_lo;
-    const float hu = (float)(a.g.nu >> 1), hv = (float)(a.g.nv >> 1);
-    const int e0 = c * a.cw, last = min(nin, e0 + a.cw) - 1 - e0;
-    const float fu0 = axis_floor(uf, cf[e0].su, uvw, fold, &cd[e0].su);
-    const float fu1 = axis_floor(uf, cf[e0 + last].su, uvw, fold, &cd[e0 + last].su);
-    const float fv0 = axis_floor(vf, cf[e0].sv, uvw + 1, fold, &cd[e0].sv);
-    const float fv1 = axis_floor(vf, cf[e0 + last].sv, uvw + 1, fold, &cd[e0 + last].sv);
-    // both ends off the grid on the same side of one axis: off throughout
-    const bool offu = (fu0 < -hu && fu1 < -hu) || (fu0 >= hu && fu1 >= hu);
-    const bool offv = (fv0 < -hv && fv1 < -hv) || (fv0 >= hv && fv1 >= hv);
-    const bool in = fu0 >= -hu && fu0 < hu && fu1 >= -hu && fu1 < hu && fv0 >= -hv && fv0 < hv &&
-                    fv1 >= -hv && fv1 < hv;
-    int2 cc;
-    if (offu || offv) {
-        cc = make_int2(-1, CC_NOCHANGE);
-    } else if (!in || fabsf(fu1 - fu0) > 1.0f || fabsf(fv1 - fv0) > 1.0f) {
-        cc = make_int2(-1, CC_MIXED);
-    } else {
-        uint32_t m = CC_NOCHANGE;
-        if (fu1 != fu0) {
-            const int b = axis_step(uf, cf, cd, e0, 0, last, uvw, fold, false, fu0);
-            m = (m & ~0xffu) | (uint32_t)b | (fu1 < fu0 ? 0x10000u : 0u);
-        }
-        if (fv1 != fv0) {
-            const int b = axis_step(vf, cf, cd, e0, 0, last, uvw + 1, fold, true, fv0);
-            m = (m & ~0xff00u) | ((uint32_t)b << 8) | (fv1 < fv0 ? 0x20000u : 0u);
-        }
-        cc = make_int2(((int)fv0 + (a.g.nv >> 1)) * a.g.nu + ((int)fu0 + (a.g.nu >> 1)), (int)m);
-    }
-    a.ccells[S.cell_off + loc] = cc;
+    int2 *out = a.ccells + S.cell_off + q;
+    const int nchunk = S.nchunk;
+    for (int c = 0; c < nchunk; ++c) out[(int64_t)c * S.nrow] = chunk_cell(a, S, cf, cd, c, uf, vf, uvw, fold);
 }
 
-cudaError_t launch_prepare(const RunArgs &a, cudaStream_t st)
+cudaError_t launch_prepare(const RunArgs &a, cudaStream_t st, int *nlaunch)
 {
     const SortArgs &so = a.so;
+    int n = 0;
     cudaError_t e = cudaMemsetAsync(so.hist, 0, sizeof(uint32_t) * (size_t)a.nsrc * so.nstripe, st);
     if (e != cudaSuccess) return e;
     const unsigned rb = (unsigned)((a.nrows_total + 255) / 256);
     if (so.nseg_total > 0) {
         k_keys<<<(unsigned)so.nseg_total, 256, 0, st>>>(a);
         const int64_t nb = (int64_t)a.nsrc * so.nstripe;
-        k_segscan<<<(unsigned)((nb + 255) / 256), 256, 0, st>>>(a);
-        k_slots<<<(unsigned)so.nseg_total, 256, 0, st>>>(a);
+        k_segscan<<<(unsigned)((nb * 32 + 255) / 256), 256, 0, st>>>(a);
+        const int nws = table_warps(so.nstripe, 0);
+        const size_t smem_s = (size_t)nws * so.nstripe * sizeof(uint32_t);
+        const cudaError_t ea = allow_smem(k_slots, smem_s);
+        if (ea != cudaSuccess) return ea;
+        k_slots<<<(unsigned)so.nseg_total, 32 * nws, smem_s, st>>>(a);
+        n += 3;
     }
     k_scan<<<1, 1024, 0, st>>>(a);
-    if (so.max_items > 0) k_items<<<(unsigned)((so.max_items + 255) / 256), 256, 0, st>>>(a);
-    if (rb) k_scatter<<<rb, 256, 0, st>>>(a);
+    ++n;
+    if (so.max_items > 0) {
+        k_items<<<(unsigned)((so.max_items + 255) / 256), 256, 0, st>>>(a);
+        ++n;
+    }
+    if (rb) {
+        k_scatter<<<rb, 256, 0, st>>>(a);
+        ++n;
+    }
     const int64_t nbuckets = (int64_t)a.nsrc * so.nstripe;
-    if (rb && nbuckets) k_bucket_sort<<<(unsigned)nbuckets, 256, 0, st>>>(a);
-    if (rb) k_records<<<rb, 256, 0, st>>>(a);
-    if (a.ncells_total > 0) k_cells<<<(unsigned)((a.ncells_total + 255) / 256), 256, 0, st>>>(a);
+    if (rb && nbuckets) {
+        const int nk = so.stripe_rows * so.nuk, nw = table_warps(nk, 1);
+        const size_t smem = (size_t)(nw + 1) * nk * sizeof(uint32_t);
+        const cudaError_t ea = allow_smem(k_bucket_sort, smem);
+        if (ea != cudaSuccess) return ea;
+        k_bucket_sort<<<(unsigned)nbuckets, 32 * nw, smem, st>>>(a);
+        ++n;
+    }
+    if (rb) {
+        k_rows<<<rb, 256, 0, st>>>(a);
+        ++n;
+    }
+    if (nlaunch) *nlaunch = n;
     return cudaGetLastError();
 }
 

@@ -161,9 +161,10 @@ cudaError_t device_pass(vista_stack *h, cudaStream_t st)
             if (h->timing) h->tacc.launches += 1;
         } else {
             int sp = span_begin(h, 0);
-            e = launch_prepare(a, st);
+            int nk = 0;
+            e = launch_prepare(a, st, &nk);
             span_end(h, sp);
-            if (h->timing) h->tacc.launches += 9;
+            if (h->timing) h->tacc.launches += nk;
             if (e == cudaSuccess) {
                 sp = span_begin(h, 1);
                 e = launch_mixed(a, cr.key, cfg.warps_per_cta, cfg.prefetch_rows, st);
