@@ -378,6 +378,8 @@ def run_ours(args):
         # the whole stack is ~5e11 visibilities (aliased on the device): it has
         # no host-memory form to copy from
         e2e = {"skipped": "the batched stack exists only as views into a device pool"}
+    elif args.e2e_steps > 0 and wl.name.startswith("wideband_hi"):
+        e2e = {"skipped": "a pinned host copy of the 127 GB wideband inputs is not made"}
     elif args.e2e_steps > 0:
         try:
             e2e = run_e2e(args, wl, tuning, n_vis, ws)

@@ -113,6 +113,28 @@ uint64_t freq_digest(const double *f, size_t n)
     return d;
 }
 
+cudaError_t xfer_fork(vista_stack *h)
+{
+    cudaError_t e = cudaSuccess;
+    for (int j = 0; j < NXFER && e == cudaSuccess; ++j)
+        if (!h->xfer[j]) e = cudaStreamCreateWithFlags(&h->xfer[j], cudaStreamNonBlocking);
+    for (int j = 0; j <= NXFER && e == cudaSuccess; ++j)
+        if (!h->xfer_ev[j]) e = cudaEventCreateWithFlags(&h->xfer_ev[j], cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventRecord(h->xfer_ev[NXFER], h->stream);
+    for (int j = 0; j < NXFER && e == cudaSuccess; ++j) e = cudaStreamWaitEvent(h->xfer[j], h->xfer_ev[NXFER], 0);
+    return e;
+}
+
+cudaError_t xfer_join(vista_stack *h)
+{
+    cudaError_t e = cudaSuccess;
+    for (int j = 0; j < NXFER && e == cudaSuccess; ++j) {
+        e = cudaEventRecord(h->xfer_ev[j], h->xfer[j]);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(h->stream, h->xfer_ev[j], 0);
+    }
+    return e;
+}
+
 void drop_graph(vista_stack *h)
 {
     if (h->gexec) cudaGraphExecDestroy(h->gexec);
@@ -301,10 +323,13 @@ int read_common(vista_stack *h, void *sum_wv, void *sum_w, void *sum_wvv, uint32
     char *d_vv = sum_wvv ? p + b_wv + b_w : nullptr;
     uint32_t *d_c = count ? (uint32_t *)(p + b_wv + b_w + b_vv) : nullptr;
     e = launch_unpack(h->cube, h->cube_master, h->count, fp64, n, d_wv, d_w, d_vv, d_c, out_f64, h->stream);
-    if (e == cudaSuccess && sum_wv) e = cudaMemcpyAsync(sum_wv, d_wv, b_wv, cudaMemcpyDeviceToHost, h->stream);
-    if (e == cudaSuccess && sum_w) e = cudaMemcpyAsync(sum_w, d_w, b_w, cudaMemcpyDeviceToHost, h->stream);
-    if (e == cudaSuccess && sum_wvv) e = cudaMemcpyAsync(sum_wvv, d_vv, b_vv, cudaMemcpyDeviceToHost, h->stream);
-    if (e == cudaSuccess && count) e = cudaMemcpyAsync(count, d_c, b_c, cudaMemcpyDeviceToHost, h->stream);
+    // the four arrays go back on the copy streams, in parallel
+    if (e == cudaSuccess) e = xfer_fork(h);
+    if (e == cudaSuccess && sum_wv) e = cudaMemcpyAsync(sum_wv, d_wv, b_wv, cudaMemcpyDeviceToHost, h->xfer[0]);
+    if (e == cudaSuccess && sum_w) e = cudaMemcpyAsync(sum_w, d_w, b_w, cudaMemcpyDeviceToHost, h->xfer[1]);
+    if (e == cudaSuccess && sum_wvv) e = cudaMemcpyAsync(sum_wvv, d_vv, b_vv, cudaMemcpyDeviceToHost, h->xfer[2]);
+    if (e == cudaSuccess && count) e = cudaMemcpyAsync(count, d_c, b_c, cudaMemcpyDeviceToHost, h->xfer[3]);
+    if (e == cudaSuccess) e = xfer_join(h);
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
     if (e != cudaSuccess) return cuda_fail(h, e, "cube readback");
     return VISTA_OK;
@@ -480,6 +505,13 @@ extern "C" int vista_close(vista_stack *h)
     for (cudaEvent_t ev : h->ev_pool) cudaEventDestroy(ev);
     drop_graph(h);
     if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
+    for (int j = 0; j < NXFER; ++j)
+        if (h->xfer[j]) {
+            cudaStreamSynchronize(h->xfer[j]);
+            cudaStreamDestroy(h->xfer[j]);
+        }
+    for (int j = 0; j <= NXFER; ++j)
+        if (h->xfer_ev[j]) cudaEventDestroy(h->xfer_ev[j]);
     cudaFree(h->cube);
     cudaFree(h->cube_master);
     cudaFree(h->count);

@@ -90,6 +90,10 @@ struct vista_stack {
     std::vector<uint8_t> plan_sig;
     uint64_t plan_nvis = 0;
     cudaStream_t cap_stream = nullptr;   // capture stream (handle-owned)
+    // host<->device copies spread over several streams (copy engines run in
+    // parallel), forked from and joined back into `stream`
+    cudaStream_t xfer[4] = {};
+    cudaEvent_t xfer_ev[5] = {};
     cudaGraphExec_t gexec = nullptr;
     uint64_t graph_launches = 0;
     // stripe geometry of the row ordering (depends on the cube only)
@@ -111,5 +115,8 @@ void span_end(vista_stack *h, int id);
 size_t vis_elem_bytes(int vt);
 uint64_t freq_digest(const double *f, size_t n);   // change detection of a frequency axis
 void drop_graph(vista_stack *h);
+constexpr int NXFER = 4;
+cudaError_t xfer_fork(vista_stack *h);   // copy streams wait for the work queued on h->stream
+cudaError_t xfer_join(vista_stack *h);   // h->stream waits for the copies queued on them
 
 }  // namespace vista

@@ -355,6 +355,9 @@ extern "C" int vista_run(vista_stack *h)
     std::vector<Copy2D> copies;
     size_t stage_pos = 0;
     const int span_copy = stage_bytes ? span_begin(h, 2) : -1;
+    // host windows are copied on the copy streams, window j on stream j mod NXFER
+    int nhost = 0;
+    if (stage_bytes && (e = xfer_fork(h)) != cudaSuccess) return cuda_fail(h, e, "copy stream setup");
     for (size_t ci = 0; ci < classes.size(); ++ci) {
         ClassRun &cr = classes[ci];
         const int cw = 32 * cr.ns;
@@ -396,19 +399,22 @@ extern "C" int vista_run(vista_stack *h)
                 }
                 const size_t row_in = (size_t)s.d.nchan * P, row_out = (size_t)nin * P;
                 // whole rows go as one contiguous copy, partial rows as a 2-D copy
+                const cudaStream_t cs = h->xfer[nhost++ % NXFER];
                 auto copy_rows = [&](void *dst, size_t dpitch, const void *src, size_t spitch, size_t width) {
                     if (width == spitch && width == dpitch)
-                        return cudaMemcpyAsync(dst, src, width * nr, cudaMemcpyHostToDevice, h->stream);
-                    return cudaMemcpy2DAsync(dst, dpitch, src, spitch, width, nr, cudaMemcpyHostToDevice, h->stream);
+                        return cudaMemcpyAsync(dst, src, width * nr, cudaMemcpyHostToDevice, cs);
+                    return cudaMemcpy2DAsync(dst, dpitch, src, spitch, width, nr, cudaMemcpyHostToDevice, cs);
                 };
-                e = cudaMemcpyAsync(p_uvw, s.d.uvw, nr * 24, cudaMemcpyHostToDevice, h->stream);
+                e = cudaMemcpyAsync(p_uvw, s.d.uvw, nr * 24, cudaMemcpyHostToDevice, cs);
                 if (e == cudaSuccess)
                     e = copy_rows(p_vis, row_out * esz, (const char *)s.d.vis + (size_t)pl.k_lo * P * esz, row_in * esz,
                                   row_out * esz);
-                if (e == cudaSuccess)
-                    e = cudaMemcpyAsync(p_w, s.d.weights, nr * 4 * P, cudaMemcpyHostToDevice, h->stream);
+                if (e == cudaSuccess) e = cudaMemcpyAsync(p_w, s.d.weights, nr * 4 * P, cudaMemcpyHostToDevice, cs);
                 if (e == cudaSuccess && p_f) e = copy_rows(p_f, fp, s.d.flags + (size_t)pl.k_lo * P, row_in, row_out);
-                if (e != cudaSuccess) return cuda_fail(h, e, "host-to-device copy of a host-memory window");
+                if (e != cudaSuccess) {
+                    xfer_join(h);   // later work on the stream still waits for the copies issued
+                    return cuda_fail(h, e, "host-to-device copy of a host-memory window");
+                }
                 d.uvw = (const double *)p_uvw;
                 d.vis = p_vis;
                 d.wts = (const float *)p_w;
@@ -476,6 +482,7 @@ extern "C" int vista_run(vista_stack *h)
         cr.args.so.max_items = max_items;
         sort_bytes = std::max(sort_bytes, layouts[ci].total);
     }
+    if (stage_bytes && (e = xfer_join(h)) != cudaSuccess) return cuda_fail(h, e, "copy stream join");
     span_end(h, span_copy);
 
     // uploads and buffers
