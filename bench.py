@@ -1,8 +1,8 @@
 #!/usr/bin/env python
 """Stacked visibilities per second on GB300 (ViSta hot path, libvista).
 
-One step = one full stacking job: zero the cube, queue every (source, window)
-of the workload, vista_run.  The inputs (seeded synthetic ALMA-compact-like
+One step = one full stacking pass: queue every (source, window) of the
+workload, vista_run (the cube is zeroed once and accumulates across steps).  The inputs (seeded synthetic ALMA-compact-like
 stack: 64 sources x 2 windows x 120 channels x 2 pols, 43 antennas, 120
 integrations; cube 256 x 256 uv cells x 512 rest channels x 2 pols) are
 resident in HBM before the timed region; they total ~30 GB, far larger than
@@ -58,17 +58,27 @@ def parse():
 
 # ------------------------------------------------------------------ plumbing
 
-def dist_setup(args):
+def dist_setup(args, backend=None):
+    """One process per GPU (NCCL); without CUDA, or asked for (host-side
+    tests), gloo."""
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     if ws > 1:
         import torch.distributed as dist
-        torch.cuda.set_device(local)
-        dist.init_process_group("nccl")
+        backend = backend or ("nccl" if torch.cuda.is_available() else "gloo")
+        if backend == "nccl":
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend)
     elif torch.cuda.is_available():
         torch.cuda.set_device(0)
     return ws, rank, local
+
+
+def shard_ids(n, rank):
+    """Source ids of one rank: every rank stacks its own n sources (replicas,
+    disjoint seeds, no exchange on the data path)."""
+    return range(rank * n, rank * n + n)
 
 
 def barrier(ws):
@@ -77,13 +87,26 @@ def barrier(ws):
         dist.barrier()
 
 
+def _reduce(ws, x, op):
+    import torch.distributed as dist
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=op)
+    return float(t.item())
+
+
 def allmax(ws, x):
     if ws == 1:
         return x
     import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
-    dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    return float(t.item())
+    return _reduce(ws, x, dist.ReduceOp.MAX)
+
+
+def allsum(ws, x):
+    if ws == 1:
+        return x
+    import torch.distributed as dist
+    return _reduce(ws, x, dist.ReduceOp.SUM)
 
 
 class Clocks:
@@ -186,18 +209,18 @@ def make_workload(args, rank, device):
         # the sources of a 64-source set whose windows reach the cube, on the
         # lattice and cell size of the whole set (the rest never add a visibility)
         n = args.sources or 64
-        meta = synth.mixed("cpu", n_sources=n, src_ids=range(rank * n, rank * n + n), meta_only=True)
+        meta = synth.mixed("cpu", n_sources=n, src_ids=shard_ids(n, rank), meta_only=True)
         f0, df, ids = in_cube_sources(meta, meta.nrest)
         wl = synth.mixed(device, src_ids=ids, du=meta.du)
         wl.rest_f0, wl.rest_df = f0, df
     elif args.config == "wideband_hi":
         # the complex-half variant holds 48 sources (drawn directly as 16-bit pairs)
         n = args.sources or (24 if args.storage == "c64" else 48)
-        ids = range(rank * n, rank * n + n)
+        ids = shard_ids(n, rank)
         return synth.wideband_hi(device, n_sources=n, src_ids=ids, storage=args.storage)
     else:
         n = args.sources or {"alma_compact": 64, "batched": 2000}[args.config]
-        ids = range(rank * n, rank * n + n)
+        ids = shard_ids(n, rank)
         if args.config == "alma_compact":
             wl = synth.alma_compact(device, n_sources=n, src_ids=ids)
         else:
@@ -355,7 +378,8 @@ def run_ours(args):
     clocks = clk.stop()
     red_per_vis = stats["n_reductions"] / max(1, n_vis)   # of the first run
     ms_max = allmax(ws, ms)
-    value = n_vis * ws / (ms_max * 1e-3)
+    n_vis_all = allsum(ws, n_vis)   # every rank's visibilities (the ranks' source sets differ)
+    value = n_vis_all / (ms_max * 1e-3)
     stack_ms = tm["stack_ms"]
     peak, peak_kind = measured_peaks()
     achieved = alg / (stack_ms * 1e-3) / 1e9 if stack_ms > 0 else 0.0
@@ -369,7 +393,7 @@ def run_ours(args):
         ms64, _, _ = timed_steps(st64, wl, args.fp64_steps, 1, ws, split_steps=1)
         st64.close()
         ms64 = allmax(ws, ms64)
-        fp64 = {"value": n_vis * ws / (ms64 * 1e-3), "unit": UNIT, "ms_per_step": ms64,
+        fp64 = {"value": n_vis_all / (ms64 * 1e-3), "unit": UNIT, "ms_per_step": ms64,
                 "speedup_mixed_vs_fp64": ms64 / ms_max}
 
     # end to end through the C ABI with host buffers
@@ -470,7 +494,7 @@ def run_e2e(args, wl, tuning, n_vis, ws):
     d2h = sum(v.numel() * v.element_size() for v in outs.values())
     ste.close()
     dt = allmax(ws, dt)
-    return {"value": n_vis * ws / dt, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+    return {"value": allsum(ws, n_vis) / dt, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
             "d2h_bytes_per_step": int(d2h), "ms_per_step": dt * 1e3}
 
 

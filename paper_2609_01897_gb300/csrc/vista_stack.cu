@@ -31,7 +31,7 @@ constexpr int RB_MAX = 256;         // largest item (rows) the shared-memory buf
 constexpr int KMAX_THREADS = 256;   // blocks of at most 8 warps
 constexpr int STAGE_CAP = 64;       // staged runs per warp (circular; a power of two)
 constexpr uint32_t CKPT_EVERY = 8;     // valid runs of a lane between checkpoint choices (a power of two)
-constexpr uint32_t SERVICE_EVERY = 4;  // 1 / probability that a drain exchanges the chosen entries (a power of two)
+constexpr uint32_t SERVICE_EVERY = 8;  // 1 / probability that a drain exchanges the chosen entries (a power of two)
 constexpr int NO_RUN = INT_MIN;     // lane holds no run
 
 // What a window without flags reads as its flags (every row: pitch 0).

@@ -12,7 +12,8 @@ workloads:
 * wideband HI (4096 channels over 856-1712 MHz, cube 512 x 512 x 2048 x 2):
   8 of the 24 sources (lattice and cell size of all 24), the mixed path
   against the plain FP64 GPU path on every cube entry, and the FP64 oracle
-  on sampled planes."""
+  on sampled planes; and the same for the complex-half variant (48 sources
+  stored as FP16 pairs)."""
 import json
 
 import numpy as np
@@ -127,3 +128,68 @@ def test_wideband_hi(V):
     assert o["count"].sum() > 1e5
     errs = H.compare(g, o, H.TOL_MIXED, what="wideband HI sampled planes")
     print("wideband HI, sampled planes, worst errors:", json.dumps(errs))
+
+
+def test_wideband_hi_half_storage(V):
+    """The complex-half wideband stack (48 sources stored as FP16 pairs): 8 of
+    its sources on the lattice and cell size of all 48, the mixed path
+    against the plain FP64 GPU path reading the same stored values on every
+    cube entry, and the FP64 oracle on the dequantised values on a sampled
+    plane."""
+    from paper_2609_01897_gb300 import synth
+    meta = synth.wideband_hi("cpu", n_sources=48, meta_only=True)
+    f0, df, _ = _lattice_and_ids(meta, V)
+    wl = synth.wideband_hi("cuda", n_sources=48, src_ids=range(8), du=meta.du, storage="f16")
+    assert all(s.vis.dtype == torch.float16 for s in wl.spws)
+    cubes, stats = {}, {}
+    for prec in (V.PREC_MIXED, V.PREC_FP64):
+        st = V.Stack(wl.nu, wl.nv, wl.nrest, wl.npol, wl.du, wl.dv, rest_f0=f0, rest_df=df, precision=prec)
+        try:
+            for s in wl.spws:
+                st.add_source(s.uvw, s.freqs, s.vis, s.weights, s.flags, l=s.l, m=s.m, z=s.z,
+                              vis_scale=s.vis_scale)
+            st.run()
+            cubes[prec] = st.read_cube(device=True, f64=True)
+            stats[prec] = st.stats()
+        finally:
+            st.close()
+    m, d = cubes[V.PREC_MIXED], cubes[V.PREC_FP64]
+    assert torch.equal(m["count"], d["count"])
+    assert int(d["count"].sum()) > 1e9
+    worst = {}
+    for key in ("sum_w", "sum_wvv"):
+        err = (m[key] - d[key]).abs()
+        assert bool((err <= H.TOL_MIXED * d[key].abs() + 1e-300).all()), key
+        worst[key] = float((err / d[key].abs().clamp_min(1e-300)).max())
+    scale = torch.sqrt(d["sum_w"] * d["sum_wvv"])
+    err = (m["sum_wv"] - d["sum_wv"]).abs().amax(dim=-1)
+    assert bool((err <= H.TOL_MIXED * scale + 1e-300).all()), "sum_wv"
+    worst["sum_wv"] = float((err / scale.clamp_min(1e-300)).max())
+    for k in ("n_vis", "n_flagged", "n_dropped_uv", "n_stacked"):
+        assert int(stats[V.PREC_MIXED][k]) == int(stats[V.PREC_FP64][k]), k
+    print("wideband HI, FP16 storage, mixed vs FP64 GPU path, worst errors:", json.dumps(worst))
+
+    # the oracle on the dequantised values of the first source, one plane
+    plane = 256
+    sel = torch.tensor([plane], device="cuda")
+    del cubes, m, d, scale, err
+    torch.cuda.empty_cache()
+    sub = synth.Workload("hi-f16-1", wl.nu, wl.nv, wl.nrest, wl.npol, wl.du, wl.dv, wl.central_freq,
+                         wl.spws[:1], rest_df=df, rest_f0=f0)
+    st = V.Stack(sub.nu, sub.nv, sub.nrest, sub.npol, sub.du, sub.dv, rest_f0=f0, rest_df=df)
+    try:
+        s = sub.spws[0]
+        st.add_source(s.uvw, s.freqs, s.vis, s.weights, s.flags, l=s.l, m=s.m, z=s.z, vis_scale=s.vis_scale)
+        st.run()
+        c = st.read_cube(device=True, f64=True)
+        g = {k: v.index_select(0, sel).cpu().numpy() for k, v in c.items()}
+        g["sum_wv"] = g["sum_wv"][..., 0] + 1j * g["sum_wv"][..., 1]
+        del c
+    finally:
+        st.close()
+    s = sub.spws[0]
+    deq = {id(s): torch.view_as_complex(s.vis.to(torch.float64).mul_(s.vis_scale)).cpu().numpy()}
+    o = H.run_oracle(sub, iv_select=[plane], dequant=deq, nthreads=16)
+    assert o["count"].sum() > 1e4
+    errs = H.compare(g, o, H.TOL_MIXED, what="wideband HI FP16, sampled plane")
+    print("wideband HI, FP16 storage, sampled plane vs the oracle:", json.dumps(errs))
