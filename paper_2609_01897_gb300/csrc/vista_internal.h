@@ -205,8 +205,6 @@ struct RunArgs {
     RowRec *recs;
     int2 *ccells;               // chunk cells (+ 4 entries of padding for the bulk copies)
     const int64_t *row_off;     // [nsrc+1] cumulative rows
-    const int64_t *cell_cum;    // [nsrc+1] cumulative (row, chunk) entries (mixed path)
-    int64_t ncells_total;
     int64_t nrows_total;
     CubeGeom g;
     void *cube;                 // per entry: FP64 double[4], or float4 (mixed)

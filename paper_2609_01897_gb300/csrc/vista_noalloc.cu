@@ -163,7 +163,7 @@ extern "C" int vista_stack_noalloc(const vista_cube_desc *c, const vista_source_
     const size_t o_src = o;
     o += al256(sizeof(SrcDev));
     const size_t o_off = o;
-    o += al256(6 * sizeof(int64_t));
+    o += al256(4 * sizeof(int64_t));
     const size_t o_chf = o;
     o += al256(sizeof(ChanF) * (size_t)nin);
     const size_t o_chd = o;
@@ -241,8 +241,8 @@ extern "C" int vista_stack_noalloc(const vista_cube_desc *c, const vista_source_
     d.rec_off = 0;
     d.cell_off = 0;
     const int64_t nseg = (nrow + SEG_ROWS - 1) / SEG_ROWS;
-    // rows, (row, chunk) entries, row segments
-    const int64_t roff[6] = {0, nrow, 0, nrow * nchunk, 0, nseg};
+    // rows, row segments
+    const int64_t roff[4] = {0, nrow, 0, nseg};
 
     // tables into scratch; counters and the error word start at zero
     e = cudaMemcpyAsync(b + o_src, &d, sizeof d, cudaMemcpyHostToDevice, st);
@@ -265,10 +265,8 @@ extern "C" int vista_stack_noalloc(const vista_cube_desc *c, const vista_source_
     a.recs = (RowRec *)(b + o_rec);
     a.ccells = (int2 *)(b + o_cells);
     a.row_off = (const int64_t *)(b + o_off);
-    a.cell_cum = a.row_off + 2;
-    a.so.seg_off = a.row_off + 4;
+    a.so.seg_off = a.row_off + 2;
     a.so.nseg_total = nseg;
-    a.ncells_total = nrow * nchunk;
     a.nrows_total = nrow;
     a.g = CubeGeom{c->nu, c->nv, c->nrest, c->npol, gu, gv, c->hermitian_fold, 0};
     a.cube = cube4;

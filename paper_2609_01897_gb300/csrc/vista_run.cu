@@ -364,7 +364,7 @@ extern "C" int vista_run(vista_stack *h)
         cls_src0[ci] = sdev.size();
         cls_off0[ci] = offs.size();
         const size_t m = cr.members.size();
-        std::vector<int64_t> roff(m + 1, 0), croff(m + 1, 0), soff(m + 1, 0);
+        std::vector<int64_t> roff(m + 1, 0), soff(m + 1, 0);
         int64_t max_items = 0;
         for (size_t t = 0; t < m; ++t) {
             const int i = cr.members[t];
@@ -464,15 +464,12 @@ extern "C" int vista_run(vista_stack *h)
                 nvis_run += (uint64_t)(d.nrow * nread * npm);
             }
             roff[t + 1] = roff[t] + d.nrow;
-            croff[t + 1] = croff[t] + (fp64 ? 0 : d.nrow * d.nchunk);
             soff[t + 1] = soff[t] + (fp64 ? 0 : (d.nrow + SEG_ROWS - 1) / SEG_ROWS);
             max_items += (int64_t)d.nchunk * ((d.nrow + cfg.rows_per_item - 1) / cfg.rows_per_item + h->nstripe);
             sdev.push_back(d);
         }
         offs.insert(offs.end(), roff.begin(), roff.end());
-        offs.insert(offs.end(), croff.begin(), croff.end());
         offs.insert(offs.end(), soff.begin(), soff.end());
-        cr.args.ncells_total = croff[m];
         cr.args.so.nseg_total = soff[m];
         cr.args.nsrc = (int32_t)m;
         cr.args.cw = cw;
@@ -512,8 +509,7 @@ extern "C" int vista_run(vista_stack *h)
         a.recs = (RowRec *)h->b_recs.p;
         a.ccells = (int2 *)h->b_cells.p;
         a.row_off = (const int64_t *)h->b_off.p + cls_off0[ci];
-        a.cell_cum = a.row_off + cr.members.size() + 1;
-        a.so.seg_off = a.cell_cum + cr.members.size() + 1;
+        a.so.seg_off = a.row_off + cr.members.size() + 1;
         a.g = g;
         a.cube = h->cube;
         a.cube_master = h->cube_master;
