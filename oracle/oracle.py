@@ -26,7 +26,9 @@ class OrSource(C.Structure):
                 ("uvw", C.c_void_p), ("freqs", C.c_void_p), ("vis", C.c_void_p),
                 ("vis_f64", C.c_int32), ("pad0", C.c_int32),
                 ("weights", C.c_void_p), ("flags", C.c_void_p), ("pol_map", C.c_void_p),
-                ("l", C.c_double), ("m", C.c_double), ("z", C.c_double)]
+                ("l", C.c_double), ("m", C.c_double), ("z", C.c_double),
+                ("reproject", C.c_int32), ("pad1", C.c_int32),
+                ("ra0", C.c_double), ("dec0", C.c_double), ("ra1", C.c_double), ("dec1", C.c_double)]
 
 
 class OrStats(C.Structure):
@@ -49,6 +51,10 @@ def lib():
                                       C.c_double, C.POINTER(C.c_double), C.POINTER(C.c_double)]
         L.or_rest_weights.argtypes = [C.c_void_p, C.c_int32, C.c_double, C.c_double, C.c_double,
                                       C.c_int32, C.c_int32, C.c_void_p]
+        L.or_rotation.argtypes = [C.c_double, C.c_double, C.c_double, C.c_double, C.c_void_p]
+        L.or_rotation.restype = None
+        L.or_offset.argtypes = [C.c_double, C.c_double, C.c_double, C.c_double, C.c_void_p]
+        L.or_offset.restype = None
         L.or_phasors.argtypes = [C.POINTER(OrSource), C.c_void_p]
         L.or_phasors.restype = None
         L.or_cells.argtypes = [C.POINTER(OrCube), C.POINTER(OrSource), C.c_void_p]
@@ -96,9 +102,12 @@ def rest_weights(freqs, z, f0, df, nrest, bin_mode=0):
 
 class Source:
     """Host arrays of one (source, spectral window).  vis: complex64 or
-    complex128 [nrow, nchan, npol]; the arrays are kept alive here."""
+    complex128 [nrow, nchan, npol]; the arrays are kept alive here.
+    radec = (ra0, dec0, ra1, dec1), radians: re-project from the phase centre
+    (ra0, dec0) to the stacking position (ra1, dec1) (Eq. 1); l, m are then
+    ignored."""
 
-    def __init__(self, uvw, freqs, vis, weights, flags, l, m, z, pol_map=None):
+    def __init__(self, uvw, freqs, vis, weights, flags, l, m, z, pol_map=None, radec=None):
         self.uvw = np.ascontiguousarray(uvw, dtype=np.float64)
         self.freqs = np.ascontiguousarray(freqs, dtype=np.float64)
         vis = np.asarray(vis)
@@ -116,7 +125,22 @@ class Source:
         assert self.weights.shape == (nrow, npol)
         self.c = OrSource(nrow, nchan, npol, _ptr(self.uvw), _ptr(self.freqs), _ptr(self.vis),
                           f64, 0, _ptr(self.weights), _ptr(self.flags), _ptr(self.pol_map),
-                          float(l), float(m), float(z))
+                          float(l), float(m), float(z), 0 if radec is None else 1, 0,
+                          *((0.0, 0.0, 0.0, 0.0) if radec is None else tuple(float(x) for x in radec)))
+
+
+def rotation(ra0, dec0, ra1, dec1):
+    """Eq. 1's rotation R = M(ra1, dec1) M(ra0, dec0)^T as a 3 x 3 array."""
+    R = np.empty(9, dtype=np.float64)
+    lib().or_rotation(ra0, dec0, ra1, dec1, _ptr(R))
+    return R.reshape(3, 3)
+
+
+def offset(ra0, dec0, ra1, dec1):
+    """Direction cosines (l, m) of (ra1, dec1) seen from (ra0, dec0)."""
+    lm = np.empty(2, dtype=np.float64)
+    lib().or_offset(ra0, dec0, ra1, dec1, _ptr(lm))
+    return float(lm[0]), float(lm[1])
 
 
 def make_cube(nu, nv, nrest, npol, du, dv, rest_f0, rest_df, bin_mode=0, hermitian_fold=0):

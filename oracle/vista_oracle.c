@@ -13,11 +13,15 @@
  *
  * What it computes (one pass over every source, row, channel, polarisation):
  *
- *   tau   = u*l + v*m + w*(sqrt(1 - l^2 - m^2) - 1)                [Eq. 2, R = I]
+ *   tau   = u*l + v*m + w*(sqrt(1 - l^2 - m^2) - 1)                [Eq. 2]
  *   V'    = V * exp(+2 pi i frac(tau*nu_k/c))                      [Eq. 2, sign read
  *           so that a point source at (l, m) becomes real, see the point-source pin]
  *   cell  = floor(u * s_k) + nu/2, s_k = nu_k * (1/(c*du))         [uv in wavelengths,
  *           u_obs*nu_obs/c = u_rf*nu_rest/c, the z-invariant form of Eq. 1]
+ *   re-projected sources (Eq. 1 with a rotation): (l, m) are the direction
+ *           cosines of the stacking position (ra1, dec1) seen from the phase
+ *           centre (ra0, dec0), and the cell uses (u', v') = the first two
+ *           rows of R (u, v, w), R = M(ra1, dec1) M(ra0, dec0)^T
  *   w_kj  = overlap of the input channel's rest-frame edges with output bin j,
  *           divided by the input channel's rest-frame width           [Eqs. 3-4]
  *   cube[iv][iu][j][plane] += (W w_kj V', W w_kj, W w_kj |V|^2, 1)
@@ -56,6 +60,10 @@ typedef struct {
     const uint8_t *flags;   /* [nrow][nchan][npol], nonzero = flagged, may be NULL */
     const int32_t *pol_map; /* [npol] -> cube plane or -1, may be NULL (identity) */
     double l, m, z;
+    int32_t reproject;      /* 1: re-project (Eq. 1 rotation); l, m are then ignored */
+    int32_t pad1;
+    double ra0, dec0;       /* phase centre, radians */
+    double ra1, dec1;       /* stacking position, radians */
 } or_source;
 
 typedef struct {
@@ -207,6 +215,78 @@ static double delay_m(const double *uvw, double l, double m)
     return uvw[0] * l + uvw[1] * m + uvw[2] * n1;
 }
 
+/* Eq. 1's frames: the rows of M(ra, dec) are the unit vectors u (east),
+ * v (north) and w (toward (ra, dec)) in equatorial coordinates (x toward
+ * ra = 0 on the equator, z toward the north pole). */
+static void uvw_frame(double ra, double dec, double M[3][3])
+{
+    M[0][0] = -sin(ra);
+    M[0][1] = cos(ra);
+    M[0][2] = 0.0;
+    M[1][0] = -sin(dec) * cos(ra);
+    M[1][1] = -sin(dec) * sin(ra);
+    M[1][2] = cos(dec);
+    M[2][0] = cos(dec) * cos(ra);
+    M[2][1] = cos(dec) * sin(ra);
+    M[2][2] = sin(dec);
+}
+
+/* R = M(ra1, dec1) M(ra0, dec0)^T, row-major: a baseline's (u, v, w) for phase
+ * centre 0 expressed for phase centre 1 (the rotation of Eq. 1). */
+void or_rotation(double ra0, double dec0, double ra1, double dec1, double *R)
+{
+    double M0[3][3], M1[3][3];
+    uvw_frame(ra0, dec0, M0);
+    uvw_frame(ra1, dec1, M1);
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j)
+            R[3 * i + j] = M1[i][0] * M0[j][0] + M1[i][1] * M0[j][1] + M1[i][2] * M0[j][2];
+}
+
+/* Direction cosines (l, m) of (ra1, dec1) seen from the phase centre
+ * (ra0, dec0): the usual spherical offsets. */
+void or_offset(double ra0, double dec0, double ra1, double dec1, double *lm)
+{
+    double da = ra1 - ra0;
+    lm[0] = cos(dec1) * sin(da);
+    lm[1] = sin(dec1) * cos(dec0) - cos(dec1) * sin(dec0) * cos(da);
+}
+
+/* Per-source geometry: the shift's (l, m) and, for a re-projected source,
+ * the rotation applied to the baselines before the uv cell. */
+typedef struct {
+    double l, m;
+    int rot;
+    double R[9];
+} src_geom;
+
+static void source_geom(const or_source *s, src_geom *g)
+{
+    g->l = s->l;
+    g->m = s->m;
+    g->rot = s->reproject != 0;
+    if (g->rot) {
+        double lm[2];
+        or_offset(s->ra0, s->dec0, s->ra1, s->dec1, lm);
+        g->l = lm[0];
+        g->m = lm[1];
+        or_rotation(s->ra0, s->dec0, s->ra1, s->dec1, g->R);
+    }
+}
+
+/* The (u, v) a row is gridded with: the stored ones, or the first two rows of
+ * R (u, v, w) for a re-projected source. */
+static void cell_uv(const src_geom *g, const double *uvw, double *u, double *v)
+{
+    if (g->rot) {
+        *u = g->R[0] * uvw[0] + g->R[1] * uvw[1] + g->R[2] * uvw[2];
+        *v = g->R[3] * uvw[0] + g->R[4] * uvw[1] + g->R[5] * uvw[2];
+    } else {
+        *u = uvw[0];
+        *v = uvw[1];
+    }
+}
+
 /* Phase turns of the shift for frequency nu, reduced to [0, 1). */
 static double shift_turns(double tau, double nu)
 {
@@ -227,8 +307,10 @@ static int32_t uv_cell(double coord, double s_k, int32_t n)
 /* Phasors exp(+2 pi i frac(tau nu_k / c)) of one source, out[r][k][2]. */
 void or_phasors(const or_source *s, double *out)
 {
+    src_geom g;
+    source_geom(s, &g);
     for (int64_t r = 0; r < s->nrow; ++r) {
-        double tau = delay_m(s->uvw + 3 * r, s->l, s->m);
+        double tau = delay_m(s->uvw + 3 * r, g.l, g.m);
         for (int32_t k = 0; k < s->nchan; ++k) {
             double ph = 2.0 * M_PI * shift_turns(tau, s->freqs[k]);
             out[2 * (r * s->nchan + k)] = cos(ph);
@@ -242,8 +324,11 @@ void or_phasors(const or_source *s, double *out)
 void or_cells(const or_cube *c, const or_source *s, int32_t *out)
 {
     double gu = 1.0 / (OR_C_LIGHT * c->du), gv = 1.0 / (OR_C_LIGHT * c->dv);
+    src_geom g;
+    source_geom(s, &g);
     for (int64_t r = 0; r < s->nrow; ++r) {
-        double u = s->uvw[3 * r], v = s->uvw[3 * r + 1];
+        double u, v;
+        cell_uv(&g, s->uvw + 3 * r, &u, &v);
         if (c->hermitian_fold && (v < 0.0 || (v == 0.0 && u < 0.0))) { u = -u; v = -v; }
         for (int32_t k = 0; k < s->nchan; ++k) {
             int32_t iu = uv_cell(u, s->freqs[k] * gu, c->nu);
@@ -290,11 +375,14 @@ static void *stack_worker(void *arg)
         const chan_tab *tab = jb->tabs[si];
         const float *vf = (const float *)s->vis;
         const double *vd = (const double *)s->vis;
+        src_geom g;
+        source_geom(s, &g);
         for (int64_t r = 0; r < s->nrow; ++r) {
-            double u = s->uvw[3 * r], v = s->uvw[3 * r + 1];
+            double u, v;
+            cell_uv(&g, s->uvw + 3 * r, &u, &v);
             int fold = c->hermitian_fold && (v < 0.0 || (v == 0.0 && u < 0.0));
             if (fold) { u = -u; v = -v; }
-            double tau = delay_m(s->uvw + 3 * r, s->l, s->m);
+            double tau = delay_m(s->uvw + 3 * r, g.l, g.m);
             for (int32_t k = 0; k < s->nchan; ++k) {
                 const chan_tab *ct = &tab[k];
                 int32_t iu = uv_cell(u, s->freqs[k] * gu, c->nu);

@@ -403,3 +403,115 @@ def test_p8_all_flagged(oracle_mod):
     assert not out["sum_w"].any() and not out["count"].any() and not out["sum_wv"].any()
     assert out["stats"]["n_flagged"] == out["stats"]["n_vis"] > 0
     assert out["stats"]["n_stacked"] == 0
+
+
+# ----------------------------------------------------------------- Eq. 1 re-projection
+
+def _frame(ra, dec):
+    """The uvw frame of a phase centre built without the oracle's closed form:
+    w = the unit vector toward (ra, dec), u = the normalised cross product of
+    the pole with w (east), v = w x u (north)."""
+    w = np.array([math.cos(dec) * math.cos(ra), math.cos(dec) * math.sin(ra), math.sin(dec)])
+    e = np.cross(np.array([0.0, 0.0, 1.0]), w)
+    u = e / np.linalg.norm(e)
+    v = np.cross(w, u)
+    return np.stack([u, v, w])
+
+
+def _centres(rng, n, spread):
+    out = []
+    for _ in range(n):
+        ra0, dec0 = rng.uniform(0, 2 * math.pi), rng.uniform(-1.3, 1.3)
+        out.append((ra0, dec0, ra0 + rng.uniform(-spread, spread), dec0 + rng.uniform(-spread, spread)))
+    return out
+
+
+def test_reprojection_rotation_against_numeric_frames(oracle_mod):
+    """R = M(ra1, dec1) M(ra0, dec0)^T against frames built from cross
+    products of unit vectors: orthonormal, det +1, the same matrix."""
+    rng = np.random.default_rng(40)
+    for ra0, dec0, ra1, dec1 in _centres(rng, 20, 0.3):
+        R = oracle_mod.rotation(ra0, dec0, ra1, dec1)
+        ref = _frame(ra1, dec1) @ _frame(ra0, dec0).T
+        np.testing.assert_allclose(R, ref, atol=1e-14)
+        np.testing.assert_allclose(R @ R.T, np.eye(3), atol=1e-14)
+        assert abs(np.linalg.det(R) - 1.0) < 1e-14
+
+
+def test_reprojection_offset_is_the_rotated_w_axis(oracle_mod):
+    """(l, m) of the stacking position and R's last row are the same vector
+    (two derivations), with n = sqrt(1 - l^2 - m^2): so w' - w is the delay
+    of Eq. 2."""
+    rng = np.random.default_rng(41)
+    for ra0, dec0, ra1, dec1 in _centres(rng, 50, 0.05):
+        l, m = oracle_mod.offset(ra0, dec0, ra1, dec1)
+        R = oracle_mod.rotation(ra0, dec0, ra1, dec1)
+        assert abs(R[2, 0] - l) < 1e-15 and abs(R[2, 1] - m) < 1e-15
+        assert abs(R[2, 2] - math.sqrt(1 - l * l - m * m)) < 1e-14
+        # the same offsets from the numerical frames
+        s1 = _frame(ra1, dec1)[2]
+        F0 = _frame(ra0, dec0)
+        assert abs(F0[0] @ s1 - l) < 1e-14 and abs(F0[1] @ s1 - m) < 1e-14
+
+
+def test_reprojection_same_centre_is_identity(oracle_mod):
+    rng = np.random.default_rng(42)
+    for ra0, dec0, _, _ in _centres(rng, 10, 0.0):
+        assert oracle_mod.offset(ra0, dec0, ra0, dec0) == (0.0, 0.0)
+        np.testing.assert_allclose(oracle_mod.rotation(ra0, dec0, ra0, dec0), np.eye(3), atol=1e-15)
+
+
+def test_reprojected_point_source_is_real(oracle_mod):
+    """A point source at (ra1, dec1) observed with phase centre (ra0, dec0)
+    (visibilities from the numerically built frames) stacks to S + 0i when the
+    oracle re-projects to (ra1, dec1)."""
+    rng = np.random.default_rng(43)
+    ra0, dec0 = 1.1, -0.5
+    ra1, dec1 = ra0 + 40 * ARCSEC / math.cos(dec0), dec0 - 25 * ARCSEC
+    s1 = _frame(ra1, dec1)[2]
+    F0 = _frame(ra0, dec0)
+    l0, m0 = float(F0[0] @ s1), float(F0[1] @ s1)
+    uvw = _uvw(30, rng, 6000.0)
+    freqs = 345e9 + 7.8125e6 * np.arange(12)
+    S = 2e-3
+    vis = _point_vis(uvw, freqs, l0, m0, S, 2)
+    src = oracle_mod.Source(uvw, freqs, vis, np.ones((30, 2), np.float32), None, 0.0, 0.0, 2.0,
+                            radec=(ra0, dec0, ra1, dec1))
+    f0, df = oracle_mod.auto_lattice([freqs], [2.0], 64, 345e9 * 3.0)
+    du = 2 * 1.01 * np.abs(uvw[:, :2]).max() * freqs.max() / C / 32
+    cube = oracle_mod.make_cube(32, 32, 64, 2, du, du, f0, df, 0, 0)
+    out = oracle_mod.stack(cube, [src])
+    sel = out["sum_w"] > 0
+    assert sel.sum() > 50
+    np.testing.assert_allclose((out["sum_wv"][sel] / out["sum_w"][sel]).real, S, rtol=1e-8)
+    np.testing.assert_allclose((out["sum_wv"][sel] / out["sum_w"][sel]).imag, 0, atol=1e-8 * S)
+
+
+def test_reprojected_cells_use_the_rotated_baseline(oracle_mod):
+    """The uv cell of a re-projected row is floor(u' nu/(c du)) + N/2 with
+    (u', v') the baseline in the new frame, computed here from the numerical
+    frames (rows away from a cell edge)."""
+    rng = np.random.default_rng(44)
+    ra0, dec0, ra1, dec1 = 0.3, 0.4, 0.3 + 0.02, 0.4 - 0.015
+    uvw = _uvw(60, rng, 900.0)
+    freqs = 230e9 + 15.625e6 * np.arange(5)
+    du, N = 17000.0, 64
+    cube = oracle_mod.make_cube(N, N, 8, 1, du, du, 1e9, 1e9, 0, 0)
+    src = oracle_mod.Source(uvw, freqs, np.ones((60, 5, 1)), np.ones((60, 1), np.float32), None, 0.0, 0.0, 0.0,
+                            radec=(ra0, dec0, ra1, dec1))
+    cl = oracle_mod.cells(cube, src)
+    R = _frame(ra1, dec1) @ _frame(ra0, dec0).T
+    rot = uvw @ R.T
+    moved = checked = 0
+    for r in range(60):
+        for k in range(5):
+            xs = [rot[r, ax] * freqs[k] / (C * du) for ax in (0, 1)]
+            if any(abs(x - math.floor(x) - 0.5) > 0.5 - 1e-6 for x in xs):
+                continue
+            want = [math.floor(x) + N // 2 for x in xs]
+            if all(0 <= w < N for w in want):
+                assert list(cl[r, k]) == want
+                checked += 1
+                plain = [math.floor(uvw[r, ax] * freqs[k] / (C * du)) + N // 2 for ax in (0, 1)]
+                moved += plain != want
+    assert checked > 150 and moved > 20   # the rotation changes cells
