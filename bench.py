@@ -41,6 +41,8 @@ def parse():
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--config", default="alma_compact", choices=["alma_compact", "tiny", "wideband_hi", "batched", "mixed"])
+    p.add_argument("--reproject", action="store_true",
+                   help="full re-projection of Eq. 1: every window names its phase centre and stacking position")
     p.add_argument("--storage", default="c64", choices=["c64", "f16", "bf16"],
                    help="visibility storage (16-bit: one power-of-two scale per window)")
     p.add_argument("--pool-gb", type=float, default=96.0, help="batched: device pool the windows alias (GB)")
@@ -217,7 +219,8 @@ def make_workload(args, rank, device):
         # the complex-half variant holds 48 sources (drawn directly as 16-bit pairs)
         n = args.sources or (24 if args.storage == "c64" else 48)
         ids = shard_ids(n, rank)
-        return synth.wideband_hi(device, n_sources=n, src_ids=ids, storage=args.storage)
+        wl = synth.wideband_hi(device, n_sources=n, src_ids=ids, storage=args.storage)
+        return synth.with_reprojection(wl, math.radians(-30.0)) if args.reproject else wl
     else:
         n = args.sources or {"alma_compact": 64, "batched": 2000}[args.config]
         ids = shard_ids(n, rank)
@@ -225,6 +228,10 @@ def make_workload(args, rank, device):
             wl = synth.alma_compact(device, n_sources=n, src_ids=ids)
         else:
             wl = synth.batched(device, n_sources=n, src_ids=ids, pool_gb=args.pool_gb)
+    if args.reproject:
+        if args.config == "batched":
+            raise SystemExit("--reproject applies to the array workloads (the batched stack has no sky geometry)")
+        wl = synth.with_reprojection(wl, math.radians(-30.0))
     if args.storage != "c64":
         if args.config == "batched":
             raise SystemExit("--storage applies to workloads with their own arrays (not the aliased pool)")
@@ -269,7 +276,7 @@ def one_step(st, wl, host=None):
     srcs = wl.spws if host is None else host
     for s in srcs:
         st.add_source(s.uvw, s.freqs, s.vis, s.weights, s.flags, l=s.l, m=s.m, z=s.z, pol_map=s.pol_map,
-                      vis_scale=s.vis_scale)
+                      vis_scale=s.vis_scale, reproject=s.radec)
     st.run()
 
 
@@ -334,7 +341,8 @@ def cpu_baseline(wl, f0, df, nsample):
     srcs = []
     for s in windows_in_cube(wl, f0, df, nsample):
         srcs.append(O.Source(s.uvw.cpu().numpy(), s.freqs, host_vis(s), s.weights.cpu().numpy(),
-                             None if s.flags is None else s.flags.cpu().numpy(), s.l, s.m, s.z, s.pol_map))
+                             None if s.flags is None else s.flags.cpu().numpy(), s.l, s.m, s.z, s.pol_map,
+                             radec=s.radec))
     cube = O.make_cube(wl.nu, wl.nv, wl.nrest, wl.npol, wl.du, wl.dv, f0, df, 0, 0)
     nthreads = os.cpu_count() or 1
     t0 = time.perf_counter()
@@ -360,7 +368,7 @@ def run_ours(args):
     if args.autotune > 0:
         for s in wl.spws:
             st.add_source(s.uvw, s.freqs, s.vis, s.weights, s.flags, l=s.l, m=s.m, z=s.z, pol_map=s.pol_map,
-                          vis_scale=s.vis_scale)
+                          vis_scale=s.vis_scale, reproject=s.radec)
         st.autotune(budget=args.autotune, reps=1)
         st.run()                       # the queue the autotuner left in place: the first run
     else:
@@ -460,7 +468,7 @@ def run_e2e(args, wl, tuning, n_vis, ws):
     f0, df = None, None
     for s in wl.spws:
         hs = synth.SourceSpw(to_pinned(s.uvw), s.freqs, to_pinned(s.vis), to_pinned(s.weights),
-                             to_pinned(s.flags), s.l, s.m, s.z, s.pol_map, s.source, s.vis_scale)
+                             to_pinned(s.flags), s.l, s.m, s.z, s.pol_map, s.source, s.vis_scale, s.radec)
         host.append(hs)
     # bytes vista_run copies per step: uvw, weights, and the channels it reads
     # (the in-cube range rounded out to whole flag words) of vis and flags
@@ -543,6 +551,8 @@ def run_reference(args):
         wl = gen(dev, n_sources=n, src_ids=ids, du=meta.du)
         keep = {(s.source, float(s.freqs[0])) for s in picked}
         wl.spws = [s for s in wl.spws if (s.source, float(s.freqs[0])) in keep]
+        if args.reproject:
+            wl = synth.with_reprojection(wl, math.radians(-30.0))
         if args.storage != "c64":
             wl = synth.half_storage(wl, args.storage)
         spws = wl.spws
@@ -552,7 +562,8 @@ def run_reference(args):
                                 wl.central_freq)
         spws = windows_in_cube(wl, f0, df, nsample)
     srcs = [O.Source(s.uvw.cpu().numpy(), s.freqs, host_vis(s), s.weights.cpu().numpy(),
-                     None if s.flags is None else s.flags.cpu().numpy(), s.l, s.m, s.z, s.pol_map) for s in spws]
+                     None if s.flags is None else s.flags.cpu().numpy(), s.l, s.m, s.z, s.pol_map,
+                     radec=s.radec) for s in spws]
     cube = O.make_cube(wl.nu, wl.nv, wl.nrest, wl.npol, wl.du, wl.dv, f0, df, 0, 0)
     nthreads = os.cpu_count() or 1
     times, n = [], 0

@@ -161,6 +161,27 @@ int vista_open_stack(const vista_cube_desc *desc, vista_stack **out);
  * alignment); the contents of device arrays are not inspected. */
 int vista_add_source(vista_stack *h, const vista_source_desc *src);
 
+/* Queue a window with the full re-projection of Eq. 1 (Sec. 3.3): the
+ * window's phase centre is (ra0, dec0) and the stacking position (ra1, dec1),
+ * radians, in one equatorial frame.  Otherwise as vista_add_source.
+ *   - The phase shift of Eq. 2 uses (l, m) = the direction cosines of
+ *     (ra1, dec1) seen from (ra0, dec0):
+ *       l = cos dec1 sin(ra1 - ra0),
+ *       m = sin dec1 cos dec0 - cos dec1 sin dec0 cos(ra1 - ra0);
+ *     src->l and src->m are ignored.
+ *   - The uv cells use the baseline expressed for the new phase centre,
+ *     (u', v', w') = R (u, v, w) with R = M(ra1, dec1) M(ra0, dec0)^T and
+ *     M(ra, dec) the rows (east, north, toward (ra, dec)) of the uvw frame;
+ *     R is formed on the host in FP64, and u' = (R00 u + R01 v) + R02 w (the
+ *     same for v') in FP64 with every product and sum rounded, so the cells
+ *     follow the same FP64 rule as without re-projection.  The Hermitian fold
+ *     (if on) tests the rotated (u', v').
+ * E_ARG: non-finite angles, |dec| > pi/2, or a stacking position 90 degrees
+ * or more from the phase centre; and every check of vista_add_source.  The
+ * handle is unchanged on error.  Not available in vista_stack_noalloc. */
+int vista_add_source_reproject(vista_stack *h, const vista_source_desc *src, double ra0, double dec0, double ra1,
+                               double dec1);
+
 /* Stack every queued source into the cube (additive across runs) and clear
  * the queue.  Host planning happens here; device work is queued on the
  * stream and the call returns without waiting for it (except that host-memory

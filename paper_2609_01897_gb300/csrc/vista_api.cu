@@ -228,9 +228,12 @@ extern "C" int vista_open_stack(const vista_cube_desc *d, vista_stack **out)
 
 // ------------------------------------------------------------- add source
 
-extern "C" int vista_add_source(vista_stack *h, const vista_source_desc *s)
+namespace {
+
+// Validation and queueing shared by the two add calls; rot: the window's
+// re-projection (row-major 3 x 3), or null.
+int add_source_impl(vista_stack *h, const vista_source_desc *s, const double *rot)
 {
-    CHECK_HANDLE(h);
     if (!s) return fail(h, VISTA_E_ARG, "null source descriptor");
     const vista_cube_desc &c = h->desc;
     if (s->nrow < 0) return fail(h, VISTA_E_ARG, "nrow must be >= 0");
@@ -285,8 +288,61 @@ extern "C" int vista_add_source(vista_stack *h, const vista_source_desc *s)
     }
     sh.d.freqs = nullptr;
     sh.d.pol_map = nullptr;
+    if (rot) {
+        sh.has_rot = true;
+        std::memcpy(sh.rot, rot, sizeof sh.rot);
+    }
     h->pending.push_back(std::move(sh));
     return VISTA_OK;
+}
+
+// Eq. 1's frames: the rows of M(ra, dec) are the unit vectors u (east),
+// v (north) and w (toward (ra, dec)) in equatorial coordinates.
+void uvw_frame(double ra, double dec, double M[3][3])
+{
+    M[0][0] = -std::sin(ra);
+    M[0][1] = std::cos(ra);
+    M[0][2] = 0.0;
+    M[1][0] = -std::sin(dec) * std::cos(ra);
+    M[1][1] = -std::sin(dec) * std::sin(ra);
+    M[1][2] = std::cos(dec);
+    M[2][0] = std::cos(dec) * std::cos(ra);
+    M[2][1] = std::cos(dec) * std::sin(ra);
+    M[2][2] = std::sin(dec);
+}
+
+}  // namespace
+
+extern "C" int vista_add_source(vista_stack *h, const vista_source_desc *s)
+{
+    CHECK_HANDLE(h);
+    return add_source_impl(h, s, nullptr);
+}
+
+extern "C" int vista_add_source_reproject(vista_stack *h, const vista_source_desc *s, double ra0, double dec0,
+                                          double ra1, double dec1)
+{
+    CHECK_HANDLE(h);
+    if (!s) return fail(h, VISTA_E_ARG, "null source descriptor");
+    const double half_pi = 1.5707963267948966;
+    if (!(is_fin(ra0) && is_fin(ra1) && is_fin(dec0) && is_fin(dec1)))
+        return fail(h, VISTA_E_ARG, "phase centre and stacking position must be finite");
+    if (std::fabs(dec0) > half_pi || std::fabs(dec1) > half_pi)
+        return fail(h, VISTA_E_ARG, "declinations must lie in [-pi/2, pi/2]");
+    // R = M(ra1, dec1) M(ra0, dec0)^T, each entry summed in order (Eq. 1)
+    double M0[3][3], M1[3][3], R[9];
+    uvw_frame(ra0, dec0, M0);
+    uvw_frame(ra1, dec1, M1);
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) R[3 * i + j] = M1[i][0] * M0[j][0] + M1[i][1] * M0[j][1] + M1[i][2] * M0[j][2];
+    // the shift's direction cosines: the stacking position seen from the phase centre
+    const double da = ra1 - ra0;
+    vista_source_desc d = *s;
+    d.l = std::cos(dec1) * std::sin(da);
+    d.m = std::sin(dec1) * std::cos(dec0) - std::cos(dec1) * std::sin(dec0) * std::cos(da);
+    if (!(d.l * d.l + d.m * d.m < 1.0 && R[8] > 0.0))
+        return fail(h, VISTA_E_ARG, "the stacking position must lie less than 90 degrees from the phase centre");
+    return add_source_impl(h, &d, R);
 }
 
 // --------------------------------------------------------------- readback
@@ -526,6 +582,8 @@ extern "C" int vista_close(vista_stack *h)
     h->b_stage.release();
     h->b_unpack.release();
     h->b_sort.release();
+    h->b_rot.release();
+    h->b_guvw.release();
     delete h;
     return VISTA_OK;
 }

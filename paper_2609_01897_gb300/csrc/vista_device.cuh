@@ -155,6 +155,21 @@ __device__ __forceinline__ int axis_cell64(double c, double s, int n)
     return (int)floor(x) + (n >> 1);
 }
 
+// Eq. 1: the gridding coordinates (u', v') = the first two rows of R (u, v, w)
+// of one row of a re-projected window, each product and sum rounded in the
+// order written (no FMA, as the oracle), so that the FP64 cell rule applied
+// to them is exact.  Stored at g[0], g[1] (g[2], w', is not needed: the delay
+// uses the stored baseline); returned as well.
+__device__ __forceinline__ double2 rotate_row(const double *R, const double *x, double *g)
+{
+    const double a = x[0], b = x[1], c = x[2];
+    const double u = __dadd_rn(__dadd_rn(__dmul_rn(R[0], a), __dmul_rn(R[1], b)), __dmul_rn(R[2], c));
+    const double v = __dadd_rn(__dadd_rn(__dmul_rn(R[3], a), __dmul_rn(R[4], b)), __dmul_rn(R[5], c));
+    g[0] = u;
+    g[1] = v;
+    return make_double2(u, v);
+}
+
 // The cell iv * nu + iu of channel `cd` of one row by the FP64 rule, -1 off
 // the grid (the fall-back of CC_MIXED chunks; out of line, rarely run).
 static __device__ __noinline__ int cell_exact(const double *uvw, int64_t row, bool fold, const ChanD *cd, int nu,

@@ -41,6 +41,8 @@ struct SrcHost {
     std::vector<double> freqs;
     std::vector<int32_t> pol_map;   // npol entries (identity filled in)
     uint64_t freq_digest = 0;       // digest of the frequencies (freq_digest())
+    bool has_rot = false;           // re-projected (Eq. 1): cells from rot (u, v, w)
+    double rot[9] = {1, 0, 0, 0, 1, 0, 0, 0, 1};
 };
 
 // A device-to-device 2-D copy of a run's device pass (flag repacking).
@@ -80,7 +82,7 @@ struct vista_stack {
     vista::DevStats *stats = nullptr;
     uint64_t host_nvis = 0;   // visibilities read, counted from the channel tables at each run
     int32_t *err = nullptr;
-    vista::DevBuf b_srcs, b_chf, b_chd, b_recs, b_cells, b_off, b_stage, b_unpack, b_sort;
+    vista::DevBuf b_srcs, b_chf, b_chd, b_recs, b_cells, b_off, b_stage, b_unpack, b_sort, b_rot, b_guvw;
     std::vector<vista::ClassRun> classes;
     std::vector<vista::Copy2D> copies;   // device copies of the last planned run
     vista::LaunchCfg cfg{48, 1, 4, 1, 4};

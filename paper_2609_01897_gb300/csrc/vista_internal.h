@@ -84,7 +84,9 @@ struct ChanD {
 
 // One (source, window) as the kernels see it.
 struct SrcDev {
-    const double *uvw;
+    const double *uvw;      // the stored baselines: the delay of Eq. 2
+    const double *guvw;     // the gridding baselines (stride 3, u and v read): uvw, or R uvw for a
+                            // re-projected window (Eq. 1)
     const void *vis;        // element (row, k, p) at (row * vstride + k - kbase) * npol + p
     const float *wts;
     int64_t nrow;
@@ -100,7 +102,7 @@ struct SrcDev {
     int32_t nchunk;         // work chunks along the channel axis
     int32_t vstride;        // channels per stored row (nchan, or k_hi - k_lo when staged)
     int32_t kbase;          // channel index of the first stored channel
-    int32_t pad;
+    int32_t rot1;           // 1 + index of the window's R in RunArgs::rot (k_rotate fills guvw), 0 = none
     float key_su, key_sv;   // fl32(s_k) at the row-ordering reference channel
     int64_t rec_off;        // first row record of this window
     int64_t cell_off;       // first chunk-cell entry of this window ([chunk][row] inside)
@@ -110,6 +112,7 @@ struct SrcDev {
     int64_t fpitch;
     int32_t fk0;
     int32_t pad3;
+    int64_t pad4;
 };
 static_assert(sizeof(SrcDev) % 16 == 0, "SrcDev is copied in 16-byte units");
 
@@ -206,6 +209,7 @@ struct RunArgs {
     int2 *ccells;               // chunk cells (+ 4 entries of padding for the bulk copies)
     const int64_t *row_off;     // [nsrc+1] cumulative rows
     int64_t nrows_total;
+    const double *rot;          // 9 doubles (row-major R of Eq. 1) per re-projected window
     CubeGeom g;
     void *cube;                 // per entry: FP64 double[4], or float4 (mixed)
     double *cube_master;        // mixed with comp = 1: FP64 double[4] per entry, the sums moved
@@ -224,6 +228,9 @@ cudaError_t launch_prepare(const RunArgs &a, cudaStream_t st, int *nlaunch = nul
 // (chans_per_lane << 8) | npol, shared by every window of the class.
 cudaError_t launch_mixed(const RunArgs &a, int key, int warps_per_cta, int prefetch, cudaStream_t st);
 cudaError_t launch_fp64(const RunArgs &a, cudaStream_t st);
+// The gridding baselines R (u, v, w) of the class's re-projected windows
+// (a.rot non-null; one thread per row of the class), for the FP64 form.
+cudaError_t launch_rotate(const RunArgs &a, cudaStream_t st);
 cudaError_t launch_unpack(const void *cube, const double *master, const uint32_t *count, int fp64, int64_t n,
                           void *sum_wv, void *sum_w, void *sum_wvv, uint32_t *cnt_out,
                           int out_f64, cudaStream_t st);

@@ -40,7 +40,7 @@ __global__ void debug_mixed(RunArgs a, int src, double *ph_out, int32_t *cell_ou
             else if (cc.y != CC_MIXED)
                 cid = chunk_cell_step(cc, kk, a.g.nu);
             else
-                cid = cell_exact(S.uvw, row, fold, cd, a.g.nu, a.g.nv);
+                cid = cell_exact(S.guvw, row, fold, cd, a.g.nu, a.g.nv);
             const int iu = cid < 0 ? -1 : cid % a.g.nu, iv = cid < 0 ? -1 : cid / a.g.nu;
             const int64_t o = row * S.nchan + k;
             if (ph_out) {
@@ -79,10 +79,10 @@ __global__ void __launch_bounds__(128) stack_fp64(RunArgs a, int only_src, doubl
     if (EXPORT && s != only_src) return;
     const SrcDev &S = a.srcs[s];
     const int64_t r = gid - a.row_off[s];
-    const double *uvw = S.uvw + 3 * r;
-    double u = uvw[0], v = uvw[1], w = uvw[2];
+    const double *uvw = S.uvw + 3 * r;     // the stored baseline: the delay of Eq. 2
+    const double tau = uvw[0] * S.l + uvw[1] * S.m + uvw[2] * S.n1;
+    double u = S.guvw[3 * r], v = S.guvw[3 * r + 1];   // the gridding baseline (Eq. 1)
     const bool fold = a.g.fold && (v < 0.0 || (v == 0.0 && u < 0.0));
-    const double tau = u * S.l + v * S.m + w * S.n1;
     if (fold) {
         u = -u;
         v = -v;

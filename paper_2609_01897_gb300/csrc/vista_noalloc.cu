@@ -214,6 +214,7 @@ extern "C" int vista_stack_noalloc(const vista_cube_desc *c, const vista_source_
 
     SrcDev d{};
     d.uvw = s->uvw;
+    d.guvw = s->uvw;   // no re-projection here
     d.vis = s->vis;
     d.wts = s->weights;
     d.fbase = repack ? (const uint8_t *)(b + o_flags) : s->flags;

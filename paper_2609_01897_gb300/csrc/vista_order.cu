@@ -7,7 +7,8 @@
 //
 //   k_keys         cell of every row at the window's highest in-cube
 //                  frequency -> (stripe, local cell key); stripe counts per
-//                  segment of rows
+//                  segment of rows; a re-projected window's gridding
+//                  baselines R (u, v, w) (Eq. 1)
 //   k_segscan      segment offsets inside each (window, stripe) bucket (a
 //                  warp scan per bucket)
 //   k_slots        each row's slot in its bucket, in row order
@@ -57,10 +58,14 @@ __global__ void __launch_bounds__(256) k_keys(RunArgs a)
     const int64_t seg = blockIdx.x;
     const SegRange sr = seg_range(a, seg);
     const SrcDev &S = a.srcs[sr.w];
+    // a re-projected window's gridding baselines are written here (Eq. 1)
+    const double *R = S.rot1 ? a.rot + 9 * (int64_t)(S.rot1 - 1) : nullptr;
+    double *G = R ? const_cast<double *>(S.guvw) : nullptr;
     if (!so.sorted) {
         for (int64_t r = sr.r0 + threadIdx.x; r < sr.r1; r += blockDim.x) {
             so.slot[sr.g0 + r] = (uint32_t)r;
             so.key[sr.g0 + r] = 0u;
+            if (G) rotate_row(R, S.uvw + 3 * r, G + 3 * r);
         }
         if (threadIdx.x == 0 && sr.r0 == 0) so.hist[sr.w] = (uint32_t)S.nrow;
         return;
@@ -70,7 +75,15 @@ __global__ void __launch_bounds__(256) k_keys(RunArgs a)
     for (int64_t r = sr.r0 + threadIdx.x; r < sr.r1; r += blockDim.x) {
         uint32_t stripe = 0, L = 0;
         if (S.k_hi > S.k_lo) {
-            double u = S.uvw[3 * r], v = S.uvw[3 * r + 1];
+            double u, v;
+            if (G) {
+                const double2 g = rotate_row(R, S.uvw + 3 * r, G + 3 * r);
+                u = g.x;
+                v = g.y;
+            } else {
+                u = S.uvw[3 * r];
+                v = S.uvw[3 * r + 1];
+            }
             if (a.g.fold && (v < 0.0 || (v == 0.0 && u < 0.0))) {
                 u = -u;
                 v = -v;
@@ -431,10 +444,11 @@ __global__ void __launch_bounds__(256) k_rows(RunArgs a)
     const SrcDev &S = a.srcs[w];
     const int64_t q = p - a.row_off[w];
     const int64_t r = a.so.perm[p];
-    const double *uvw = S.uvw + 3 * r;
-    const double u = uvw[0], v = uvw[1], wz = uvw[2];
+    const double *uvw = S.uvw + 3 * r;     // the stored baseline: the delay of Eq. 2
+    const double *guvw = S.guvw + 3 * r;   // the gridding baseline (rotated for a re-projected window)
+    const double tau = uvw[0] * S.l + uvw[1] * S.m + uvw[2] * S.n1;
+    const double u = guvw[0], v = guvw[1];
     const bool fold = a.g.fold && (v < 0.0 || (v == 0.0 && u < 0.0));
-    const double tau = u * S.l + v * S.m + wz * S.n1;
     RowRec rec;
     split_ff(tau, rec.tau_hi, rec.tau_lo);
     rec.row = (uint32_t)r;
@@ -451,7 +465,28 @@ __global__ void __launch_bounds__(256) k_rows(RunArgs a)
     const ChanF *cf = a.chf + S.chan_off;
     int2 *out = a.ccells + S.cell_off + q;
     const int nchunk = S.nchunk;
-    for (int c = 0; c < nchunk; ++c) out[(int64_t)c * S.nrow] = chunk_cell(a, S, cf, cd, c, uf, vf, uvw, fold);
+    for (int c = 0; c < nchunk; ++c) out[(int64_t)c * S.nrow] = chunk_cell(a, S, cf, cd, c, uf, vf, guvw, fold);
+}
+
+// Re-projected windows (Eq. 1): their gridding baselines R (u, v, w) (see
+// rotate_row), one thread per row.  The mixed path forms them in k_keys,
+// which reads every row anyway; this kernel serves the plain FP64 form.
+__global__ void __launch_bounds__(256) k_rotate(RunArgs a)
+{
+    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= a.nrows_total) return;
+    const int w = find_owner(a.row_off, a.nsrc, p);
+    const SrcDev &S = a.srcs[w];
+    if (!S.rot1) return;
+    const int64_t r = p - a.row_off[w];
+    rotate_row(a.rot + 9 * (int64_t)(S.rot1 - 1), S.uvw + 3 * r, const_cast<double *>(S.guvw) + 3 * r);
+}
+
+cudaError_t launch_rotate(const RunArgs &a, cudaStream_t st)
+{
+    if (!a.rot || a.nrows_total == 0) return cudaSuccess;
+    k_rotate<<<(unsigned)((a.nrows_total + 255) / 256), 256, 0, st>>>(a);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_prepare(const RunArgs &a, cudaStream_t st, int *nlaunch)

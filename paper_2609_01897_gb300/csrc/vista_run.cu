@@ -154,6 +154,15 @@ cudaError_t device_pass(vista_stack *h, cudaStream_t st)
     }
     for (ClassRun &cr : h->classes) {
         const RunArgs &a = cr.args;
+        if (a.rot && fp64) {
+            // gridding baselines of the re-projected windows (the mixed path
+            // forms them in its pre-pass)
+            const int sp = span_begin(h, 0);
+            e = launch_rotate(a, st);
+            span_end(h, sp);
+            if (h->timing) h->tacc.launches += 1;
+            if (e != cudaSuccess) return e;
+        }
         if (fp64) {
             const int sp = span_begin(h, 1);
             e = launch_fp64(a, st);
@@ -179,7 +188,7 @@ cudaError_t device_pass(vista_stack *h, cudaStream_t st)
 
 // Everything the plan of a run depends on, as bytes: the cube and lattice,
 // the launch configuration, and per window its arrays, shape, position,
-// redshift, pol map and frequencies (by digest).
+// re-projection, redshift, pol map and frequencies (by digest).
 template <typename T>
 void put(std::vector<uint8_t> &v, const T &x)
 {
@@ -209,6 +218,8 @@ std::vector<uint8_t> run_signature(const vista_stack *h)
         put(v, s.d.m);
         put(v, s.d.z);
         put(v, s.freq_digest);
+        put(v, s.has_rot);
+        if (s.has_rot) put(v, s.rot);
         for (int32_t p : s.pol_map) put(v, p);
     }
     return v;
@@ -346,6 +357,14 @@ extern "C" int vista_run(vista_stack *h)
     }
 
     std::vector<SrcDev> sdev;
+    std::vector<double> rots;   // 9 per re-projected window (SrcDev::rot1 - 1 indexes them)
+    std::vector<char> cls_rot(classes.size(), 0);
+    // gridding baselines of the re-projected windows (filled by k_rotate)
+    int64_t rot_rows = 0, guvw_pos = 0;
+    for (const SrcHost &s : h->pending)
+        if (s.has_rot) rot_rows += s.d.nrow;
+    if (rot_rows > 0 && (e = h->b_guvw.ensure((size_t)rot_rows * 24)) != cudaSuccess)
+        return cuda_fail(h, e, "re-projection buffer allocation");
     std::vector<int64_t> offs;
     std::vector<size_t> cls_src0(classes.size()), cls_off0(classes.size());
     std::vector<SortLayout> layouts(classes.size());
@@ -466,6 +485,14 @@ extern "C" int vista_run(vista_stack *h)
             roff[t + 1] = roff[t] + d.nrow;
             soff[t + 1] = soff[t] + (fp64 ? 0 : (d.nrow + SEG_ROWS - 1) / SEG_ROWS);
             max_items += (int64_t)d.nchunk * ((d.nrow + cfg.rows_per_item - 1) / cfg.rows_per_item + h->nstripe);
+            d.guvw = d.uvw;
+            if (s.has_rot) {
+                d.rot1 = (int32_t)(rots.size() / 9) + 1;
+                rots.insert(rots.end(), s.rot, s.rot + 9);
+                d.guvw = (const double *)h->b_guvw.p + 3 * guvw_pos;
+                guvw_pos += d.nrow;
+                cls_rot[ci] = 1;
+            }
             sdev.push_back(d);
         }
         offs.insert(offs.end(), roff.begin(), roff.end());
@@ -487,6 +514,8 @@ extern "C" int vista_run(vista_stack *h)
     if ((e = upload(h->b_chf, chf, h->stream)) != cudaSuccess) return cuda_fail(h, e, "channel table upload");
     if ((e = upload(h->b_chd, chd, h->stream)) != cudaSuccess) return cuda_fail(h, e, "channel table upload");
     if ((e = upload(h->b_off, offs, h->stream)) != cudaSuccess) return cuda_fail(h, e, "offset table upload");
+    if (!rots.empty() && (e = upload(h->b_rot, rots, h->stream)) != cudaSuccess)
+        return cuda_fail(h, e, "re-projection table upload");
     if (!fp64) {
         if ((e = h->b_recs.ensure((size_t)(rec_total > 0 ? rec_total : 1) * sizeof(RowRec))) != cudaSuccess)
             return cuda_fail(h, e, "row record allocation");
@@ -507,6 +536,7 @@ extern "C" int vista_run(vista_stack *h)
         a.chf = (const ChanF *)h->b_chf.p;
         a.chd = (const ChanD *)h->b_chd.p;
         a.recs = (RowRec *)h->b_recs.p;
+        a.rot = cls_rot[ci] ? (const double *)h->b_rot.p : nullptr;
         a.ccells = (int2 *)h->b_cells.p;
         a.row_off = (const int64_t *)h->b_off.p + cls_off0[ci];
         a.so.seg_off = a.row_off + cr.members.size() + 1;

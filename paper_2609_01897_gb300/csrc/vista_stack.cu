@@ -263,7 +263,7 @@ __global__ void __launch_bounds__(KMAX_THREADS) stack_mixed(RunArgs a)
         {
             const SrcDev &H = *S.hdr;
             const Item &I = *S.self;
-            uvw = H.uvw;
+            uvw = H.guvw;   // the gridding baselines (the per-channel cell fall-back)
             vscale = H.vis_scale;
             nch = I.nch;
             chf0 = I.chf0;

@@ -55,6 +55,7 @@ class SourceSpw:
     pol_map: Optional[np.ndarray] = None
     source: int = 0
     vis_scale: float = 1.0       # 16-bit storage: stored value x vis_scale = visibility
+    radec: Optional[tuple] = None  # (ra0, dec0, ra1, dec1): re-project (Eq. 1) instead of (l, m)
 
 
 @dataclass
@@ -276,6 +277,28 @@ def mixed(device="cpu", n_sources=64, src_ids=None, meta_only=False, du=None) ->
     n = 256
     du = _cube_du(spws, n) if du is None else du
     return Workload("mixed", n, n, 512, 2, du, du, CO10_9_REST, spws)
+
+
+def sky_position(ra0, dec0, l, m):
+    """The sky position (ra, dec) at direction cosines (l, m) from the phase
+    centre (ra0, dec0): l east, m north, from the frame's unit vectors."""
+    w = np.array([math.cos(dec0) * math.cos(ra0), math.cos(dec0) * math.sin(ra0), math.sin(dec0)])
+    e = np.cross([0.0, 0.0, 1.0], w)
+    e /= np.linalg.norm(e)
+    n = np.cross(w, e)
+    s = l * e + m * n + math.sqrt(1.0 - l * l - m * m) * w
+    return math.atan2(s[1], s[0]), math.asin(s[2])
+
+
+def with_reprojection(wl: Workload, dec0: float) -> Workload:
+    """Every window re-projected (Eq. 1): source s observed with phase centre
+    (0.3 + 0.01 s, dec0) radians and stacked at the position of its synthetic
+    source (its l, m), so the shift is the same and the cells are rotated."""
+    for sp in wl.spws:
+        ra0 = 0.3 + 0.01 * sp.source
+        sp.radec = (ra0, dec0) + sky_position(ra0, dec0, sp.l, sp.m)
+    wl.name += "+reproject"
+    return wl
 
 
 def half_pairs(vis: torch.Tensor, kind: str):

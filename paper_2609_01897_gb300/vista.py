@@ -74,6 +74,8 @@ _P = C.c_void_p
 SIGNATURES = {
     "vista_open_stack": (C.c_int, [C.POINTER(CubeDesc), C.POINTER(_P)]),
     "vista_add_source": (C.c_int, [_P, C.POINTER(SourceDesc)]),
+    "vista_add_source_reproject": (C.c_int, [_P, C.POINTER(SourceDesc), C.c_double, C.c_double, C.c_double,
+                                             C.c_double]),
     "vista_run": (C.c_int, [_P]),
     "vista_read_cube": (C.c_int, [_P, _P, _P, _P, _P, C.c_int]),
     "vista_read_cube_f64": (C.c_int, [_P, _P, _P, _P, _P, C.c_int]),
@@ -172,12 +174,14 @@ class Stack:
         self._inflight = []
 
     # -- sources
-    def add_source(self, uvw, freqs, vis, weights, flags=None, *, l, m, z, pol_map=None,
-                   vis_scale=1.0):
+    def add_source(self, uvw, freqs, vis, weights, flags=None, *, l=0.0, m=0.0, z, pol_map=None,
+                   vis_scale=1.0, reproject=None):
         """uvw [nrow,3] f64, freqs [nchan] f64 (host), vis [nrow,nchan,npol] complex
         (or 16-bit [nrow,nchan,npol,2]), weights [nrow,npol] f32, flags u8 or None.
         CUDA tensors are borrowed device arrays; CPU tensors are host arrays
-        (pin them for asynchronous copies)."""
+        (pin them for asynchronous copies).  reproject = (ra0, dec0, ra1, dec1),
+        radians: the window's phase centre and the stacking position, for the
+        full re-projection of Eq. 1 (l, m are then derived, not read)."""
         vt = _vis_type(vis)
         nrow, nchan, npol = int(vis.shape[0]), int(vis.shape[1]), int(vis.shape[2])
         if vt in (VIS_F16X2, VIS_BF16X2) and (vis.dim() != 4 or vis.shape[3] != 2):
@@ -198,7 +202,12 @@ class Stack:
         d = SourceDesc(nrow, nchan, npol, _ptr(uvw), f.ctypes.data, _ptr(vis), vt, float(vis_scale),
                        _ptr(weights), _ptr(flags), None if pm is None else pm.ctypes.data,
                        float(l), float(m), float(z), MEM_DEVICE if dev else MEM_HOST, 0)
-        _check("vista_add_source", lib().vista_add_source(self.h, C.byref(d)), self.h)
+        if reproject is None:
+            _check("vista_add_source", lib().vista_add_source(self.h, C.byref(d)), self.h)
+        else:
+            ra0, dec0, ra1, dec1 = (float(x) for x in reproject)
+            _check("vista_add_source_reproject",
+                   lib().vista_add_source_reproject(self.h, C.byref(d), ra0, dec0, ra1, dec1), self.h)
         self._pending.append((uvw, vis, weights, flags))
 
     def run(self):

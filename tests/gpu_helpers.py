@@ -20,15 +20,16 @@ PHASE_TOL_MIXED = 1e-5   # rad
 PHASE_TOL_FP64 = 1e-9
 
 
-def oracle_sources(wl, dequant=None):
+def oracle_sources(wl, dequant=None, reproject=None):
     """Host copies of a workload's windows as oracle sources.  dequant:
-    optional dict id(spw) -> complex128 array replacing vis (16-bit inputs)."""
+    optional dict id(spw) -> complex128 array replacing vis (16-bit inputs);
+    reproject: optional per-window (ra0, dec0, ra1, dec1) (Eq. 1)."""
     out = []
-    for s in wl.spws:
+    for i, s in enumerate(wl.spws):
         vis = s.vis.cpu().numpy() if dequant is None else dequant[id(s)]
         flags = None if s.flags is None else s.flags.cpu().numpy()
         out.append(O.Source(s.uvw.cpu().numpy(), s.freqs, vis, s.weights.cpu().numpy(), flags,
-                            s.l, s.m, s.z, s.pol_map))
+                            s.l, s.m, s.z, s.pol_map, radec=None if reproject is None else reproject[i]))
     return out
 
 
@@ -39,7 +40,7 @@ def lattice_of(wl):
 
 
 def run_gpu(wl, precision=V.PREC_MIXED, bin_mode=V.BIN_OVERLAP, fold=False, tuning=None,
-            host_mem=False, vis_override=None, scales=None, f64=True):
+            host_mem=False, vis_override=None, scales=None, f64=True, reproject=None):
     st = V.Stack(wl.nu, wl.nv, wl.nrest, wl.npol, wl.du, wl.dv, rest_f0=wl.rest_f0,
                  rest_df=wl.rest_df, central_freq=wl.central_freq, bin_mode=bin_mode,
                  precision=precision, hermitian_fold=fold)
@@ -52,7 +53,8 @@ def run_gpu(wl, precision=V.PREC_MIXED, bin_mode=V.BIN_OVERLAP, fold=False, tuni
             if host_mem:
                 args = [a.cpu().pin_memory() if isinstance(a, torch.Tensor) else a for a in args]
             st.add_source(*args, l=s.l, m=s.m, z=s.z, pol_map=s.pol_map,
-                          vis_scale=1.0 if scales is None else scales[i])
+                          vis_scale=1.0 if scales is None else scales[i],
+                          reproject=None if reproject is None else reproject[i])
         st.run()
         cube = st.read_cube(device=True, f64=f64)
         out = {k: v.cpu().numpy() for k, v in cube.items()}
@@ -64,10 +66,11 @@ def run_gpu(wl, precision=V.PREC_MIXED, bin_mode=V.BIN_OVERLAP, fold=False, tuni
         st.close()
 
 
-def run_oracle(wl, bin_mode=V.BIN_OVERLAP, fold=False, iv_select=None, dequant=None, nthreads=4):
+def run_oracle(wl, bin_mode=V.BIN_OVERLAP, fold=False, iv_select=None, dequant=None, nthreads=4,
+               reproject=None):
     f0, df = lattice_of(wl)
     cube = O.make_cube(wl.nu, wl.nv, wl.nrest, wl.npol, wl.du, wl.dv, f0, df, bin_mode, 1 if fold else 0)
-    srcs = oracle_sources(wl, dequant)
+    srcs = oracle_sources(wl, dequant, reproject)
     out = O.stack(cube, srcs, iv_select=iv_select, nthreads=nthreads, with_abs=True)
     out["lattice"] = (f0, df)
     return out
