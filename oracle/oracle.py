@@ -143,6 +143,25 @@ def offset(ra0, dec0, ra1, dec1):
     return float(lm[0]), float(lm[1])
 
 
+def regrid_rows(src, rest_f0, rest_df, nrest, bin_mode=0):
+    """The paper's per-row output (Eq. 3): each row's shifted spectrum on the
+    rest lattice, V_out(r, j, p) = sum_k V'(r, k, p) w_kj / sum_k w_kj over
+    the unflagged channels k (0 where that sum is 0), and the sum itself.
+    V' is the shifted visibility of Eq. 2 (phasors(): the same shift as the
+    stack, re-projection included) and w_kj the Eq. 4 weights (rest_weights());
+    the two sums are plain matrix products.  Returns (vis_out complex128
+    [nrow, nrest, npol], wsum float64 [nrow, nrest, npol])."""
+    vis = src.vis.astype(np.complex128) * phasors(src)[..., None]
+    w = rest_weights(src.freqs, src.c.z, rest_f0, rest_df, nrest, bin_mode)     # [nchan, nrest]
+    ok = np.ones(vis.shape, dtype=np.float64) if src.flags is None else (src.flags == 0).astype(np.float64)
+    num = np.einsum("rkp,kj->rjp", vis * ok, w)
+    den = np.einsum("rkp,kj->rjp", ok, w)
+    out = np.zeros_like(num)
+    nz = den > 0
+    out[nz] = num[nz] / den[nz]
+    return out, den
+
+
 def make_cube(nu, nv, nrest, npol, du, dv, rest_f0, rest_df, bin_mode=0, hermitian_fold=0):
     return OrCube(nu, nv, nrest, npol, du, dv, rest_f0, rest_df, bin_mode, hermitian_fold)
 

@@ -515,3 +515,71 @@ def test_reprojected_cells_use_the_rotated_baseline(oracle_mod):
                 plain = [math.floor(uvw[r, ax] * freqs[k] / (C * du)) + N // 2 for ax in (0, 1)]
                 moved += plain != want
     assert checked > 150 and moved > 20   # the rotation changes cells
+
+
+# ----------------------------------------------------------------- Eq. 3 per-row output
+
+def test_regrid_rows_brute_force(oracle_mod):
+    """Eq. 3 per row written as plain loops: the unreduced phase exp(2 pi i
+    tau nu/c), the Eq. 4 weights, flagged channels left out of both sums."""
+    rng = np.random.default_rng(50)
+    uvw = _uvw(3, rng, 800.0)
+    freqs = 115e9 + 7.8125e6 * np.arange(9)
+    vis = rng.normal(size=(3, 9, 2)) + 1j * rng.normal(size=(3, 9, 2))
+    flags = (rng.uniform(size=(3, 9, 2)) < 0.2).astype(np.uint8)
+    l0, m0, z = 15 * ARCSEC, -8 * ARCSEC, 1.7
+    src = _src(oracle_mod, uvw, freqs, vis, l0, m0, z, flags=flags)
+    f0, df = oracle_mod.auto_lattice([freqs], [z], 40, 115e9 * 2.7)
+    out, den = oracle_mod.regrid_rows(src, f0, df, 40)
+    W = oracle_mod.rest_weights(freqs, z, f0, df, 40)
+    n1 = math.sqrt(1 - l0 * l0 - m0 * m0) - 1
+    for r in range(3):
+        tau = uvw[r, 0] * l0 + uvw[r, 1] * m0 + uvw[r, 2] * n1
+        for p in range(2):
+            for j in range(40):
+                num = 0j
+                d = 0.0
+                for k in range(9):
+                    if flags[r, k, p] or W[k, j] == 0:
+                        continue
+                    num += vis[r, k, p] * cmath.exp(2j * math.pi * tau * freqs[k] / C) * W[k, j]
+                    d += W[k, j]
+                assert abs(den[r, j, p] - d) <= 1e-14
+                want = num / d if d > 0 else 0j
+                assert abs(out[r, j, p] - want) <= 1e-9 * max(1.0, abs(want))
+    assert (den > 0).sum() > 40
+
+
+def test_regrid_rows_flat_spectrum(oracle_mod):
+    """No shift and a constant spectrum: every covered output channel holds
+    the constant (Eq. 3 is a weighted mean)."""
+    rng = np.random.default_rng(51)
+    uvw = _uvw(5, rng)
+    freqs = 100e9 + 15.625e6 * np.arange(16)
+    vis = np.full((5, 16, 1), 0.3 - 0.4j)
+    src = _src(oracle_mod, uvw, freqs, vis, 0.0, 0.0, 2.0)
+    f0, df = oracle_mod.auto_lattice([freqs], [2.0], 48, 300e9)
+    out, den = oracle_mod.regrid_rows(src, f0, df, 48)
+    cov = den > 0
+    assert cov.sum() >= 5 * 15
+    np.testing.assert_allclose(out[cov], 0.3 - 0.4j, rtol=1e-14)
+    np.testing.assert_allclose(den.sum(axis=1), 16.0, rtol=1e-12)   # every channel is inside the lattice
+
+
+def test_regrid_rows_equals_one_row_stack(oracle_mod):
+    """One row alone in its cells: the stack's sum_wv / sum_w (W = 1) is the
+    row's Eq. 3 output -- the C stack and the per-row product agree."""
+    rng = np.random.default_rng(52)
+    uvw = _uvw(1, rng, 400.0)
+    freqs = 230e9 + 15.625e6 * np.arange(12)
+    vis = rng.normal(size=(1, 12, 2)) + 1j * rng.normal(size=(1, 12, 2))
+    src = _src(oracle_mod, uvw, freqs, vis, 5 * ARCSEC, 3 * ARCSEC, 1.2)
+    f0, df = oracle_mod.auto_lattice([freqs], [1.2], 32, 230e9 * 2.2)
+    out, den = oracle_mod.regrid_rows(src, f0, df, 32)
+    cube = oracle_mod.make_cube(8, 8, 32, 2, 1e6, 1e6, f0, df, 0, 0)   # one huge cell: every channel in it
+    st = oracle_mod.stack(cube, [src])
+    sw = st["sum_w"].sum(axis=(0, 1))          # [nrest, npol]
+    swv = st["sum_wv"].sum(axis=(0, 1))
+    cov = sw > 0
+    np.testing.assert_allclose(swv[cov] / sw[cov], out[0][cov], rtol=1e-12, atol=1e-15)
+    np.testing.assert_allclose(sw, den[0], rtol=1e-12, atol=1e-15)
