@@ -182,6 +182,26 @@ int vista_add_source(vista_stack *h, const vista_source_desc *src);
 int vista_add_source_reproject(vista_stack *h, const vista_source_desc *src, double ra0, double dec0, double ra1,
                                double dec1);
 
+/* The paper's per-row output (Eq. 3, Sec. 3.3): every row of one window
+ * regridded onto the handle's rest lattice, as the rows of an output
+ * measurement set (no uv cube).  For row r, output channel j, pol p:
+ *   out_vis[r][j][p]  = sum_k V'(r,k,p) w_kj / sum_k w_kj   (complex64 as
+ *                       float pairs; 0 where the sum of weights is 0),
+ *   out_wsum[r][j][p] = sum_k w_kj,
+ * over the unflagged channels k, with V' the shifted visibility of Eq. 2
+ * (src->l, src->m) and w_kj the Eq. 4 weights (or the nearest bin, as the
+ * handle's bin_mode).  out_uvw, if not NULL, gets uvw / (1 + z) ([nrow][3],
+ * Eq. 1 with R = I).  The visibility weights are not used (Eq. 3 has none).
+ * src must describe device arrays (mem = VISTA_MEM_DEVICE); the outputs are
+ * device arrays of nrow x nrest x npol entries.  FP64 arithmetic, one thread
+ * per (row, output channel); synchronous on the handle's stream.  The cube
+ * and the queue are not touched.
+ * E_STATE: the lattice is not fixed yet (open with rest_df > 0, or run
+ * first).  E_ARG: a host-visible field fails the checks of vista_add_source
+ * (nchan >= 2 here). */
+int vista_regrid_rows(vista_stack *h, const vista_source_desc *src, float *out_vis, float *out_wsum,
+                      double *out_uvw);
+
 /* Stack every queued source into the cube (additive across runs) and clear
  * the queue.  Host planning happens here; device work is queued on the
  * stream and the call returns without waiting for it (except that host-memory

@@ -18,7 +18,7 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libvista.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-CU_SOURCES = ["vista_stack.cu", "vista_kernels.cu", "vista_order.cu", "vista_run.cu", "vista_api.cu",
+CU_SOURCES = ["vista_stack.cu", "vista_kernels.cu", "vista_order.cu", "vista_run.cu", "vista_api.cu", "vista_regrid.cu",
               "vista_noalloc.cu", "vista_autotune.cu"]
 CXX_SOURCES = ["planner.cpp"]
 

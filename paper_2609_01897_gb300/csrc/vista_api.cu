@@ -584,6 +584,7 @@ extern "C" int vista_close(vista_stack *h)
     h->b_sort.release();
     h->b_rot.release();
     h->b_guvw.release();
+    h->b_regrid.release();
     delete h;
     return VISTA_OK;
 }

@@ -82,7 +82,7 @@ struct vista_stack {
     vista::DevStats *stats = nullptr;
     uint64_t host_nvis = 0;   // visibilities read, counted from the channel tables at each run
     int32_t *err = nullptr;
-    vista::DevBuf b_srcs, b_chf, b_chd, b_recs, b_cells, b_off, b_stage, b_unpack, b_sort, b_rot, b_guvw;
+    vista::DevBuf b_srcs, b_chf, b_chd, b_recs, b_cells, b_off, b_stage, b_unpack, b_sort, b_rot, b_guvw, b_regrid;
     std::vector<vista::ClassRun> classes;
     std::vector<vista::Copy2D> copies;   // device copies of the last planned run
     vista::LaunchCfg cfg{48, 1, 4, 1, 4};

@@ -1,0 +1,187 @@
+// The paper's per-row output (Eq. 3): every row of one window regridded onto
+// the rest lattice, V_out(j) = sum_k V'(k) w_kj / sum_k w_kj over unflagged
+// channels, with V' the shifted visibility of Eq. 2 and w_kj the Eq. 4
+// weights.  Not the stacking hot path: one FP64 thread per (row, output
+// channel), the contributing channels of each output channel listed on the
+// host (a compressed row table built from the FP64 planner's bins).
+#include <cmath>
+#include <vector>
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
+#include "planner.h"
+#include "vista_handle.h"
+
+namespace vista {
+namespace {
+
+struct RegridArgs {
+    const double *uvw;
+    const void *vis;
+    const uint8_t *flags;
+    const double *freq;     // [nchan] Hz
+    const int32_t *start;   // [nrest + 1] first contributor of each output channel
+    const int32_t *chan;    // contributing channel
+    const double *w;        // its Eq. 4 weight
+    float *out_vis;         // [nrow][nrest][npol][2]
+    float *out_wsum;        // [nrow][nrest][npol]
+    double *out_uvw;        // [nrow][3] or null
+    int64_t nrow;
+    int32_t nchan, npol, nrest, vis_type;
+    float vis_scale;
+    double l, m, n1, inv_zf;
+};
+
+__device__ __forceinline__ double2 load_vis(const RegridArgs &a, int64_t i)
+{
+    switch (a.vis_type) {
+    case VISTA_VIS_C128: return reinterpret_cast<const double2 *>(a.vis)[i];
+    case VISTA_VIS_C64: {
+        const float2 v = reinterpret_cast<const float2 *>(a.vis)[i];
+        return make_double2(v.x, v.y);
+    }
+    case VISTA_VIS_F16X2: {
+        const __half2 v = reinterpret_cast<const __half2 *>(a.vis)[i];
+        return make_double2((double)__low2float(v) * a.vis_scale, (double)__high2float(v) * a.vis_scale);
+    }
+    default: {
+        const __nv_bfloat162 v = reinterpret_cast<const __nv_bfloat162 *>(a.vis)[i];
+        return make_double2((double)__low2float(v) * a.vis_scale, (double)__high2float(v) * a.vis_scale);
+    }
+    }
+}
+
+__global__ void __launch_bounds__(256) k_regrid(RegridArgs a)
+{
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= a.nrow * a.nrest) return;
+    const int64_t r = t / a.nrest;
+    const int j = (int)(t - r * a.nrest);
+    const double *x = a.uvw + 3 * r;
+    const double tau = x[0] * a.l + x[1] * a.m + x[2] * a.n1;   // Eq. 2 delay, metres
+    double sr[4] = {0, 0, 0, 0}, si[4] = {0, 0, 0, 0}, sw[4] = {0, 0, 0, 0};
+    for (int e = a.start[j]; e < a.start[j + 1]; ++e) {
+        const int k = a.chan[e];
+        const double w = a.w[e];
+        const double turns = tau * a.freq[k] / C_LIGHT;
+        double s, c;
+        sincospi(2.0 * (turns - floor(turns)), &s, &c);
+#pragma unroll
+        for (int p = 0; p < 4; ++p) {
+            if (p >= a.npol) break;
+            const int64_t i = (r * a.nchan + k) * a.npol + p;
+            if (a.flags && a.flags[i]) continue;
+            const double2 v = load_vis(a, i);
+            sr[p] += w * (v.x * c - v.y * s);
+            si[p] += w * (v.x * s + v.y * c);
+            sw[p] += w;
+        }
+    }
+    for (int p = 0; p < a.npol; ++p) {
+        const int64_t o = (r * a.nrest + j) * a.npol + p;
+        const bool any = sw[p] > 0.0;
+        a.out_vis[2 * o] = any ? (float)(sr[p] / sw[p]) : 0.0f;
+        a.out_vis[2 * o + 1] = any ? (float)(si[p] / sw[p]) : 0.0f;
+        a.out_wsum[o] = (float)sw[p];
+    }
+    if (a.out_uvw && j == 0)
+        for (int c = 0; c < 3; ++c) a.out_uvw[3 * r + c] = x[c] * a.inv_zf;   // Eq. 1 with R = I
+}
+
+}  // namespace
+}  // namespace vista
+
+using namespace vista;
+
+extern "C" int vista_regrid_rows(vista_stack *h, const vista_source_desc *s, float *out_vis, float *out_wsum,
+                                 double *out_uvw)
+{
+    if (!handle_live(h)) return fail(nullptr, VISTA_E_STATE, "unknown or closed handle");
+    if (!s || !out_vis || !out_wsum) return fail(h, VISTA_E_ARG, "null descriptor or output");
+    if (!h->lattice_fixed)
+        return fail(h, VISTA_E_STATE, "the rest lattice is not fixed yet (give rest_df at open, or run first)");
+    if (s->mem != VISTA_MEM_DEVICE) return fail(h, VISTA_E_ARG, "vista_regrid_rows reads device arrays only");
+    if (s->nrow < 0 || s->nchan < 2) return fail(h, VISTA_E_ARG, "need nrow >= 0 and nchan >= 2");
+    if (s->npol != 1 && s->npol != 2 && s->npol != 4) return fail(h, VISTA_E_ARG, "npol must be 1, 2 or 4");
+    if (s->vis_type < VISTA_VIS_C64 || s->vis_type > VISTA_VIS_BF16X2)
+        return fail(h, VISTA_E_ARG, "bad vis_type %d", s->vis_type);
+    if (!s->freqs || (s->nrow > 0 && (!s->uvw || !s->vis)))
+        return fail(h, VISTA_E_ARG, "freqs, uvw and vis must be non-NULL");
+    if (!(std::isfinite(s->l) && std::isfinite(s->m) && s->l * s->l + s->m * s->m < 1.0))
+        return fail(h, VISTA_E_ARG, "need finite l, m with l^2 + m^2 < 1");
+    if (!(std::isfinite(s->z) && s->z > -1.0)) return fail(h, VISTA_E_ARG, "need finite z > -1");
+    const int32_t n = s->nchan, nrest = h->desc.nrest;
+    for (int32_t k = 0; k < n; ++k)
+        if (!(std::isfinite(s->freqs[k]) && s->freqs[k] > 0.0))
+            return fail(h, VISTA_E_ARG, "freqs[%d] is not finite and > 0", k);
+    const bool up = s->freqs[1] > s->freqs[0];
+    for (int32_t k = 1; k < n; ++k)
+        if (up ? !(s->freqs[k] > s->freqs[k - 1]) : !(s->freqs[k] < s->freqs[k - 1]))
+            return fail(h, VISTA_E_ARG, "freqs must be strictly monotone (index %d)", k);
+    if (s->nrow == 0) return VISTA_OK;
+
+    // contributors of each output channel (Eq. 4), from the FP64 planner
+    std::vector<int32_t> j0((size_t)n), nb((size_t)n);
+    std::vector<double> wk((size_t)n * VISTA_MAX_BINS);
+    const int rc = channel_bins(s->freqs, n, s->z, h->f0, h->df, nrest, h->desc.bin_mode, j0.data(), nb.data(),
+                                wk.data());
+    if (rc != VISTA_OK) return fail(h, rc, "channel planning failed");
+    std::vector<int32_t> start((size_t)nrest + 1, 0);
+    for (int32_t k = 0; k < n; ++k)
+        for (int b = 0; b < nb[(size_t)k]; ++b) ++start[(size_t)j0[(size_t)k] + b + 1];
+    for (int32_t j = 0; j < nrest; ++j) start[(size_t)j + 1] += start[(size_t)j];
+    const size_t nnz = (size_t)start[(size_t)nrest];
+    std::vector<int32_t> chan(nnz > 0 ? nnz : 1), fill(start.begin(), start.end() - 1);
+    std::vector<double> w(nnz > 0 ? nnz : 1);
+    for (int32_t k = 0; k < n; ++k)
+        for (int b = 0; b < nb[(size_t)k]; ++b) {
+            const int32_t e = fill[(size_t)j0[(size_t)k] + b]++;
+            chan[(size_t)e] = k;
+            w[(size_t)e] = wk[(size_t)k * VISTA_MAX_BINS + b];
+        }
+
+    // one device table: freqs | start | chan | w
+    auto al = [](size_t b) { return (b + 255) / 256 * 256; };
+    const size_t o_f = 0, o_s = al(sizeof(double) * (size_t)n), o_c = o_s + al(sizeof(int32_t) * start.size()),
+                 o_w = o_c + al(sizeof(int32_t) * chan.size()), total = o_w + al(sizeof(double) * w.size());
+    cudaError_t e = h->b_regrid.ensure(total);
+    if (e != cudaSuccess) return cuda_fail(h, e, "regrid table allocation");
+    char *b = (char *)h->b_regrid.p;
+    e = cudaMemcpyAsync(b + o_f, s->freqs, sizeof(double) * (size_t)n, cudaMemcpyHostToDevice, h->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(b + o_s, start.data(), sizeof(int32_t) * start.size(), cudaMemcpyHostToDevice, h->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(b + o_c, chan.data(), sizeof(int32_t) * chan.size(), cudaMemcpyHostToDevice, h->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(b + o_w, w.data(), sizeof(double) * w.size(), cudaMemcpyHostToDevice, h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "regrid table upload");
+
+    RegridArgs a{};
+    a.uvw = s->uvw;
+    a.vis = s->vis;
+    a.flags = s->flags;
+    a.freq = (const double *)(b + o_f);
+    a.start = (const int32_t *)(b + o_s);
+    a.chan = (const int32_t *)(b + o_c);
+    a.w = (const double *)(b + o_w);
+    a.out_vis = out_vis;
+    a.out_wsum = out_wsum;
+    a.out_uvw = out_uvw;
+    a.nrow = s->nrow;
+    a.nchan = n;
+    a.npol = s->npol;
+    a.nrest = nrest;
+    a.vis_type = s->vis_type;
+    a.vis_scale = (s->vis_type == VISTA_VIS_F16X2 || s->vis_type == VISTA_VIS_BF16X2) ? s->vis_scale : 1.0f;
+    a.l = s->l;
+    a.m = s->m;
+    a.n1 = std::sqrt(1.0 - s->l * s->l - s->m * s->m) - 1.0;
+    a.inv_zf = 1.0 / (1.0 + s->z);
+    const int64_t threads = s->nrow * (int64_t)nrest;
+    k_regrid<<<(unsigned)((threads + 255) / 256), 256, 0, h->stream>>>(a);
+    e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "regrid kernel");
+    return VISTA_OK;
+}

@@ -76,6 +76,7 @@ SIGNATURES = {
     "vista_add_source": (C.c_int, [_P, C.POINTER(SourceDesc)]),
     "vista_add_source_reproject": (C.c_int, [_P, C.POINTER(SourceDesc), C.c_double, C.c_double, C.c_double,
                                              C.c_double]),
+    "vista_regrid_rows": (C.c_int, [_P, C.POINTER(SourceDesc), _P, _P, _P]),
     "vista_run": (C.c_int, [_P]),
     "vista_read_cube": (C.c_int, [_P, _P, _P, _P, _P, C.c_int]),
     "vista_read_cube_f64": (C.c_int, [_P, _P, _P, _P, _P, C.c_int]),
@@ -209,6 +210,31 @@ class Stack:
             _check("vista_add_source_reproject",
                    lib().vista_add_source_reproject(self.h, C.byref(d), ra0, dec0, ra1, dec1), self.h)
         self._pending.append((uvw, vis, weights, flags))
+
+    def regrid_rows(self, uvw, freqs, vis, flags=None, *, l=0.0, m=0.0, z, vis_scale=1.0, with_uvw=False):
+        """The paper's per-row output (Eq. 3) of one window of device arrays:
+        returns (vis_out complex64 [nrow, nrest, npol], wsum float32 [nrow,
+        nrest, npol], uvw / (1 + z) float64 [nrow, 3] or None), on the device.
+        The rest lattice must be fixed (rest_df at open, or after a run)."""
+        vt = _vis_type(vis)
+        nrow, nchan, npol = int(vis.shape[0]), int(vis.shape[1]), int(vis.shape[2])
+        if not vis.is_cuda or not uvw.is_cuda or (flags is not None and not flags.is_cuda):
+            raise ValueError("regrid_rows reads device arrays")
+        for name, t in (("uvw", uvw), ("vis", vis), ("flags", flags)):
+            if t is not None and not t.is_contiguous():
+                raise ValueError("%s must be contiguous" % name)
+        if uvw.dtype != torch.float64 or (flags is not None and flags.dtype != torch.uint8):
+            raise TypeError("uvw must be float64 and flags uint8")
+        nrest = self.shape[2]
+        out = torch.zeros((nrow, nrest, npol, 2), dtype=torch.float32, device=vis.device)
+        wsum = torch.zeros((nrow, nrest, npol), dtype=torch.float32, device=vis.device)
+        ruvw = torch.empty((nrow, 3), dtype=torch.float64, device=vis.device) if with_uvw else None
+        f = np.ascontiguousarray(np.asarray(freqs, dtype=np.float64))
+        d = SourceDesc(nrow, nchan, npol, _ptr(uvw), f.ctypes.data, _ptr(vis), vt, float(vis_scale),
+                       None, _ptr(flags), None, float(l), float(m), float(z), MEM_DEVICE, 0)
+        _check("vista_regrid_rows", lib().vista_regrid_rows(self.h, C.byref(d), _ptr(out), _ptr(wsum),
+                                                            _ptr(ruvw)), self.h)
+        return torch.view_as_complex(out), wsum, ruvw
 
     def run(self):
         _check("vista_run", lib().vista_run(self.h), self.h)
