@@ -5,21 +5,24 @@
  * For every source, row, channel and polarisation the library
  *   1. phase-shifts the visibility to the source position
  *      V' = V exp(+2 pi i nu_k tau / c),  tau = u l + v m + w (sqrt(1-l^2-m^2) - 1)
- *      (paper Eq. 2 with the rotation of Eq. 1 taken as the identity; the sign
- *      makes a point source at (l, m) real),
+ *      (paper Eq. 2; the sign makes a point source at (l, m) real), and grids
+ *      it with the stored baseline, or with the baseline rotated to the
+ *      stacking position (Eq. 1, vista_add_source_reproject),
  *   2. maps the observed channel to the rest frame, nu_rest = nu_obs (1+z)
  *      (Eq. 1's frequency scaling), spreading it over the output bins of a
  *      common rest lattice with the channel-overlap weights of Eqs. 3-4,
  *   3. accumulates sum W w_kj V', sum W w_kj, sum W w_kj |V|^2 and a count into
  *      a cube [nv][nu][nrest][npol] of uv cells x rest channels x pol planes.
+ * vista_regrid_rows() gives the paper's own per-row output (Eq. 3) instead.
  *
  * Conventions shared by every call
  *   - Every call returns VISTA_OK (0) or a negative VISTA_E_* status.  A
  *     failing call leaves the handle as it was.  vista_last_error() gives a
  *     one-line reason.
  *   - A handle is used by one host thread at a time.
- *   - Device work is asynchronous on the stream given at open; only
- *     vista_read_cube(), vista_get_stats() and vista_close() wait for it.
+ *   - Device work is asynchronous on the stream given at open; vista_read_cube(),
+ *     vista_get_stats(), vista_regrid_rows(), vista_close() and a vista_run()
+ *     with host-memory windows wait for it.
  *   - Sizes are element counts, not bytes.
  */
 #ifndef VISTA_H
@@ -31,7 +34,7 @@
 extern "C" {
 #endif
 
-#define VISTA_ABI_VERSION 1
+#define VISTA_ABI_VERSION 2   /* 2: vista_add_source_reproject, vista_regrid_rows */
 #define VISTA_MAX_BINS 4      /* rest bins one input channel may touch */
 #define VISTA_MAX_POL 4
 
