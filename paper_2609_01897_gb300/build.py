@@ -5,6 +5,7 @@ linked into paper_2609_01897_gb300/libvista.so with the CUDA runtime linked
 statically.  The host planner is compiled with -ffp-contract=off so its FP64
 tables are the separately rounded operations the source spells out.
 """
+import fcntl
 import os
 import shutil
 import subprocess
@@ -47,8 +48,21 @@ def up_to_date() -> bool:
 def build(force: bool = False, verbose: bool = False) -> str:
     if not force and up_to_date():
         return LIB
-    nvcc = _nvcc()
     os.makedirs(BUILD, exist_ok=True)
+    # one builder at a time (several ranks of one job may call this at once);
+    # the others find the library up to date once they get the lock
+    with open(os.path.join(BUILD, ".lock"), "w") as lk:
+        fcntl.flock(lk, fcntl.LOCK_EX)
+        try:
+            if not force and up_to_date():
+                return LIB
+            return _build(verbose)
+        finally:
+            fcntl.flock(lk, fcntl.LOCK_UN)
+
+
+def _build(verbose: bool) -> str:
+    nvcc = _nvcc()
     inc = ["-I" + INCLUDE, "-I" + CSRC]
     jobs, objs = [], []
     for f in CU_SOURCES:
