@@ -52,13 +52,19 @@ def build(force: bool = False, verbose: bool = False) -> str:
     # one builder at a time (several ranks of one job may call this at once);
     # the others find the library up to date once they get the lock
     with open(os.path.join(BUILD, ".lock"), "w") as lk:
-        fcntl.flock(lk, fcntl.LOCK_EX)
+        try:
+            fcntl.flock(lk, fcntl.LOCK_EX)
+        except OSError:   # a filesystem without locks: build unserialised
+            pass
         try:
             if not force and up_to_date():
                 return LIB
             return _build(verbose)
         finally:
-            fcntl.flock(lk, fcntl.LOCK_UN)
+            try:
+                fcntl.flock(lk, fcntl.LOCK_UN)
+            except OSError:
+                pass
 
 
 def _build(verbose: bool) -> str:
