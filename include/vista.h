@@ -155,16 +155,27 @@ typedef struct {
 } vista_tuning;
 
 /* Open a cube (zeroed) on the current CUDA device.  Allocates the cube.
+ * Defined by Sec. 3.1 ("Architecture"): before the stacking loop the
+ * pipeline computes one common output grid for all inputs, with the output
+ * channel width the widest rest-frame input channel (rest_df = 0 here) and
+ * the grid centred on central_freq; the cube is this library's form of that
+ * common grid, extended by uv cells (the paper writes one spectral window per
+ * input instead).
  * E_ARG on an invalid descriptor, E_NOMEM / E_CUDA on allocation failure.
  * On failure *out is set to NULL and vista_last_error(NULL) has the reason. */
 int vista_open_stack(const vista_cube_desc *desc, vista_stack **out);
 
-/* Queue one (source, spectral window) for the next vista_run().  Validates
- * every host-visible field (sizes, freqs, l, m, z, pol_map, pointer
- * alignment); the contents of device arrays are not inspected. */
+/* Queue one (source, spectral window) for the next vista_run().  Defined by
+ * Sec. 3.1: each input is listed with its redshift z and sky position, and
+ * the reader materialises its visibilities, flags, UVW coordinates and
+ * per-channel frequencies (the DATA, FLAG, UVW columns and the SPECTRAL_WINDOW
+ * table); here the position is the offset (l, m) of Eq. 2 and WEIGHT rides
+ * along for the weighted sums.  Validates every host-visible field (sizes,
+ * freqs, l, m, z, pol_map, pointer alignment); the contents of device arrays
+ * are not inspected. */
 int vista_add_source(vista_stack *h, const vista_source_desc *src);
 
-/* Queue a window with the full re-projection of Eq. 1 (Sec. 3.3): the
+/* Queue a window with the full re-projection of Eq. 1 (Sec. 3.2): the
  * window's phase centre is (ra0, dec0) and the stacking position (ra1, dec1),
  * radians, in one equatorial frame.  Otherwise as vista_add_source.
  *   - The phase shift of Eq. 2 uses (l, m) = the direction cosines of
@@ -185,7 +196,7 @@ int vista_add_source(vista_stack *h, const vista_source_desc *src);
 int vista_add_source_reproject(vista_stack *h, const vista_source_desc *src, double ra0, double dec0, double ra1,
                                double dec1);
 
-/* The paper's per-row output (Eq. 3, Sec. 3.3): every row of one window
+/* The paper's per-row output (Eq. 3, Sec. 3.2): every row of one window
  * regridded onto the handle's rest lattice, as the rows of an output
  * measurement set (no uv cube).  For row r, output channel j, pol p:
  *   out_vis[r][j][p]  = sum_k V'(r,k,p) w_kj / sum_k w_kj   (complex64 as
@@ -206,14 +217,21 @@ int vista_regrid_rows(vista_stack *h, const vista_source_desc *src, float *out_v
                       double *out_uvw);
 
 /* Stack every queued source into the cube (additive across runs) and clear
- * the queue.  Host planning happens here; device work is queued on the
+ * the queue.  Defined by Sec. 3.2 ("C++/OpenMP Kernel"): per row and channel
+ * the phase shift of Eq. 2, the rest-frame mapping of Eq. 1 and the
+ * channel-overlap weights of Eqs. 3-4; all queued windows go to the device
+ * together, as the N_batch measurement sets of one launch in Sec. 3.3 ("GPU
+ * Acceleration").  Host planning happens here; device work is queued on the
  * stream and the call returns without waiting for it (except that host-memory
  * sources are copied before it returns).  E_STATE if nothing is queued,
  * E_RANGE if a channel would touch more than VISTA_MAX_BINS rest bins. */
 int vista_run(vista_stack *h);
 
-/* Wait for the stream, then copy the cube out.  Any pointer may be NULL to
- * skip that array.  Layout [nv][nu][nrest][npol] (sum_wv with a trailing
+/* Wait for the stream, then copy the cube out.  The arrays are the two
+ * sums of Eq. 3 per cube entry (numerator sum W w_kj V', denominator
+ * sum W w_kj; their ratio is Eq. 3's V_out for that uv cell), with
+ * sum W w_kj |V|^2 and the count of contributions beside them; normalising
+ * is the caller's.  Any pointer may be NULL to skip that array.  Layout [nv][nu][nrest][npol] (sum_wv with a trailing
  * [2] = re, im).  dst_is_device: 1 = device pointers, 0 = host.  Returns
  * E_TIMEOUT if a device-side wait of an earlier run gave up. */
 int vista_read_cube(vista_stack *h, float *sum_wv, float *sum_w, float *sum_wvv,
@@ -239,7 +257,7 @@ int vista_get_tuning(vista_stack *h, vista_tuning *t);
 
 /* Per-phase device time of vista_run(), measured with CUDA events recorded
  * on the handle's stream around each phase (the paper's compute_s timer,
- * Sec. 4.2, split by kernel).  Accumulated over runs while enabled. */
+ * Sec. 4.3, split by kernel).  Accumulated over runs while enabled. */
 typedef struct {
     double prepass_ms;   /* FP64 per-row pre-pass (and row ordering) kernels */
     double stack_ms;     /* the stacking kernel(s) */
@@ -279,11 +297,13 @@ int vista_enable_graphs(vista_stack *h, int on);
 int vista_graph_runs(vista_stack *h, uint64_t *out);
 
 /* Wait for the stream, free every device and host resource, and forget the
- * handle; any later call with it returns E_STATE. */
+ * handle; any later call with it returns E_STATE.  A library convention (the
+ * paper has no counterpart). */
 int vista_close(vista_stack *h);
 
 /* One-line reason for the last failure on h (NULL: the calling thread's last
- * failure without a handle).  Valid until the next call on the same handle. */
+ * failure without a handle).  Valid until the next call on the same handle.
+ * A library convention (the paper has no counterpart). */
 const char *vista_last_error(const vista_stack *h);
 
 int vista_abi_version(void);
@@ -337,8 +357,11 @@ int vista_debug_order(vista_stack *h, int32_t src, int32_t *dst);
  *           the caller's), precision must be VISTA_PREC_MIXED; stream used.
  *   src     one window, device memory (mem = VISTA_MEM_DEVICE).
  *   cube4   caller's device array [nv][nu][nrest][npol][4] float:
- *           (sum W V'.re, sum W V'.im, sum W, sum W |V|^2), added to.
- *   count   caller's device array [nv][nu][nrest][npol] uint32, added to.
+ *           (sum W V'.re, sum W V'.im, sum W, sum W |V|^2), added to;
+ *           16-byte aligned.
+ *   count   caller's device array [nv][nu][nrest][npol] uint32, added to;
+ *           8-byte aligned.
+ *   A misaligned cube4 or count gives E_ARG before any device work.
  *
  * Returns after the work has finished.  E_RANGE when the window needs more
  * scratch than the array holds: about 52 bytes per row (a 32-byte row

@@ -60,6 +60,11 @@ extern "C" int vista_stack_noalloc(const vista_cube_desc *c, const vista_source_
                                    uint32_t *count)
 {
     if (!c || !s || !cube4 || !count) return fail(nullptr, VISTA_E_ARG, "null argument");
+    // the stacking kernel adds to the cube with 16-byte vector reductions and,
+    // for a pol pair on an even plane pair, to the counts with 8-byte ones:
+    // reject pointers those would fault on, before any device work
+    if ((uintptr_t)cube4 % 16) return fail(nullptr, VISTA_E_ARG, "cube4 must be 16-byte aligned");
+    if ((uintptr_t)count % 8) return fail(nullptr, VISTA_E_ARG, "count must be 8-byte aligned");
     if (c->nu < 2 || c->nv < 2 || (c->nu & 1) || (c->nv & 1) || c->nrest < 1 || c->npol < 1 ||
         c->npol > VISTA_MAX_POL)
         return fail(nullptr, VISTA_E_ARG, "bad cube shape");

@@ -127,3 +127,18 @@ def test_plan_channels_range_error(V):
     with pytest.raises(V.VistaError) as ei:
         V.plan_channels(np.array([100.0, 200.0, 300.0]), 0.0, 0.0, 1.0, 1000, 0)
     assert ei.value.code == V.E_RANGE
+
+
+def test_noalloc_rejects_misaligned_outputs_without_gpu(V):
+    """The no-allocation call checks the caller's cube and count pointers
+    before any device work: a cube not on a 16-byte boundary or counts not on
+    an 8-byte boundary give E_ARG (the pointers are never dereferenced)."""
+    L = V.lib()
+    d = V.CubeDesc(8, 8, 4, 2, 1.0, 1.0, 1e9, 1e6, 0.0, V.BIN_OVERLAP, V.PREC_MIXED, 0, 0, None)
+    f = np.array([1e9, 1.001e9])
+    s = V.SourceDesc(1, 2, 2, 0x1000, f.ctypes.data, 0x2000, V.VIS_C64, 1.0, 0x3000, None, None,
+                     0.0, 0.0, 0.0, V.MEM_DEVICE, 0)
+    for cube4, count, what in ((0x10008, 0x20000, "cube4"), (0x10004, 0x20000, "cube4"),
+                               (0x10000, 0x20004, "count"), (0x10000, 0x20002, "count")):
+        assert L.vista_stack_noalloc(C.byref(d), C.byref(s), cube4, count) == V.E_ARG
+        assert what in V.last_error(None)

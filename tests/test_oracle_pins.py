@@ -325,9 +325,10 @@ def test_p6_brute_force(oracle_mod, fold, mode):
     df = 31.25e6 * (1 + z) * 1.3
     f0 = freqs[0] * (1 + z) - 6.5 * df
     cube = oracle_mod.make_cube(N, N, nrest, npol, du, du, f0, df, mode, fold)
-    out = oracle_mod.stack(cube, [src])
+    out = oracle_mod.stack(cube, [src], with_abs=True)
     exp = np.zeros((N, N, nrest, npol), dtype=np.complex128)
     expw = np.zeros((N, N, nrest, npol))
+    expa = np.zeros((N, N, nrest, npol))
     expc = np.zeros((N, N, nrest, npol), dtype=np.int64)
     n1 = math.sqrt(1 - l0 ** 2 - m0 ** 2) - 1
     widths = [freqs[1] - freqs[0]] + [(freqs[k + 1] - freqs[k - 1]) / 2 for k in range(1, nchan - 1)] + [freqs[-1] - freqs[-2]]
@@ -359,10 +360,62 @@ def test_p6_brute_force(oracle_mod, fold, mode):
                     if wk > 0:
                         exp[iv, iu, j, p] += wts[r, p] * wk * Vs
                         expw[iv, iu, j, p] += wts[r, p] * wk
+                        expa[iv, iu, j, p] += wts[r, p] * wk * abs(vis[r, k, p])
                         expc[iv, iu, j, p] += 1
     np.testing.assert_array_equal(out["count"].astype(np.int64), expc)
     np.testing.assert_allclose(out["sum_w"], expw, rtol=1e-12, atol=1e-12)
     np.testing.assert_allclose(out["sum_wv"], exp, rtol=1e-9, atol=1e-9)
+    # the scale of the sum_wv parity bound: sum of W w_kj |V| (|V'| = |V|)
+    np.testing.assert_allclose(out["sum_wabs"], expa, rtol=1e-12, atol=1e-12)
+    assert (out["sum_wabs"] >= np.abs(out["sum_wv"]) * (1 - 1e-12)).all()
+    assert (out["sum_wabs"] > 0).sum() == (expc > 0).sum()
+
+
+# ----------------------------------------------------------------- sampled planes
+
+@pytest.mark.parametrize("fold", [0, 1])
+@pytest.mark.parametrize("nthreads", [1, 3])
+def test_iv_select_equals_full_cube_planes(oracle_mod, fold, nthreads):
+    """Sampled mode (iv_select) accumulates exactly the chosen iv planes of the
+    full cube: the same values bit for bit, in increasing iv, and nothing of
+    the other planes.  The channel axis spans a 40 % fractional band, so a
+    row's cell moves by several iv planes across its channels and many rows
+    straddle a selected and an unselected plane."""
+    rng = np.random.default_rng(77 + fold + 10 * nthreads)
+    nchan, npol, N, nrest = 24, 2, 16, 20
+    freqs = 100e9 + 1.75e9 * np.arange(nchan)
+    srcs = []
+    for s in range(3):
+        nrow = 30
+        uvw = _uvw(nrow, rng, 40.0)
+        vis = rng.normal(size=(nrow, nchan, npol)) + 1j * rng.normal(size=(nrow, nchan, npol))
+        wts = rng.uniform(0.5, 2.0, size=(nrow, npol)).astype(np.float32)
+        flags = (rng.random((nrow, nchan, npol)) < 0.1).astype(np.uint8)
+        srcs.append(_src(oracle_mod, uvw, freqs, vis, 3 * ARCSEC * s, -2 * ARCSEC, 0.3 + 0.1 * s, wts, flags))
+    du = 2 * 1.01 * 40.0 * freqs.max() / C / N
+    f0, df = oracle_mod.auto_lattice([freqs] * 3, [0.3, 0.4, 0.5], nrest, 140e9 * 1.4)
+    cube = oracle_mod.make_cube(N, N, nrest, npol, du, du, f0, df, 0, fold)
+    full = oracle_mod.stack(cube, srcs, nthreads=nthreads, with_abs=True)
+    sel = [1, 4, 5, 8, 13]
+    part = oracle_mod.stack(cube, srcs, iv_select=sel, nthreads=nthreads, with_abs=True)
+    np.testing.assert_array_equal(part["planes"], sel)
+    for k in ("sum_wv", "sum_w", "sum_wvv", "sum_wabs", "count"):
+        assert part[k].shape[0] == len(sel)
+        np.testing.assert_array_equal(part[k], full[k][sel])   # bit for bit
+    assert part["count"].sum() > 0 and part["count"].sum() < full["count"].sum()
+    # the sample has teeth: some rows put channels both in and out of the
+    # selected planes
+    straddle = 0
+    gv = 1.0 / (C * du)
+    for sc in srcs:
+        for r in range(sc.uvw.shape[0]):
+            v = sc.uvw[r, 1]
+            u = sc.uvw[r, 0]
+            if fold and (v < 0 or (v == 0 and u < 0)):
+                v = -v
+            ivs = {math.floor(v * (f * gv)) + N // 2 for f in freqs}
+            straddle += bool(ivs & set(sel)) and bool(ivs - set(sel))
+    assert straddle >= 10
 
 
 # ----------------------------------------------------------------- Hermitian fold
