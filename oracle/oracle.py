@@ -154,8 +154,9 @@ def regrid_rows(src, rest_f0, rest_df, nrest, bin_mode=0):
     vis = src.vis.astype(np.complex128) * phasors(src)[..., None]
     w = rest_weights(src.freqs, src.c.z, rest_f0, rest_df, nrest, bin_mode)     # [nchan, nrest]
     ok = np.ones(vis.shape, dtype=np.float64) if src.flags is None else (src.flags == 0).astype(np.float64)
-    num = np.einsum("rkp,kj->rjp", vis * ok, w)
-    den = np.einsum("rkp,kj->rjp", ok, w)
+    # [r, p, k] @ [k, j] -> [r, p, j] -> [r, j, p]
+    num = np.moveaxis(np.matmul(np.moveaxis(vis * ok, 2, 1), w), 1, 2)
+    den = np.moveaxis(np.matmul(np.moveaxis(ok, 2, 1), w), 1, 2)
     out = np.zeros_like(num)
     nz = den > 0
     out[nz] = num[nz] / den[nz]
