@@ -1,8 +1,9 @@
 """Build libvista.so in-tree for sm_103a.
 
-Three translation units compiled in parallel (two CUDA, one host C++), then
-linked into paper_2609_01897_gb300/libvista.so with the CUDA runtime linked
-statically.  The host planner is compiled with -ffp-contract=off so its FP64
+The translation units are compiled in parallel (the CUDA sources, with the
+stacking kernel's instantiations split by visibility type, and one host C++
+file), then linked into paper_2609_01897_gb300/libvista.so with the CUDA
+runtime linked statically.  The host planner is compiled with -ffp-contract=off so its FP64
 tables are the separately rounded operations the source spells out.
 """
 import fcntl
@@ -19,8 +20,9 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libvista.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-CU_SOURCES = ["vista_stack.cu", "vista_kernels.cu", "vista_order.cu", "vista_run.cu", "vista_api.cu", "vista_regrid.cu",
-              "vista_noalloc.cu", "vista_autotune.cu"]
+CU_SOURCES = ["vista_stack_c64.cu", "vista_stack_c128.cu", "vista_stack_f16.cu", "vista_stack_bf16.cu",
+              "vista_stack.cu", "vista_kernels.cu", "vista_order.cu", "vista_run.cu", "vista_api.cu", "vista_regrid.cu",
+              "vista_noalloc.cu", "vista_autotune.cu", "vista_contsub.cu"]
 CXX_SOURCES = ["planner.cpp"]
 
 
