@@ -21,8 +21,8 @@
  *     one-line reason.
  *   - A handle is used by one host thread at a time.
  *   - Device work is asynchronous on the stream given at open; vista_read_cube(),
- *     vista_get_stats(), vista_regrid_rows(), vista_close() and a vista_run()
- *     with host-memory windows wait for it.
+ *     vista_get_stats(), vista_regrid_rows(), vista_contsub() and
+ *     vista_close() wait for it.
  *   - Sizes are element counts, not bytes.
  */
 #ifndef VISTA_H
@@ -34,7 +34,8 @@
 extern "C" {
 #endif
 
-#define VISTA_ABI_VERSION 2   /* 2: vista_add_source_reproject, vista_regrid_rows */
+#define VISTA_ABI_VERSION 3   /* 2: vista_add_source_reproject, vista_regrid_rows;
+                                 3: vista_contsub, vista_set_wave_bytes, vista_get_waves */
 #define VISTA_MAX_BINS 4      /* rest bins one input channel may touch */
 #define VISTA_MAX_POL 4
 
@@ -71,9 +72,10 @@ typedef struct vista_stack vista_stack;   /* opaque handle */
  *   precision  VISTA_PREC_MIXED: FP64 geometry and tables (the delay of
  *              each row kept as a float-float pair), FP32 per-visibility
  *              body, an FP32 cube whose entries are moved into an FP64 master
- *              cube at periodic checkpoints (so the sums stay within ~1e-6
- *              relative at any stack depth); VISTA_PREC_FP64: the plain
- *              form, FP64 throughout with an FP64 cube.
+ *              cube at checkpoints spread over the drains (measured within
+ *              ~7e-6 relative on the deepest entries of a 3.8e11-visibility
+ *              stack); VISTA_PREC_FP64: the plain form, FP64 throughout with
+ *              an FP64 cube.
  *   hermitian_fold  1: rows with v < 0 (or v == 0, u < 0) are negated and
  *              their shifted visibility conjugated before binning.
  *   stream     cudaStream_t for all device work (NULL = legacy default stream). */
@@ -110,8 +112,11 @@ typedef struct {
  *              work of the vista_run() that consumes them has completed.
  *              VISTA_MEM_HOST: they are host pointers (pinned memory gives
  *              asynchronous copies); vista_run() copies them to device
- *              buffers owned by the handle, and they must stay valid until
- *              vista_run() returns. */
+ *              buffers owned by the handle, in waves that overlap the
+ *              stacking of the wave before, and returns without waiting:
+ *              they must stay valid and unchanged until the run's stream
+ *              work has completed (vista_read_cube(), vista_get_stats() or a
+ *              stream synchronize). */
 typedef struct {
     int64_t nrow;
     int32_t nchan, npol;
@@ -222,18 +227,31 @@ int vista_regrid_rows(vista_stack *h, const vista_source_desc *src, float *out_v
  * channel-overlap weights of Eqs. 3-4; all queued windows go to the device
  * together, as the N_batch measurement sets of one launch in Sec. 3.3 ("GPU
  * Acceleration").  Host planning happens here; device work is queued on the
- * stream and the call returns without waiting for it (except that host-memory
- * sources are copied before it returns).  E_STATE if nothing is queued,
+ * stream and the call returns without waiting for it.  Host-memory windows
+ * stream through two device staging slots in waves of about a quarter of
+ * their bytes (64 MB to 2 GB): the copies of one wave, on four copy streams,
+ * run while the wave before is stacked (the paper's read -> compute overlap,
+ * Sec. 3.1 and 3.3).  E_STATE if nothing is queued,
  * E_RANGE if a channel would touch more than VISTA_MAX_BINS rest bins. */
 int vista_run(vista_stack *h);
+
+/* Staged bytes per wave of host-memory windows (vista_run()): 0 = the
+ * library's rule (about a quarter of the run's host bytes, 64 MB to 2 GB);
+ * smaller waves overlap more finely, each costs a round of kernel launches.
+ * A window is never split: a window larger than the budget is a wave. */
+int vista_set_wave_bytes(vista_stack *h, int64_t bytes);
+/* The number of waves the last vista_run() streamed its host-memory windows
+ * in (0: it had none). */
+int vista_get_waves(vista_stack *h, int32_t *out);
 
 /* Wait for the stream, then copy the cube out.  The arrays are the two
  * sums of Eq. 3 per cube entry (numerator sum W w_kj V', denominator
  * sum W w_kj; their ratio is Eq. 3's V_out for that uv cell), with
  * sum W w_kj |V|^2 and the count of contributions beside them; normalising
- * is the caller's.  Any pointer may be NULL to skip that array.  Layout [nv][nu][nrest][npol] (sum_wv with a trailing
- * [2] = re, im).  dst_is_device: 1 = device pointers, 0 = host.  Returns
- * E_TIMEOUT if a device-side wait of an earlier run gave up. */
+ * is the caller's.  Any pointer may be NULL to skip that array.  Layout
+ * [nv][nu][nrest][npol] (sum_wv with a trailing [2] = re, im).
+ * dst_is_device: 1 = device pointers, 0 = host.  Returns E_TIMEOUT if a
+ * device-side wait of an earlier run gave up. */
 int vista_read_cube(vista_stack *h, float *sum_wv, float *sum_w, float *sum_wvv,
                     uint32_t *count, int dst_is_device);
 
@@ -295,6 +313,28 @@ int vista_autotune(vista_stack *h, int32_t budget, int32_t reps, vista_tuning *b
 int vista_enable_graphs(vista_stack *h, int on);
 /* Number of runs replayed from a graph since the handle was opened. */
 int vista_graph_runs(vista_stack *h, uint64_t *out);
+
+/* Continuum subtraction over the rest axis (Sec. 3.4, "Post-processing":
+ * the paper's first post-processing step, done there by CASA on the output
+ * measurement set).  Waits for the stream, then for every uv cell and cube
+ * plane fits a polynomial of degree d = min(order, |F| - 1) in the rest-channel
+ * abscissa x_j = (2 j - (nrest - 1)) / nrest to the cell's spectrum
+ * V_j = sum_wv_j / sum_w_j by weighted least squares (weights sum_w_j) over
+ * F = { j : line_free[j] != 0 and sum_w_j > 0 }, and writes
+ *   sum_wv_out[..][j][..] = sum_wv_j - sum_w_j p(x_j)
+ * for every channel (no fit, and so no change, when F is empty).  The output
+ * is again a sum (divide by sum_w for the continuum-subtracted spectrum);
+ * sum_w, sum_w|V|^2 and the counts are unchanged and come from
+ * vista_read_cube().  The cube itself is not modified.
+ *   line_free   HOST [nrest] uint8, nonzero = free of line emission.
+ *   order       0..3.
+ *   sum_wv_out  [nv][nu][nrest][npol][2] float32 (re, im); device memory if
+ *               dst_is_device, else host memory.
+ * FP64 fit (moments reduced over each cell's channels, Cholesky solve).
+ * E_ARG: null pointers or an order outside 0..3; E_TIMEOUT as
+ * vista_read_cube(). */
+int vista_contsub(vista_stack *h, const uint8_t *line_free, int32_t order, float *sum_wv_out,
+                  int dst_is_device);
 
 /* Wait for the stream, free every device and host resource, and forget the
  * handle; any later call with it returns E_STATE.  A library convention (the

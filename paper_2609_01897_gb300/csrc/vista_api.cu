@@ -70,6 +70,12 @@ int cuda_fail(vista_stack *h, cudaError_t e, const char *what)
                 cudaGetErrorString(e));
 }
 
+int device_fail(vista_stack *h, int32_t code)
+{
+    if (code == 1) return fail(h, VISTA_E_TIMEOUT, "a device-side wait gave up (code 1)");
+    return fail(h, VISTA_E_STATE, "a device-side check failed (code %d)", code);
+}
+
 static cudaEvent_t take_event(vista_stack *h)
 {
     if (!h->ev_pool.empty()) {
@@ -212,6 +218,7 @@ extern "C" int vista_open_stack(const vista_cube_desc *d, vista_stack **out)
     if (e != cudaSuccess) {
         const int rc = cuda_fail(nullptr, e, "cube allocation");
         cudaFree(h->cube);
+        cudaFree(h->cube_master);
         cudaFree(h->count);
         cudaFree(h->stats);
         cudaFree(h->err);
@@ -357,7 +364,7 @@ int read_common(vista_stack *h, void *sum_wv, void *sum_w, void *sum_wvv, uint32
     int32_t err = 0;
     e = cudaMemcpy(&err, h->err, sizeof err, cudaMemcpyDeviceToHost);
     if (e != cudaSuccess) return cuda_fail(h, e, "error word read");
-    if (err != 0) return fail(h, VISTA_E_TIMEOUT, "a device-side wait or check gave up (code %d)", err);
+    if (err != 0) return device_fail(h, err);
     const int fp64 = h->desc.precision == VISTA_PREC_FP64;
     const int64_t n = h->nentries;
     const size_t fe = out_f64 ? 8 : 4;
@@ -405,6 +412,22 @@ extern "C" int vista_read_cube_f64(vista_stack *h, double *sum_wv, double *sum_w
 {
     CHECK_HANDLE(h);
     return read_common(h, sum_wv, sum_w, sum_wvv, count, dst_is_device, 1);
+}
+
+extern "C" int vista_set_wave_bytes(vista_stack *h, int64_t bytes)
+{
+    CHECK_HANDLE(h);
+    if (bytes < 0) return fail(h, VISTA_E_ARG, "wave bytes must be >= 0");
+    h->wave_bytes = bytes;
+    return VISTA_OK;
+}
+
+extern "C" int vista_get_waves(vista_stack *h, int32_t *out)
+{
+    CHECK_HANDLE(h);
+    if (!out) return fail(h, VISTA_E_ARG, "null output");
+    *out = h->nwaves;
+    return VISTA_OK;
 }
 
 extern "C" int vista_zero_cube(vista_stack *h)
@@ -568,6 +591,8 @@ extern "C" int vista_close(vista_stack *h)
         }
     for (int j = 0; j <= NXFER; ++j)
         if (h->xfer_ev[j]) cudaEventDestroy(h->xfer_ev[j]);
+    for (int j = 0; j < 2; ++j)
+        if (h->slot_ev[j]) cudaEventDestroy(h->slot_ev[j]);
     cudaFree(h->cube);
     cudaFree(h->cube_master);
     cudaFree(h->count);
@@ -585,6 +610,7 @@ extern "C" int vista_close(vista_stack *h)
     h->b_rot.release();
     h->b_guvw.release();
     h->b_regrid.release();
+    h->b_contsub.release();
     delete h;
     return VISTA_OK;
 }

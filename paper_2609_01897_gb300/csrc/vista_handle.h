@@ -53,10 +53,22 @@ struct Copy2D {
     size_t spitch, width, height;
 };
 
+// A host-to-device copy of a host-memory window's array (whole rows as one
+// copy when the pitches allow, else a 2-D copy), into the staging slot of
+// its wave.
+struct HostCopy {
+    int wave;
+    void *dst;
+    size_t dpitch;
+    const void *src;
+    size_t spitch, width, height;
+};
+
 // One launch class of a run: windows that share the kernel instantiation.
 struct ClassRun {
     int key = 0;                    // mixed: (vis_type << 16) | (NS << 8) | npol
     int ns = 1;
+    int wave = 0;                   // host-memory runs: the wave of windows the class belongs to
     RunArgs args{};
     std::vector<int> members;       // run-order index of each window
 };
@@ -82,9 +94,14 @@ struct vista_stack {
     vista::DevStats *stats = nullptr;
     uint64_t host_nvis = 0;   // visibilities read, counted from the channel tables at each run
     int32_t *err = nullptr;
-    vista::DevBuf b_srcs, b_chf, b_chd, b_recs, b_cells, b_off, b_stage, b_unpack, b_sort, b_rot, b_guvw, b_regrid;
+    vista::DevBuf b_srcs, b_chf, b_chd, b_recs, b_cells, b_off, b_stage, b_unpack, b_sort, b_rot, b_guvw, b_regrid,
+        b_contsub;
     std::vector<vista::ClassRun> classes;
     std::vector<vista::Copy2D> copies;   // device copies of the last planned run
+    std::vector<vista::HostCopy> hcopies;   // host-memory windows of the last run, by wave
+    int nwaves = 0;                      // waves of host-memory windows of the last run (0: none)
+    int64_t wave_bytes = 0;              // staged bytes per wave (0: the library's rule)
+    cudaEvent_t slot_ev[2] = {};         // a staging slot's wave has been stacked
     vista::LaunchCfg cfg{48, 1, 4, 1, 4};
     // CUDA-graph replay of the device pass while the source set is unchanged
     bool graphs = true;
@@ -112,6 +129,9 @@ namespace vista {
 bool handle_live(const vista_stack *h);
 int fail(vista_stack *h, int code, const char *fmt, ...) __attribute__((format(printf, 3, 4)));
 int cuda_fail(vista_stack *h, cudaError_t e, const char *what);
+// A nonzero device error word as a status: 1 a bounded wait gave up
+// (E_TIMEOUT), other codes an internal sizing check (E_STATE).
+int device_fail(vista_stack *h, int32_t code);
 int span_begin(vista_stack *h, int kind);
 void span_end(vista_stack *h, int id);
 size_t vis_elem_bytes(int vt);

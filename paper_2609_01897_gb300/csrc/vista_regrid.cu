@@ -1,9 +1,13 @@
 // The paper's per-row output (Eq. 3): every row of one window regridded onto
 // the rest lattice, V_out(j) = sum_k V'(k) w_kj / sum_k w_kj over unflagged
 // channels, with V' the shifted visibility of Eq. 2 and w_kj the Eq. 4
-// weights.  Not the stacking hot path: one FP64 thread per (row, output
-// channel), the contributing channels of each output channel listed on the
-// host (a compressed row table built from the FP64 planner's bins).
+// weights.  The contributing channels of each output channel are listed on
+// the host (a compressed row table built from the FP64 planner's bins).  A
+// first kernel forms each row's delay in FP64 and keeps it as a float-float
+// pair; then one thread per (row, output channel) forms each contributor's
+// phasor as the stacking kernel does (float-float product tau nu_k / c,
+// reduced mod 1 turn, __sincosf: below 5e-7 rad) and sums in FP32 (a few
+// terms per output channel).
 #include <cmath>
 #include <vector>
 
@@ -11,6 +15,7 @@
 #include <cuda_fp16.h>
 
 #include "planner.h"
+#include "vista_device.cuh"
 #include "vista_handle.h"
 
 namespace vista {
@@ -20,10 +25,11 @@ struct RegridArgs {
     const double *uvw;
     const void *vis;
     const uint8_t *flags;
-    const double *freq;     // [nchan] Hz
+    const float2 *nuc;      // [nchan] nu_k / c as a float-float pair (1/m)
     const int32_t *start;   // [nrest + 1] first contributor of each output channel
     const int32_t *chan;    // contributing channel
-    const double *w;        // its Eq. 4 weight
+    const float *w;         // its Eq. 4 weight
+    float2 *tau;            // [nrow] the row's delay (m) as a float-float pair
     float *out_vis;         // [nrow][nrest][npol][2]
     float *out_wsum;        // [nrow][nrest][npol]
     double *out_uvw;        // [nrow][3] or null
@@ -33,23 +39,37 @@ struct RegridArgs {
     double l, m, n1, inv_zf;
 };
 
-__device__ __forceinline__ double2 load_vis(const RegridArgs &a, int64_t i)
+__device__ __forceinline__ float2 load_vis(const RegridArgs &a, int64_t i)
 {
     switch (a.vis_type) {
-    case VISTA_VIS_C128: return reinterpret_cast<const double2 *>(a.vis)[i];
-    case VISTA_VIS_C64: {
-        const float2 v = reinterpret_cast<const float2 *>(a.vis)[i];
-        return make_double2(v.x, v.y);
+    case VISTA_VIS_C128: {
+        const double2 v = reinterpret_cast<const double2 *>(a.vis)[i];
+        return make_float2((float)v.x, (float)v.y);
     }
+    case VISTA_VIS_C64: return reinterpret_cast<const float2 *>(a.vis)[i];
     case VISTA_VIS_F16X2: {
         const __half2 v = reinterpret_cast<const __half2 *>(a.vis)[i];
-        return make_double2((double)__low2float(v) * a.vis_scale, (double)__high2float(v) * a.vis_scale);
+        return make_float2(__low2float(v) * a.vis_scale, __high2float(v) * a.vis_scale);
     }
     default: {
         const __nv_bfloat162 v = reinterpret_cast<const __nv_bfloat162 *>(a.vis)[i];
-        return make_double2((double)__low2float(v) * a.vis_scale, (double)__high2float(v) * a.vis_scale);
+        return make_float2(__low2float(v) * a.vis_scale, __high2float(v) * a.vis_scale);
     }
     }
+}
+
+// One thread per row: the Eq. 2 delay in FP64, kept as a float-float pair,
+// and the rest-frame baseline (Eq. 1 with R = I) if asked for.
+__global__ void __launch_bounds__(256) k_regrid_tau(RegridArgs a)
+{
+    const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= a.nrow) return;
+    const double *x = a.uvw + 3 * r;
+    float hi, lo;
+    split_ff(x[0] * a.l + x[1] * a.m + x[2] * a.n1, hi, lo);
+    a.tau[r] = make_float2(hi, lo);
+    if (a.out_uvw)
+        for (int c = 0; c < 3; ++c) a.out_uvw[3 * r + c] = x[c] * a.inv_zf;
 }
 
 __global__ void __launch_bounds__(256) k_regrid(RegridArgs a)
@@ -58,35 +78,31 @@ __global__ void __launch_bounds__(256) k_regrid(RegridArgs a)
     if (t >= a.nrow * a.nrest) return;
     const int64_t r = t / a.nrest;
     const int j = (int)(t - r * a.nrest);
-    const double *x = a.uvw + 3 * r;
-    const double tau = x[0] * a.l + x[1] * a.m + x[2] * a.n1;   // Eq. 2 delay, metres
-    double sr[4] = {0, 0, 0, 0}, si[4] = {0, 0, 0, 0}, sw[4] = {0, 0, 0, 0};
+    const float2 tau = a.tau[r];
+    float sr[4] = {0, 0, 0, 0}, si[4] = {0, 0, 0, 0}, sw[4] = {0, 0, 0, 0};
     for (int e = a.start[j]; e < a.start[j + 1]; ++e) {
         const int k = a.chan[e];
-        const double w = a.w[e];
-        const double turns = tau * a.freq[k] / C_LIGHT;
-        double s, c;
-        sincospi(2.0 * (turns - floor(turns)), &s, &c);
+        const float w = a.w[e];
+        const float2 nuc = a.nuc[k];
+        const float2 ph = shift_phasor(tau.x, tau.y, nuc.x, nuc.y);
 #pragma unroll
         for (int p = 0; p < 4; ++p) {
             if (p >= a.npol) break;
             const int64_t i = (r * a.nchan + k) * a.npol + p;
             if (a.flags && a.flags[i]) continue;
-            const double2 v = load_vis(a, i);
-            sr[p] += w * (v.x * c - v.y * s);
-            si[p] += w * (v.x * s + v.y * c);
+            const float2 v = load_vis(a, i);
+            sr[p] = __fmaf_rn(w, v.x * ph.x - v.y * ph.y, sr[p]);
+            si[p] = __fmaf_rn(w, v.x * ph.y + v.y * ph.x, si[p]);
             sw[p] += w;
         }
     }
     for (int p = 0; p < a.npol; ++p) {
         const int64_t o = (r * a.nrest + j) * a.npol + p;
-        const bool any = sw[p] > 0.0;
-        a.out_vis[2 * o] = any ? (float)(sr[p] / sw[p]) : 0.0f;
-        a.out_vis[2 * o + 1] = any ? (float)(si[p] / sw[p]) : 0.0f;
-        a.out_wsum[o] = (float)sw[p];
+        const bool any = sw[p] > 0.0f;
+        a.out_vis[2 * o] = any ? sr[p] / sw[p] : 0.0f;
+        a.out_vis[2 * o + 1] = any ? si[p] / sw[p] : 0.0f;
+        a.out_wsum[o] = sw[p];
     }
-    if (a.out_uvw && j == 0)
-        for (int c = 0; c < 3; ++c) a.out_uvw[3 * r + c] = x[c] * a.inv_zf;   // Eq. 1 with R = I
 }
 
 }  // namespace
@@ -133,38 +149,48 @@ extern "C" int vista_regrid_rows(vista_stack *h, const vista_source_desc *s, flo
     for (int32_t j = 0; j < nrest; ++j) start[(size_t)j + 1] += start[(size_t)j];
     const size_t nnz = (size_t)start[(size_t)nrest];
     std::vector<int32_t> chan(nnz > 0 ? nnz : 1), fill(start.begin(), start.end() - 1);
-    std::vector<double> w(nnz > 0 ? nnz : 1);
+    std::vector<float> w(nnz > 0 ? nnz : 1);
     for (int32_t k = 0; k < n; ++k)
         for (int b = 0; b < nb[(size_t)k]; ++b) {
             const int32_t e = fill[(size_t)j0[(size_t)k] + b]++;
             chan[(size_t)e] = k;
-            w[(size_t)e] = wk[(size_t)k * VISTA_MAX_BINS + b];
+            w[(size_t)e] = (float)wk[(size_t)k * VISTA_MAX_BINS + b];
         }
 
-    // one device table: freqs | start | chan | w
+    // nu_k / c of every channel as a float-float pair
+    std::vector<float2> nuc((size_t)n);
+    for (int32_t k = 0; k < n; ++k) {
+        const double x = s->freqs[k] / C_LIGHT;
+        nuc[(size_t)k].x = (float)x;
+        nuc[(size_t)k].y = (float)(x - (double)nuc[(size_t)k].x);
+    }
+
+    // one device buffer: nu/c | start | chan | w | per-row delays
     auto al = [](size_t b) { return (b + 255) / 256 * 256; };
-    const size_t o_f = 0, o_s = al(sizeof(double) * (size_t)n), o_c = o_s + al(sizeof(int32_t) * start.size()),
-                 o_w = o_c + al(sizeof(int32_t) * chan.size()), total = o_w + al(sizeof(double) * w.size());
+    const size_t o_f = 0, o_s = al(sizeof(float2) * (size_t)n), o_c = o_s + al(sizeof(int32_t) * start.size()),
+                 o_w = o_c + al(sizeof(int32_t) * chan.size()), o_t = o_w + al(sizeof(float) * w.size()),
+                 total = o_t + al(sizeof(float2) * (size_t)s->nrow);
     cudaError_t e = h->b_regrid.ensure(total);
     if (e != cudaSuccess) return cuda_fail(h, e, "regrid table allocation");
     char *b = (char *)h->b_regrid.p;
-    e = cudaMemcpyAsync(b + o_f, s->freqs, sizeof(double) * (size_t)n, cudaMemcpyHostToDevice, h->stream);
+    e = cudaMemcpyAsync(b + o_f, nuc.data(), sizeof(float2) * (size_t)n, cudaMemcpyHostToDevice, h->stream);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(b + o_s, start.data(), sizeof(int32_t) * start.size(), cudaMemcpyHostToDevice, h->stream);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(b + o_c, chan.data(), sizeof(int32_t) * chan.size(), cudaMemcpyHostToDevice, h->stream);
     if (e == cudaSuccess)
-        e = cudaMemcpyAsync(b + o_w, w.data(), sizeof(double) * w.size(), cudaMemcpyHostToDevice, h->stream);
+        e = cudaMemcpyAsync(b + o_w, w.data(), sizeof(float) * w.size(), cudaMemcpyHostToDevice, h->stream);
     if (e != cudaSuccess) return cuda_fail(h, e, "regrid table upload");
 
     RegridArgs a{};
     a.uvw = s->uvw;
     a.vis = s->vis;
     a.flags = s->flags;
-    a.freq = (const double *)(b + o_f);
+    a.nuc = (const float2 *)(b + o_f);
     a.start = (const int32_t *)(b + o_s);
     a.chan = (const int32_t *)(b + o_c);
-    a.w = (const double *)(b + o_w);
+    a.w = (const float *)(b + o_w);
+    a.tau = (float2 *)(b + o_t);
     a.out_vis = out_vis;
     a.out_wsum = out_wsum;
     a.out_uvw = out_uvw;
@@ -179,8 +205,10 @@ extern "C" int vista_regrid_rows(vista_stack *h, const vista_source_desc *s, flo
     a.n1 = std::sqrt(1.0 - s->l * s->l - s->m * s->m) - 1.0;
     a.inv_zf = 1.0 / (1.0 + s->z);
     const int64_t threads = s->nrow * (int64_t)nrest;
-    k_regrid<<<(unsigned)((threads + 255) / 256), 256, 0, h->stream>>>(a);
+    k_regrid_tau<<<(unsigned)((s->nrow + 255) / 256), 256, 0, h->stream>>>(a);
     e = cudaGetLastError();
+    if (e == cudaSuccess) k_regrid<<<(unsigned)((threads + 255) / 256), 256, 0, h->stream>>>(a);
+    if (e == cudaSuccess) e = cudaGetLastError();
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
     if (e != cudaSuccess) return cuda_fail(h, e, "regrid kernel");
     return VISTA_OK;

@@ -5,7 +5,11 @@
 //      range of channels that reach the cube, the chunk width
 //   3. launch classes: windows sharing one kernel instantiation
 //   4. host-memory windows: only the channels that reach the cube are
-//      copied (2-D copies), into handle-owned device buffers
+//      copied (whole rows as one copy, else 2-D copies), into handle-owned
+//      device buffers, in waves: the copies of one wave (on four copy
+//      streams) run while the wave before is stacked, two staging slots
+//      taking turns (the streaming pipeline of Sec. 3.1/3.3: read ->
+//      compute overlapped)
 //   5. per mixed class: row ordering + records + work list, then the
 //      persistent stacking kernel; FP64 precision: the plain kernel
 #include <algorithm>
@@ -139,20 +143,14 @@ SortLayout sort_layout(int64_t rows, int64_t nbuckets, int64_t max_items, int64_
     return L;
 }
 
-// The device work of a planned run: flag repacking copies, then per launch
-// class the row-ordering pre-pass and the stacking kernel (or the FP64
-// kernel).  The same sequence is launched directly or captured in a graph.
-cudaError_t device_pass(vista_stack *h, cudaStream_t st)
+// One launch class: the row-ordering pre-pass and the stacking kernel (or
+// the FP64 kernel).
+cudaError_t launch_class(vista_stack *h, const ClassRun &cr, cudaStream_t st)
 {
     const bool fp64 = h->desc.precision == VISTA_PREC_FP64;
     const LaunchCfg cfg = h->cfg;
     cudaError_t e = cudaSuccess;
-    for (const Copy2D &cp : h->copies) {
-        e = cudaMemcpy2DAsync(cp.dst, cp.dpitch, cp.src, cp.spitch, cp.width, cp.height, cudaMemcpyDeviceToDevice,
-                              st);
-        if (e != cudaSuccess) return e;
-    }
-    for (ClassRun &cr : h->classes) {
+    {
         const RunArgs &a = cr.args;
         if (a.rot && fp64) {
             // gridding baselines of the re-projected windows (the mixed path
@@ -181,9 +179,63 @@ cudaError_t device_pass(vista_stack *h, cudaStream_t st)
                 if (h->timing) h->tacc.launches += 1;
             }
         }
+    }
+    return e;
+}
+
+// The device work of a planned run without host-memory windows: flag
+// repacking copies, then every launch class.  The same sequence is launched
+// directly or captured in a graph.
+cudaError_t device_pass(vista_stack *h, cudaStream_t st)
+{
+    cudaError_t e = cudaSuccess;
+    for (const Copy2D &cp : h->copies) {
+        e = cudaMemcpy2DAsync(cp.dst, cp.dpitch, cp.src, cp.spitch, cp.width, cp.height, cudaMemcpyDeviceToDevice,
+                              st);
         if (e != cudaSuccess) return e;
     }
+    for (const ClassRun &cr : h->classes)
+        if ((e = launch_class(h, cr, st)) != cudaSuccess) return e;
     return cudaSuccess;
+}
+
+// A run with host-memory windows, streamed wave by wave: the copies of wave
+// w go on the copy streams into staging slot w mod 2 once the wave that used
+// the slot before has been stacked; the handle's stream waits for them and
+// stacks the wave's classes.  So the copies of wave w + 1 overlap the
+// stacking of wave w, and nothing waits on the host.
+cudaError_t streamed_pass(vista_stack *h)
+{
+    // the copy streams first wait for work already queued (an earlier run
+    // may still read the staging buffer)
+    cudaError_t e = xfer_fork(h);
+    for (int j = 0; j < 2 && e == cudaSuccess; ++j)
+        if (!h->slot_ev[j]) e = cudaEventCreateWithFlags(&h->slot_ev[j], cudaEventDisableTiming);
+    for (const Copy2D &cp : h->copies) {
+        if (e != cudaSuccess) break;
+        e = cudaMemcpy2DAsync(cp.dst, cp.dpitch, cp.src, cp.spitch, cp.width, cp.height, cudaMemcpyDeviceToDevice,
+                              h->stream);
+    }
+    size_t ci = 0;
+    for (int w = 0; w < h->nwaves && e == cudaSuccess; ++w) {
+        const int slot = w & 1;
+        for (int j = 0; j < NXFER && e == cudaSuccess && w >= 2; ++j)
+            e = cudaStreamWaitEvent(h->xfer[j], h->slot_ev[slot], 0);
+        int k = 0;
+        for (const HostCopy &c : h->hcopies) {
+            if (c.wave != w || e != cudaSuccess) continue;
+            const cudaStream_t cs = h->xfer[k++ % NXFER];
+            if (c.width == c.spitch && c.width == c.dpitch)
+                e = cudaMemcpyAsync(c.dst, c.src, c.width * c.height, cudaMemcpyHostToDevice, cs);
+            else
+                e = cudaMemcpy2DAsync(c.dst, c.dpitch, c.src, c.spitch, c.width, c.height, cudaMemcpyHostToDevice, cs);
+        }
+        if (e == cudaSuccess) e = xfer_join(h);   // the stream waits for this wave's copies
+        while (e == cudaSuccess && ci < h->classes.size() && h->classes[ci].wave == w)
+            e = launch_class(h, h->classes[ci++], h->stream);
+        if (e == cudaSuccess) e = cudaEventRecord(h->slot_ev[slot], h->stream);
+    }
+    return e;
 }
 
 // Everything the plan of a run depends on, as bytes: the cube and lattice,
@@ -297,7 +349,42 @@ extern "C" int vista_run(vista_stack *h)
     }
     h->lattice_fixed = true;
 
-    // 3. launch classes (windows with no row or no channel in the cube are skipped)
+    // 3. waves of host-memory windows (by staged bytes, about a quarter of
+    //    them each, 64 MB to 2 GB), then the launch classes, wave by wave
+    //    (windows with no row or no channel in the cube are skipped)
+    auto staged_bytes = [&](int i) {
+        const SrcHost &s = h->pending[(size_t)i];
+        const size_t nr = (size_t)s.d.nrow;
+        const int32_t nin = plans[(size_t)i].k_hi - plans[(size_t)i].k_lo;
+        const size_t fbytes = s.d.flags ? al256(nr * (size_t)flag_pitch(nin, s.d.npol)) : 0;
+        return al256(nr * 24) + al256(nr * (size_t)nin * (size_t)s.d.npol * vis_elem_bytes(s.d.vis_type)) +
+               al256(nr * 4 * (size_t)s.d.npol) + fbytes;
+    };
+    auto in_cube = [&](int i) {
+        return h->pending[(size_t)i].d.nrow > 0 && plans[(size_t)i].k_hi > plans[(size_t)i].k_lo;
+    };
+    std::vector<int> wave_of((size_t)nsrc, 0);
+    int nwaves = 0;
+    size_t slot_bytes = 0;
+    {
+        size_t host_total = 0;
+        for (int i = 0; i < nsrc; ++i)
+            if (h->pending[(size_t)i].d.mem == VISTA_MEM_HOST && in_cube(i)) host_total += staged_bytes(i);
+        const size_t budget = h->wave_bytes > 0 ? (size_t)h->wave_bytes
+                                                : std::max((size_t)64 << 20, std::min((size_t)2 << 30, host_total / 4));
+        size_t cur = 0;
+        for (int i = 0; i < nsrc; ++i) {
+            if (h->pending[(size_t)i].d.mem != VISTA_MEM_HOST || !in_cube(i)) continue;
+            const size_t b = staged_bytes(i);
+            if (nwaves == 0 || (cur > 0 && cur + b > budget)) {
+                ++nwaves;
+                cur = 0;
+            }
+            wave_of[(size_t)i] = nwaves - 1;
+            cur += b;
+            slot_bytes = std::max(slot_bytes, cur);
+        }
+    }
     const LaunchCfg cfg = h->cfg;
     std::vector<ClassRun> classes;
     std::vector<int> ns_of((size_t)nsrc, 1);
@@ -310,17 +397,21 @@ extern "C" int vista_run(vista_stack *h)
         const int ns = fp64 ? 1 : choose_ns(pl.k_hi - pl.k_lo, cap);
         ns_of[(size_t)i] = ns;
         const int key = fp64 ? 0 : ((s.d.vis_type << 16) | (ns << 8) | s.d.npol);
+        const int wv = wave_of[(size_t)i];
         int ci = -1;
         for (size_t j = 0; j < classes.size(); ++j)
-            if (classes[j].key == key) ci = (int)j;
+            if (classes[j].key == key && classes[j].wave == wv) ci = (int)j;
         if (ci < 0) {
             classes.emplace_back();
             classes.back().key = key;
             classes.back().ns = ns;
+            classes.back().wave = wv;
             ci = (int)classes.size() - 1;
         }
         classes[(size_t)ci].members.push_back(i);
     }
+    std::stable_sort(classes.begin(), classes.end(),
+                     [](const ClassRun &x, const ClassRun &y) { return x.wave < y.wave; });
     std::vector<ChanF> chf;
     std::vector<ChanD> chd;
     std::vector<int32_t> chan_off((size_t)nsrc);
@@ -331,24 +422,20 @@ extern "C" int vista_run(vista_stack *h)
     }
     if (chf.size() > (size_t)0x7fffffff) return fail(h, VISTA_E_RANGE, "too many channels in one run");
 
-    // 4. staging layout: host-memory windows (the channels read only), and
-    //    the flags of device windows the mixed path cannot read in words
+    // 4. staging layout: two slots for the waves of host-memory windows (the
+    //    channels read only), then the flags of device windows the mixed
+    //    path cannot read in words
     auto repack_flags = [&](const SrcHost &s) {
         return !fp64 && s.d.mem == VISTA_MEM_DEVICE && s.d.flags && !flags_direct(s.d.flags, s.d.nchan, s.d.npol);
     };
-    size_t stage_bytes = 0;
+    const size_t host_region = slot_bytes * (size_t)(nwaves >= 2 ? 2 : nwaves);
+    size_t stage_bytes = host_region;
     for (const ClassRun &cr : classes)
         for (int i : cr.members) {
             const SrcHost &s = h->pending[(size_t)i];
-            const size_t nr = (size_t)s.d.nrow;
-            const int32_t nin = plans[(size_t)i].k_hi - plans[(size_t)i].k_lo;
-            const size_t fbytes = s.d.flags ? al256(nr * (size_t)flag_pitch(nin, s.d.npol)) : 0;
-            if (s.d.mem == VISTA_MEM_HOST) {
-                const size_t nvv = nr * (size_t)nin * (size_t)s.d.npol;
-                stage_bytes += al256(nr * 24) + al256(nvv * vis_elem_bytes(s.d.vis_type)) +
-                               al256(nr * 4 * (size_t)s.d.npol) + fbytes;
-            } else if (repack_flags(s)) {
-                stage_bytes += fbytes;
+            if (repack_flags(s)) {
+                const int32_t nin = plans[(size_t)i].k_hi - plans[(size_t)i].k_lo;
+                stage_bytes += al256((size_t)s.d.nrow * (size_t)flag_pitch(nin, s.d.npol));
             }
         }
     if (stage_bytes) {
@@ -372,11 +459,9 @@ extern "C" int vista_run(vista_stack *h)
     int64_t rec_total = 0, cell_total = 0;
     uint64_t nvis_run = 0;
     std::vector<Copy2D> copies;
-    size_t stage_pos = 0;
-    const int span_copy = stage_bytes ? span_begin(h, 2) : -1;
-    // host windows are copied on the copy streams, window j on stream j mod NXFER
-    int nhost = 0;
-    if (stage_bytes && (e = xfer_fork(h)) != cudaSuccess) return cuda_fail(h, e, "copy stream setup");
+    std::vector<HostCopy> hcopies;
+    std::vector<size_t> wave_pos((size_t)std::max(nwaves, 1), 0);   // next free byte of each wave's slot
+    size_t stage_pos = host_region;                                  // the repacked flags follow the slots
     for (size_t ci = 0; ci < classes.size(); ++ci) {
         ClassRun &cr = classes[ci];
         const int cw = 32 * cr.ns;
@@ -400,40 +485,32 @@ extern "C" int vista_run(vista_stack *h)
             d.fpitch = (int64_t)s.d.nchan * s.d.npol;
             d.fk0 = 0;
             if (s.d.mem == VISTA_MEM_HOST) {
+                // staged in its wave's slot; the copies are issued by streamed_pass
+                const int wv = wave_of[(size_t)i];
                 const size_t nr = (size_t)s.d.nrow, P = (size_t)s.d.npol;
                 const size_t esz = vis_elem_bytes(s.d.vis_type);
                 const size_t nvv = nr * (size_t)nin * P;
-                char *base = (char *)h->b_stage.p;
-                char *p_uvw = base + stage_pos;
-                stage_pos += al256(nr * 24);
-                char *p_vis = base + stage_pos;
-                stage_pos += al256(nvv * esz);
-                char *p_w = base + stage_pos;
-                stage_pos += al256(nr * 4 * P);
+                char *base = (char *)h->b_stage.p + (size_t)(wv & 1) * slot_bytes;
+                size_t &pos = wave_pos[(size_t)wv];
+                char *p_uvw = base + pos;
+                pos += al256(nr * 24);
+                char *p_vis = base + pos;
+                pos += al256(nvv * esz);
+                char *p_w = base + pos;
+                pos += al256(nr * 4 * P);
                 char *p_f = nullptr;
                 const size_t fp = (size_t)flag_pitch(nin, s.d.npol);
                 if (s.d.flags) {
-                    p_f = base + stage_pos;
-                    stage_pos += al256(nr * fp);
+                    p_f = base + pos;
+                    pos += al256(nr * fp);
                 }
                 const size_t row_in = (size_t)s.d.nchan * P, row_out = (size_t)nin * P;
-                // whole rows go as one contiguous copy, partial rows as a 2-D copy
-                const cudaStream_t cs = h->xfer[nhost++ % NXFER];
-                auto copy_rows = [&](void *dst, size_t dpitch, const void *src, size_t spitch, size_t width) {
-                    if (width == spitch && width == dpitch)
-                        return cudaMemcpyAsync(dst, src, width * nr, cudaMemcpyHostToDevice, cs);
-                    return cudaMemcpy2DAsync(dst, dpitch, src, spitch, width, nr, cudaMemcpyHostToDevice, cs);
-                };
-                e = cudaMemcpyAsync(p_uvw, s.d.uvw, nr * 24, cudaMemcpyHostToDevice, cs);
-                if (e == cudaSuccess)
-                    e = copy_rows(p_vis, row_out * esz, (const char *)s.d.vis + (size_t)pl.k_lo * P * esz, row_in * esz,
-                                  row_out * esz);
-                if (e == cudaSuccess) e = cudaMemcpyAsync(p_w, s.d.weights, nr * 4 * P, cudaMemcpyHostToDevice, cs);
-                if (e == cudaSuccess && p_f) e = copy_rows(p_f, fp, s.d.flags + (size_t)pl.k_lo * P, row_in, row_out);
-                if (e != cudaSuccess) {
-                    xfer_join(h);   // later work on the stream still waits for the copies issued
-                    return cuda_fail(h, e, "host-to-device copy of a host-memory window");
-                }
+                hcopies.push_back(HostCopy{wv, p_uvw, nr * 24, s.d.uvw, nr * 24, nr * 24, 1});
+                hcopies.push_back(HostCopy{wv, p_vis, row_out * esz, (const char *)s.d.vis + (size_t)pl.k_lo * P * esz,
+                                           row_in * esz, row_out * esz, nr});
+                hcopies.push_back(HostCopy{wv, p_w, nr * 4 * P, s.d.weights, nr * 4 * P, nr * 4 * P, 1});
+                if (p_f)
+                    hcopies.push_back(HostCopy{wv, p_f, fp, s.d.flags + (size_t)pl.k_lo * P, row_in, row_out, nr});
                 d.uvw = (const double *)p_uvw;
                 d.vis = p_vis;
                 d.wts = (const float *)p_w;
@@ -506,8 +583,6 @@ extern "C" int vista_run(vista_stack *h)
         cr.args.so.max_items = max_items;
         sort_bytes = std::max(sort_bytes, layouts[ci].total);
     }
-    if (stage_bytes && (e = xfer_join(h)) != cudaSuccess) return cuda_fail(h, e, "copy stream join");
-    span_end(h, span_copy);
 
     // uploads and buffers
     if ((e = upload(h->b_srcs, sdev, h->stream)) != cudaSuccess) return cuda_fail(h, e, "source table upload");
@@ -571,16 +646,18 @@ extern "C" int vista_run(vista_stack *h)
     }
     h->classes = std::move(classes);
     h->copies = std::move(copies);
-    if ((e = device_pass(h, h->stream)) != cudaSuccess) {
+    h->hcopies = std::move(hcopies);
+    h->nwaves = nwaves;
+    bool any_host = false;
+    for (const SrcHost &s : h->pending) any_host |= s.d.mem == VISTA_MEM_HOST;
+    // host-memory windows: streamed wave by wave (their arrays must stay valid
+    // until this stream work completes); otherwise the device pass at once
+    if ((e = (nwaves > 0 ? streamed_pass(h) : device_pass(h, h->stream))) != cudaSuccess) {
         h->plan_valid = false;
-        return cuda_fail(h, e, "kernel launch");
+        return cuda_fail(h, e, "kernel launch or host-to-device copy");
     }
     if (h->timing) h->tacc.runs += 1;
     h->host_nvis += nvis_run;
-    bool any_host = false;
-    for (const SrcHost &s : h->pending) any_host |= s.d.mem == VISTA_MEM_HOST;
-    if (any_host && (e = cudaStreamSynchronize(h->stream)) != cudaSuccess)
-        return cuda_fail(h, e, "stream synchronize after host-memory copies");
     // the device tables now hold this source set's plan: an unchanged set is
     // replayed from a graph of the device pass next time
     drop_graph(h);

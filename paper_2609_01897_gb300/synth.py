@@ -354,7 +354,7 @@ CII_REST = 1900.537e9   # [CII] 158 um, Hz
 
 
 def batched(device="cpu", n_sources=2000, median_rows=20000, pool_gb=96.0, src_ids=None,
-            meta_only=False, du=None, seed_pool=True) -> Workload:
+            meta_only=False, du=None, seed_pool=True, nrest=1024) -> Workload:
     """Batched uneven stack: per source, rows lognormal(median 20k, sigma_ln 1),
     1-4 windows of 1.875 GHz with 128/240/480/960/3840 channels in 84-950 GHz
     (window 0 centred on [CII] 1900.537 GHz/(1+z) when that falls in the
@@ -368,7 +368,8 @@ def batched(device="cpu", n_sources=2000, median_rows=20000, pool_gb=96.0, src_i
     within 0.25-5 km, 30 s integrations at dec -30, lat -23 (rows = the first
     nrow of the baseline tracks), offsets within +-10", weights U[0.5, 1.5];
     a window's rows are capped so that it fits the pool (the far lognormal
-    tail only)."""
+    tail only).  nrest < 1024 narrows the rest range of the cube (same
+    channel width and centre: a smaller cube for profiling captures)."""
     cid = CONFIG_IDS["batched"]
     nsrc_ids = range(n_sources) if src_ids is None else src_ids
     choices = np.array([128, 240, 480, 960, 3840])
@@ -431,7 +432,7 @@ def batched(device="cpu", n_sources=2000, median_rows=20000, pool_gb=96.0, src_i
                 spws.append(SourceSpw(uvw, w.freqs(), vis, wts, flags, l0, m0, z, source=s))
     n = 256
     du = _cube_du(spws, n) if du is None else du
-    return Workload("batched", n, n, 1024, 4, du, du, CII_REST, spws)
+    return Workload("batched", n, n, nrest, 4, du, du, CII_REST, spws)
 
 
 def scaled(w: Workload, frac: float) -> Workload:

@@ -77,6 +77,9 @@ SIGNATURES = {
     "vista_add_source_reproject": (C.c_int, [_P, C.POINTER(SourceDesc), C.c_double, C.c_double, C.c_double,
                                              C.c_double]),
     "vista_regrid_rows": (C.c_int, [_P, C.POINTER(SourceDesc), _P, _P, _P]),
+    "vista_contsub": (C.c_int, [_P, _P, C.c_int32, _P, C.c_int]),
+    "vista_set_wave_bytes": (C.c_int, [_P, C.c_int64]),
+    "vista_get_waves": (C.c_int, [_P, C.POINTER(C.c_int32)]),
     "vista_run": (C.c_int, [_P]),
     "vista_read_cube": (C.c_int, [_P, _P, _P, _P, _P, C.c_int]),
     "vista_read_cube_f64": (C.c_int, [_P, _P, _P, _P, _P, C.c_int]),
@@ -238,7 +241,9 @@ class Stack:
 
     def run(self):
         _check("vista_run", lib().vista_run(self.h), self.h)
-        self._inflight = self._pending
+        # host-memory windows are copied by stream work that may still run
+        # when run() returns: their arrays stay referenced until a sync
+        self._inflight = self._inflight + self._pending
         self._pending = []
 
     # -- results
@@ -270,9 +275,37 @@ class Stack:
         self._inflight = []
         return {k: v for k, v in out.items() if v is not None}
 
+    def contsub(self, line_free, order=1, device=True, out=None):
+        """Continuum-subtracted sum W w V' of the cube (vista_contsub): a
+        polynomial of degree <= order in rest channel, fitted per uv cell and
+        plane over the line-free channels (line_free: [nrest] bools), is
+        subtracted.  Returns a float32 tensor [nv, nu, nrest, npol, 2] on the
+        device (or in pinned host memory)."""
+        nv, nu, nrest, npol = self.shape
+        lf = np.ascontiguousarray(np.asarray(line_free, dtype=np.uint8).reshape(-1))
+        if lf.size != nrest:
+            raise ValueError("line_free must have nrest = %d entries" % nrest)
+        if out is None:
+            kw = {"device": "cuda"} if device else {"pin_memory": torch.cuda.is_available()}
+            out = torch.empty((nv, nu, nrest, npol, 2), dtype=torch.float32, **kw)
+        _check("vista_contsub", lib().vista_contsub(self.h, lf.ctypes.data, int(order), _ptr(out),
+                                                    1 if device else 0), self.h)
+        return out
+
+    def set_wave_bytes(self, nbytes):
+        """Staged bytes per wave of host-memory windows (0 = the library's rule)."""
+        _check("vista_set_wave_bytes", lib().vista_set_wave_bytes(self.h, int(nbytes)), self.h)
+
+    def waves(self):
+        """Waves the last run streamed its host-memory windows in."""
+        n = C.c_int32(0)
+        _check("vista_get_waves", lib().vista_get_waves(self.h, C.byref(n)), self.h)
+        return int(n.value)
+
     def stats(self):
         s = Stats()
         _check("vista_get_stats", lib().vista_get_stats(self.h, C.byref(s)), self.h)
+        self._inflight = []   # the call waited for the stream
         return s.as_dict()
 
     def lattice(self):

@@ -4,10 +4,12 @@
 * a reduced instance (30 sources, median 600 rows) against the FP64 oracle,
   every cube entry;
 * the full instance (2000 sources, ~1.9e11 visibilities reach the cube, the
-  launch configuration bench.py times) against the plain FP64 GPU path on
-  every cube entry: counts identical, sums within 1e-5 of the Cauchy-Schwarz
-  scale sqrt(sum_w * sum_wvv) >= sum W w |V| (the cancellation-aware bound,
-  computed from the cube itself), and visibility counters that add up."""
+  launch configuration bench.py times) stacked twice into one cube (twice the
+  depth: the accuracy of the mixed cube must not depend on it) against the
+  plain FP64 GPU path doing the same, on every cube entry: counts identical,
+  sums within 1e-5 of the Cauchy-Schwarz scale sqrt(sum_w * sum_wvv) >=
+  sum W w |V| (the cancellation-aware bound, computed from the cube itself),
+  and visibility counters that add up."""
 import numpy as np
 import pytest
 import torch
@@ -38,7 +40,7 @@ def test_batched_reduced_against_oracle(V):
     H.stats_equal(g, o)
 
 
-def test_batched_full_mixed_against_fp64(V):
+def test_batched_full_twice_mixed_against_fp64(V):
     from paper_2609_01897_gb300 import synth
     free, _ = torch.cuda.mem_get_info()
     if free < 150e9:
@@ -50,9 +52,11 @@ def test_batched_full_mixed_against_fp64(V):
         try:
             if prec == V.PREC_MIXED:
                 st.set_tuning(rows_per_item=48, chans_per_lane=1, warps_per_cta=4, sort_rows=1, prefetch_rows=4)
-            for s in wl.spws:
-                st.add_source(s.uvw, s.freqs, s.vis, s.weights, s.flags, l=s.l, m=s.m, z=s.z, pol_map=s.pol_map)
-            st.run()
+            for _ in range(2):
+                for s in wl.spws:
+                    st.add_source(s.uvw, s.freqs, s.vis, s.weights, s.flags, l=s.l, m=s.m, z=s.z,
+                                  pol_map=s.pol_map)
+                st.run()
             cubes[prec] = st.read_cube(device=True, f64=True)
             stats[prec] = st.stats()
         finally:
@@ -68,10 +72,10 @@ def test_batched_full_mixed_against_fp64(V):
             float(rel.flatten()[i]), i, int(d["count"].flatten()[i]), float(ref.flatten()[i]))
     for key in ("sum_w", "sum_wvv"):
         err = (m[key] - d[key]).abs()
-        print("batched full, %s: %s" % (key, worst(err, d[key].abs())))
+        print("batched full x2, %s: %s" % (key, worst(err, d[key].abs())))
         assert bool((err <= H.TOL_MIXED * d[key].abs() + 1e-300).all()), key + ": " + worst(err, d[key].abs())
     err = (m["sum_wv"] - d["sum_wv"]).abs().amax(dim=-1)
-    print("batched full, sum_wv: %s" % worst(err, scale))
+    print("batched full x2, sum_wv: %s" % worst(err, scale))
     assert bool((err <= H.TOL_MIXED * scale + 1e-300).all()), "sum_wv: " + worst(err, scale)
     sm, sd = stats[V.PREC_MIXED], stats[V.PREC_FP64]
     for k in ("n_vis", "n_flagged", "n_dropped_uv", "n_stacked"):

@@ -1,7 +1,8 @@
 """The paper's per-row output (Eq. 3, vista_regrid_rows) against the oracle's
 plain per-row products: every row of every tiny window, both binning modes,
-16-bit storage, the rest-frame uvw, and the state error before the lattice
-is fixed."""
+16-bit storage, the rest-frame uvw, the state error before the lattice is
+fixed, and a full 3840-channel, 4-pol window (wide as the batched stack's)
+regridded onto rest bins 32 channels wide."""
 import numpy as np
 import pytest
 import torch
@@ -30,10 +31,11 @@ def tiny():
 
 def _check(g_vis, g_w, o_vis, o_w, vis_scale):
     g_vis, g_w = g_vis.cpu().numpy().astype(np.complex128), g_w.cpu().numpy().astype(np.float64)
-    # FP64 on both sides, rounded once to FP32 on output
+    # the kernel: FP32 weights and sums of a few terms (~1e-7 relative) and a
+    # phasor within 5e-7 rad; the oracle: FP64
     np.testing.assert_allclose(g_w, o_w, rtol=1e-6, atol=1e-7)
     err = np.abs(g_vis - o_vis)
-    assert (err <= 1e-6 * (np.abs(o_vis) + vis_scale)).all(), float(err.max())
+    assert (err <= 2e-6 * (np.abs(o_vis) + vis_scale)).all(), float((err / (np.abs(o_vis) + vis_scale)).max())
     assert (o_w > 0).sum() > 0
 
 
@@ -88,3 +90,36 @@ def test_regrid_rows_needs_a_lattice(V, tiny):
                      s.flags.cpu().numpy(), s.l, s.m, s.z)
     o_vis, o_w = H.O.regrid_rows(src, f0, df, tiny.nrest)
     _check(g_vis, g_w, o_vis, o_w, float(s.vis.abs().max()))
+
+
+def test_regrid_rows_full_wide_window(V):
+    """A window as wide as the batched stack's widest (3840 channels over
+    1.875 GHz, 4 pols, 2000 rows, 3 % flags, offset 8 arcsec) on a lattice of
+    rest bins 32 channels wide, every row and bin against the oracle."""
+    from paper_2609_01897_gb300 import synth
+    rng = np.random.default_rng(12)
+    nrow, nchan, npol = 2000, 3840, 4
+    enu = synth.array_enu(30, 3000.0, rng)
+    uvw = synth.uvw_tracks(enu, -23.0, -30.0, (nrow + 434) // 435, 30.0, 0.1)[:nrow]
+    df_obs = 1.875e9 / nchan
+    f = 380e9 + df_obs * np.arange(nchan)
+    g = torch.Generator(device="cuda")
+    g.manual_seed(12)
+    vis = torch.complex(torch.randn((nrow, nchan, npol), generator=g, device="cuda"),
+                        torch.randn((nrow, nchan, npol), generator=g, device="cuda")).to(torch.complex64)
+    flags = (torch.rand((nrow, nchan, npol), generator=g, device="cuda") < 0.03).to(torch.uint8)
+    u = torch.as_tensor(uvw, device="cuda")
+    l0, m0, z = 8 * np.pi / 180 / 3600, -5 * np.pi / 180 / 3600, 1.7
+    rest_df = 32 * df_obs * (1 + z)
+    nrest = nchan // 32 + 4
+    f0 = f[0] * (1 + z) - 2 * rest_df
+    st = V.Stack(16, 16, nrest, npol, 1.0, 1.0, rest_f0=f0, rest_df=rest_df)
+    try:
+        g_vis, g_w, _ = st.regrid_rows(u, f, vis, flags, l=l0, m=m0, z=z)
+    finally:
+        st.close()
+    src = H.O.Source(uvw, f, vis.cpu().numpy(), np.ones((nrow, npol), dtype=np.float32), flags.cpu().numpy(),
+                     l0, m0, z)
+    o_vis, o_w = H.O.regrid_rows(src, f0, rest_df, nrest)
+    assert (o_w > 0).sum() > nrow * npol * (nchan // 32 - 2)
+    _check(g_vis, g_w, o_vis, o_w, float(vis.abs().max()))
