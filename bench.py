@@ -2,11 +2,14 @@
 """Stacked visibilities per second on GB300 (ViSta hot path, libvista).
 
 One step = one full stacking pass: queue every (source, window) of the
-workload, vista_run (the cube is zeroed once and accumulates across steps).  The inputs (seeded synthetic ALMA-compact-like
-stack: 64 sources x 2 windows x 120 channels x 2 pols, 43 antennas, 120
-integrations; cube 256 x 256 uv cells x 512 rest channels x 2 pols) are
-resident in HBM before the timed region; they total ~30 GB, far larger than
-L2, so no L2 flush is needed between steps.
+workload, vista_run (the cube is zeroed once and accumulates across steps).
+The default workload is the batched uneven stack (2000 sources, lognormal
+row counts, 1-4 windows of 128-3840 channels, 2 or 4 pols, one persistent
+launch per class replayed from a CUDA graph; cube 256 x 256 uv cells x 1024
+rest channels x 4 pols).  Its ~1.7 TB of in-cube inputs per step are views
+into a 96 GB device pool, resident in HBM before the timed region and far
+larger than L2, so no L2 flush is needed between steps.  --config
+alma_compact, mixed, wideband_hi and tiny select the other workloads.
 
 Prints one JSON line (rank 0).  --impl reference times the FP64 CPU oracle on
 the host cores instead, on bounded samples of the same workload.
@@ -40,19 +43,28 @@ def parse():
     p.add_argument("--steps", type=int, default=10)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    p.add_argument("--config", default="alma_compact", choices=["alma_compact", "tiny", "wideband_hi", "batched", "mixed"])
+    p.add_argument("--config", default="batched", choices=["alma_compact", "tiny", "wideband_hi", "batched", "mixed"])
     p.add_argument("--reproject", action="store_true",
                    help="full re-projection of Eq. 1: every window names its phase centre and stacking position")
     p.add_argument("--storage", default="c64", choices=["c64", "f16", "bf16"],
                    help="visibility storage (16-bit: one power-of-two scale per window)")
     p.add_argument("--pool-gb", type=float, default=96.0, help="batched: device pool the windows alias (GB)")
     p.add_argument("--sources", type=int, default=0, help="sources per rank (0 = the workload's own)")
-    p.add_argument("--fp64-steps", type=int, default=2, help="timed steps of the plain FP64 leg (0 = skip)")
+    p.add_argument("--nrest", type=int, default=0,
+                   help="batched: rest channels of the cube (0 = 1024; fewer gives a smaller cube for captures)")
+    p.add_argument("--fp64-steps", type=int, default=1, help="timed steps of the plain FP64 leg (0 = skip)")
     p.add_argument("--e2e-steps", type=int, default=2, help="timed host-memory steps (0 = skip)")
+    p.add_argument("--e2e-gb", type=float, default=24.0,
+                   help="pinned host memory for the end-to-end leg: windows are taken in order while their "
+                        "host copies fit (GB)")
     p.add_argument("--cpu-sample", type=int, default=40,
                    help="windows timed once in the oracle baseline of our arm (0 = skip)")
     p.add_argument("--ref-sample", type=int, default=8, help="windows per step of the reference (oracle) arm")
     p.add_argument("--tuning", default="", help="rows,chans_per_lane,warps,sort,prefetch")
+    p.add_argument("--regrid-reps", type=int, default=3,
+                   help="timed calls of the per-row output (Eq. 3) on the workload's widest window (0 = skip)")
+    p.add_argument("--contsub-reps", type=int, default=3,
+                   help="timed calls of the continuum subtraction over the cube (0 = skip)")
     p.add_argument("--autotune", type=int, default=0,
                    help="autotune the launch shape first over this many candidates (0 = no)")
     return p.parse_args()
@@ -109,6 +121,22 @@ def allsum(ws, x):
         return x
     import torch.distributed as dist
     return _reduce(ws, x, dist.ReduceOp.SUM)
+
+
+def reduce_cubes(ws, cube):
+    """The one exchange step of a multi-GPU stack: the sum of the ranks'
+    partial cubes on rank 0, sums in FP64 and counts as exact integers, one
+    reduction per array (NCCL moves them over the GPUs' links; gloo on the
+    host).  Returns rank 0's total (other ranks: their arrays, overwritten)."""
+    if ws == 1:
+        return cube
+    import torch.distributed as dist
+    out = {}
+    for k, v in cube.items():
+        t = v.to(torch.int64) if k == "count" else v.to(torch.float64)
+        dist.reduce(t, dst=0, op=dist.ReduceOp.SUM)
+        out[k] = t
+    return out
 
 
 class Clocks:
@@ -173,7 +201,7 @@ def measured_traffic(n_vis):
     except (OSError, AttributeError, ValueError):
         return None
     h = hashlib.sha256()
-    for f in ("vista_stack.cu", "vista_device.cuh"):
+    for f in ("vista_stack.cuh", "vista_device.cuh"):
         with open(os.path.join(ROOT, "paper_2609_01897_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return per_vis * n_vis if h.hexdigest() == sha else None
@@ -227,7 +255,7 @@ def make_workload(args, rank, device):
         if args.config == "alma_compact":
             wl = synth.alma_compact(device, n_sources=n, src_ids=ids)
         else:
-            wl = synth.batched(device, n_sources=n, src_ids=ids, pool_gb=args.pool_gb)
+            wl = synth.batched(device, n_sources=n, src_ids=ids, pool_gb=args.pool_gb, nrest=args.nrest or 1024)
     if args.reproject:
         if args.config == "batched":
             raise SystemExit("--reproject applies to the array workloads (the batched stack has no sky geometry)")
@@ -392,6 +420,21 @@ def run_ours(args):
     peak, peak_kind = measured_peaks()
     achieved = alg / (stack_ms * 1e-3) / 1e9 if stack_ms > 0 else 0.0
     launches = int(round(tm["launches"])) * args.steps
+    regrid = time_regrid(st, wl, f0, df, args.regrid_reps, peak) if args.regrid_reps > 0 else None
+    contsub = time_contsub(st, wl, args.contsub_reps, peak) if args.contsub_reps > 0 else None
+    # several GPUs: the final reduce-sum of the partial cubes into rank 0 (after the timed region)
+    cube_reduce_ms = None
+    if ws > 1:
+        import torch.distributed as dist
+        on_dev = dist.get_backend() == "nccl"
+        part = st.read_cube(device=on_dev, f64=True)
+        barrier(ws)
+        t0 = time.perf_counter()
+        total = reduce_cubes(ws, part)
+        if on_dev:
+            torch.cuda.synchronize()
+        cube_reduce_ms = allmax(ws, (time.perf_counter() - t0) * 1e3)
+        del part, total
     st.close()
 
     # plain FP64 GPU form on the same inputs
@@ -406,17 +449,12 @@ def run_ours(args):
 
     # end to end through the C ABI with host buffers
     e2e = None
-    if args.e2e_steps > 0 and wl.name == "batched":
-        # the whole stack is ~5e11 visibilities (aliased on the device): it has
-        # no host-memory form to copy from
-        e2e = {"skipped": "the batched stack exists only as views into a device pool"}
-    elif args.e2e_steps > 0 and wl.name.startswith("wideband_hi"):
-        e2e = {"skipped": "a pinned host copy of the 127 GB wideband inputs is not made"}
-    elif args.e2e_steps > 0:
+    if args.e2e_steps > 0:
         try:
-            e2e = run_e2e(args, wl, tuning, n_vis, ws)
+            e2e = run_e2e(args, wl, tuning, f0, df, ws)
         except (RuntimeError, MemoryError) as exc:
             e2e = {"error": str(exc)[:200]}
+    link = host_link_peak() if rank == 0 and args.e2e_steps > 0 else None
 
     cpu = None
     if rank == 0 and ws == 1 and args.cpu_sample > 0:
@@ -436,10 +474,14 @@ def run_ours(args):
                          "algorithmic_bytes_per_launch": alg, "kernel_ms": stack_ms,
                          "peak_source": peak_kind},
             "prepass_ms": tm["prepass_ms"],
+            "cube_reduce_ms": cube_reduce_ms,
             "graph_replays_timed": graph_runs,
             "cube_reductions_per_vis": red_per_vis,
             "fp64_gpu": fp64,
+            "regrid_rows": regrid,
+            "contsub": contsub,
             "e2e": e2e,
+            "host_link": link,
             "cpu_baseline": cpu,
             "gpu_launches": launches,
             "clocks": clocks,
@@ -450,6 +492,63 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+def time_regrid(st, wl, f0, df, reps, peak):
+    """The paper's per-row output (Eq. 3, vista_regrid_rows) on the workload's
+    widest window that reaches the cube: rows/s and the kernel's bytes (every
+    (row, channel, pol) value and flag of the window read once, the uvw, and
+    the [nrow][nrest][npol] outputs written: 8 + 4 B each) per second."""
+    from paper_2609_01897_gb300 import vista as V
+    best = None
+    for s in wl.spws:
+        _, nb, _ = V.plan_channels(s.freqs, s.z, f0, df, wl.nrest, V.BIN_OVERLAP)
+        if (nb > 0).any() and s.vis.shape[0] > 0 and (best is None or s.vis.shape[1] > best.vis.shape[1]):
+            best = s
+    if best is None:
+        return None
+    s = best
+    nrow, nchan, npol = (int(x) for x in s.vis.shape[:3])
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    st.regrid_rows(s.uvw, s.freqs, s.vis, s.flags, l=s.l, m=s.m, z=s.z, vis_scale=s.vis_scale)   # warm
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream()
+    e0.record(stream)
+    for _ in range(reps):
+        out = st.regrid_rows(s.uvw, s.freqs, s.vis, s.flags, l=s.l, m=s.m, z=s.z, vis_scale=s.vis_scale)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / reps
+    del out
+    nbytes = nrow * nchan * npol * (vis_bytes(s.vis) + (1 if s.flags is not None else 0)) + nrow * 24 + \
+        nrow * wl.nrest * npol * 12
+    gbs = nbytes / (ms * 1e-3) / 1e9
+    return {"window": "%d rows x %d ch x %d pol onto %d rest channels" % (nrow, nchan, npol, wl.nrest),
+            "ms": ms, "rows_per_s": nrow / (ms * 1e-3), "gb_s": gbs, "frac_hbm": gbs / peak,
+            "bytes_per_call": int(nbytes)}
+
+
+def time_contsub(st, wl, reps, peak):
+    """Continuum subtraction over the cube (vista_contsub, order 1, the
+    central eighth of the rest channels marked as line): ms per call and the
+    bytes of one pass over the cube's sums (the FP32 part and the FP64
+    master: 16 + 32 B per entry) plus the output (8 B per entry)."""
+    nrest = wl.nrest
+    free = np.ones(nrest, dtype=bool)
+    free[nrest // 2 - nrest // 16: nrest // 2 + nrest // 16] = False
+    out = st.contsub(free, 1)      # warm (the output buffer is reused)
+    t = []
+    for _ in range(reps):
+        t0 = time.perf_counter()
+        st.contsub(free, 1, out=out)
+        t.append(time.perf_counter() - t0)
+    ms = 1e3 * min(t)
+    n = wl.nu * wl.nv * nrest * wl.npol
+    nbytes = n * (16 + 32 + 8)
+    gbs = nbytes / (ms * 1e-3) / 1e9
+    del out
+    return {"order": 1, "ms": ms, "entries": n, "gb_s": gbs, "frac_hbm": gbs / peak, "bytes_per_call": nbytes,
+            "timing": "host clock around the synchronous call (includes the stream sync and error-word read)"}
+
+
 def to_pinned(t):
     if t is None:
         return None
@@ -458,52 +557,110 @@ def to_pinned(t):
     return out
 
 
-def run_e2e(args, wl, tuning, n_vis, ws):
+def window_io(s, f0, df, nrest):
+    """(in-cube visibilities, bytes vista_run copies host->device) of one
+    window: uvw and weights of every row, and the channels it reads (the
+    in-cube range rounded out to whole flag words) of vis and flags."""
+    from paper_2609_01897_gb300 import vista as V
+    _, nb, _ = V.plan_channels(s.freqs, s.z, f0, df, nrest, V.BIN_OVERLAP)
+    nrow, nch, npol = (int(x) for x in s.vis.shape[:3])
+    ks = np.nonzero(nb > 0)[0]
+    if ks.size == 0 or nrow == 0:
+        return 0, 0
+    al = 1 if npol >= 4 else 4 // npol
+    lo, hi = int(ks[0]) // al * al, min(nch, (int(ks[-1]) + 1 + al - 1) // al * al)
+    nin = hi - lo
+    h2d = nrow * (24 + 4 * npol) + nrow * nin * npol * vis_bytes(s.vis)
+    if s.flags is not None:
+        h2d += nrow * ((nin * npol + 3) // 4 * 4)
+    npm = npol if s.pol_map is None else int((np.asarray(s.pol_map) >= 0).sum())
+    return nrow * int(ks.size) * npm, h2d
+
+
+def run_e2e(args, wl, tuning, f0, df, ws):
     """Same metric through the public API with pinned HOST buffers: every step
     copies its inputs host->device (inside vista_run) and reads the cube back
-    to host memory."""
+    to host memory.  The windows are taken in order while their pinned host
+    copies fit in --e2e-gb (all of them for the array workloads; for the
+    batched stack, whose windows are views into a device pool, a stated
+    leading subset)."""
     from paper_2609_01897_gb300 import synth
     from paper_2609_01897_gb300 import vista as V
-    host, h2d = [], 0
-    f0, df = None, None
+    host, h2d, n_vis, pinned = [], 0, 0, 0
     for s in wl.spws:
-        hs = synth.SourceSpw(to_pinned(s.uvw), s.freqs, to_pinned(s.vis), to_pinned(s.weights),
-                             to_pinned(s.flags), s.l, s.m, s.z, s.pol_map, s.source, s.vis_scale, s.radec)
-        host.append(hs)
-    # bytes vista_run copies per step: uvw, weights, and the channels it reads
-    # (the in-cube range rounded out to whole flag words) of vis and flags
-    st0 = open_stack(wl, V.PREC_MIXED, tuning)
-    one_step(st0, wl)
-    f0, df = st0.lattice()
-    st0.close()
-    for s in wl.spws:
-        _, nb, _ = V.plan_channels(s.freqs, s.z, f0, df, wl.nrest, V.BIN_OVERLAP)
-        nrow, nch, npol = (int(x) for x in s.vis.shape[:3])
-        ks = np.nonzero(nb > 0)[0]
-        if ks.size == 0 or nrow == 0:
+        nv, hb = window_io(s, f0, df, wl.nrest)
+        if nv == 0:
             continue
-        al = 1 if npol >= 4 else 4 // npol
-        lo, hi = int(ks[0]) // al * al, min(nch, (int(ks[-1]) + 1 + al - 1) // al * al)
-        nin = hi - lo
-        h2d += nrow * (24 + 4 * npol) + nrow * nin * npol * vis_bytes(s.vis)
-        if s.flags is not None:
-            h2d += nrow * ((nin * npol + 3) // 4 * 4)
-    ste = open_stack(wl, V.PREC_MIXED, tuning)
+        size = sum(t.numel() * t.element_size() for t in (s.uvw, s.vis, s.weights, s.flags) if t is not None)
+        if pinned + size > args.e2e_gb * 1e9:
+            break
+        pinned += size
+        host.append(synth.SourceSpw(to_pinned(s.uvw), s.freqs, to_pinned(s.vis), to_pinned(s.weights),
+                                    to_pinned(s.flags), s.l, s.m, s.z, s.pol_map, s.source, s.vis_scale, s.radec))
+        n_vis += nv
+        h2d += hb
+    if not host:
+        return {"error": "no window fits in --e2e-gb"}
+    sub = synth.Workload(wl.name, wl.nu, wl.nv, wl.nrest, wl.npol, wl.du, wl.dv, wl.central_freq, host,
+                         df, f0)
+    ste = open_stack(sub, V.PREC_MIXED, tuning)
     outs, t0 = None, 0.0
+    split = {"queue_ms": 0.0, "device_ms": 0.0, "readback_ms": 0.0}
     for it in range(1 + args.e2e_steps):
         if it == 1:
             torch.cuda.synchronize()
             barrier(ws)
             t0 = time.perf_counter()
-        one_step(ste, wl, host)
+        ta = time.perf_counter()
+        one_step(ste, sub)
+        tb = time.perf_counter()
+        if it >= 1 and args.e2e_steps > 1 and it == args.e2e_steps:
+            # the last step also splits its time (the wait costs nothing extra:
+            # read_cube waits for the stream anyway)
+            torch.cuda.current_stream().synchronize()
+        tc = time.perf_counter()
         # the pinned result buffers are allocated once (first, untimed step)
         outs = ste.read_cube(device=False, out=outs)
+        td = time.perf_counter()
+        if it >= 1 and it == args.e2e_steps:
+            split = {"queue_ms": (tb - ta) * 1e3, "device_ms": (tc - tb) * 1e3, "readback_ms": (td - tc) * 1e3}
     dt = (time.perf_counter() - t0) / args.e2e_steps
     d2h = sum(v.numel() * v.element_size() for v in outs.values())
     ste.close()
     dt = allmax(ws, dt)
+    n_in = sum(1 for s in wl.spws if window_io(s, f0, df, wl.nrest)[0] > 0)
     return {"value": allsum(ws, n_vis) / dt, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
-            "d2h_bytes_per_step": int(d2h), "ms_per_step": dt * 1e3}
+            "d2h_bytes_per_step": int(d2h), "ms_per_step": dt * 1e3,
+            "windows": "%d of the %d windows that reach the cube (%d visibilities, %.1f GB pinned on the host)" % (
+                len(host), n_in, n_vis, pinned / 1e9),
+            "link_gbs": (h2d + d2h) / dt / 1e9,
+            "last_step_split": split}
+
+
+def host_link_peak(nbytes=4 << 30, reps=3):
+    """Pinned host <-> device copy rate: one large cudaMemcpyAsync each way,
+    best of `reps`, timed by CUDA events on the current stream."""
+    try:
+        h = torch.empty(nbytes, dtype=torch.uint8, pin_memory=True)
+        d = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
+    except RuntimeError as exc:
+        return {"error": str(exc)[:200]}
+    h.fill_(1)
+    stream = torch.cuda.current_stream()
+    best = {}
+    for name, dst, src in (("h2d_gbs", d, h), ("d2h_gbs", h, d)):
+        t = []
+        for _ in range(reps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            dst.copy_(src, non_blocking=True)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            t.append(e0.elapsed_time(e1) * 1e-3)
+        best[name] = nbytes / min(t) / 1e9
+    best["bytes"] = nbytes
+    del h, d
+    return best
 
 
 def workload_name(wl):

@@ -79,3 +79,27 @@ def test_half_pairs_scale_and_values():
         back = torch.view_as_complex(q.to(torch.float32).contiguous()) * scale
         rel = 2.0 ** -11 if kind == "f16" else 2.0 ** -8
         assert float((back - v).abs().max()) <= rel * float(v.abs().max()) * 2
+
+
+def test_e2e_window_io_counts(bench, tiny, oracle_mod):
+    """The end-to-end leg's per-window counts: in-cube visibilities sum to the
+    step's count, and the bytes copied cover uvw, weights and the channels
+    read (in-cube range rounded out to whole flag words) of vis and flags."""
+    f0, df = oracle_mod.auto_lattice([s.freqs for s in tiny.spws], [s.z for s in tiny.spws], tiny.nrest,
+                                     tiny.central_freq)
+    n_vis, _ = bench.algorithmic_bytes(tiny, f0, df, touched=0)
+    tot = 0
+    for s in tiny.spws:
+        nv, hb = bench.window_io(s, f0, df, tiny.nrest)
+        tot += nv
+        W = oracle_mod.rest_weights(s.freqs, s.z, f0, df, tiny.nrest)
+        ks = np.nonzero(W.sum(axis=1) > 0)[0]
+        nrow, nch, npol = s.vis.shape
+        if ks.size == 0:
+            assert hb == 0
+            continue
+        al = 4 // npol if npol < 4 else 1
+        lo, hi = ks[0] // al * al, min(nch, -(-(ks[-1] + 1) // al) * al)
+        flag_row = -(-(hi - lo) * npol // 4) * 4      # a word-aligned row of flag bytes
+        assert hb == nrow * (24 + 4 * npol) + nrow * (hi - lo) * npol * 8 + nrow * flag_row
+    assert tot == n_vis
