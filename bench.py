@@ -188,14 +188,15 @@ class Clocks:
                 "samples": len(sm)}
 
 
-def measured_traffic(n_vis):
-    """DRAM bytes per stacking launch from the committed ncu summary, scaled by
-    the visibilities of this launch -- or None once the kernel source differs
-    from the one the counters were taken on."""
+def measured_traffic(n_vis, config):
+    """DRAM bytes of a step's stacking launches from the committed ncu summary
+    of this workload (profiles/stack_mixed_<config>.md), scaled by the step's
+    visibilities -- or None without a summary, or once the kernel source
+    differs from the one the counters were taken on."""
     import hashlib
     import re
     try:
-        txt = open(os.path.join(ROOT, "profiles", "stack_mixed_alma_compact.md")).read()
+        txt = open(os.path.join(ROOT, "profiles", "stack_mixed_%s.md" % config)).read()
         sha = re.search(r"source_sha256:\s*([0-9a-f]{64})", txt).group(1)
         per_vis = float(re.search(r"traffic_bytes_per_vis:\s*([0-9.]+)", txt).group(1))
     except (OSError, AttributeError, ValueError):
@@ -470,7 +471,7 @@ def run_ours(args):
                        "tuning": st_tuning_str(eff_tuning),
                        "parallelism": "replicas" if ws > 1 else "single"},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": achieved / peak, "traffic": measured_traffic(n_vis), "kernel": "stack_mixed",
+                         "frac": achieved / peak, "traffic": measured_traffic(n_vis, args.config), "kernel": "stack_mixed",
                          "algorithmic_bytes_per_launch": alg, "kernel_ms": stack_ms,
                          "peak_source": peak_kind},
             "prepass_ms": tm["prepass_ms"],

@@ -27,7 +27,7 @@ std::vector<LaunchCfg> candidates(const LaunchCfg &cur)
         c.push_back(LaunchCfg{rows, cpl, wpc, cur.sort_rows, pf});
     };
     add(cur.rows_per_item, cur.chans_per_lane, cur.warps_per_cta, cur.prefetch_rows);
-    const int rows[] = {48, 32, 64, 96};
+    const int rows[] = {64, 48, 32, 96};
     const int pfs[] = {4, 2, 8};
     for (int cpl : {1, 2})
         for (int pf : pfs)

@@ -102,7 +102,7 @@ struct vista_stack {
     int nwaves = 0;                      // waves of host-memory windows of the last run (0: none)
     int64_t wave_bytes = 0;              // staged bytes per wave (0: the library's rule)
     cudaEvent_t slot_ev[2] = {};         // a staging slot's wave has been stacked
-    vista::LaunchCfg cfg{48, 1, 4, 1, 4};
+    vista::LaunchCfg cfg{64, 1, 4, 1, 4};
     // CUDA-graph replay of the device pass while the source set is unchanged
     bool graphs = true;
     bool plan_valid = false;             // device tables hold the plan of `plan_sig`

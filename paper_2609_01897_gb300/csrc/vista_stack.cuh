@@ -9,10 +9,17 @@
 // item's row records, chunk cells, window header, channel table and work-list
 // entries into the other shared-memory slot, so an item starts without a
 // global round trip.  Inside an item the visibilities and flags of the next
-// D - 1 rows are in flight into a shared-memory ring (cp.async; each lane
-// copies its own values and the 4-byte flag word that holds its flags: a
-// chunk's flags start on a word, see flag_align_channels), so the row loop
-// waits on no synchronous global load and no lane reads what another copied.
+// D - 1 rows are in flight into a shared-memory ring (cp.async), so the row
+// loop waits on no synchronous global load.  Each lane copies the 4-byte flag
+// word that holds its flags (a chunk's flags start on a word, see
+// flag_align_channels) and, when a lane's values are at most 16 bytes, its
+// own values.  Wider values (four pols, or complex128) are copied in 16-byte
+// pieces with piece i of lane L at byte 512 i + 16 L of the row's channel
+// slot, so that every cp.async instruction of the warp reads 512 contiguous
+// bytes (a lane copying its own 32 bytes as two pieces would make each
+// instruction read half of every 32-byte sector, and fetch each sector from
+// L2 twice); the warp then synchronises before a row's values are read and
+// before their ring slot is refilled.
 //
 // Per (row, channel): the FP32 phasor of Eq. 2 from the record's float-float
 // delay and the channel's float-float nu_k / c, the uv cell from the chunk's
@@ -163,6 +170,7 @@ __global__ void __launch_bounds__(KMAX_THREADS) stack_mixed(RunArgs a)
     }
     __syncwarp();
     const uint32_t vring_lane = smem_addr(vring) + (uint32_t)lane * LB;
+    const uint32_t vring_base = smem_addr(vring);
     const unsigned char *vring_lane_p = vring + lane * LB;
     const uint32_t fring_lane = smem_addr(vring) + (uint32_t)(D * NS * 32 * LB) + 4u * (uint32_t)lane;
 
@@ -300,6 +308,10 @@ __global__ void __launch_bounds__(KMAX_THREADS) stack_mixed(RunArgs a)
         float nh[NS], nl[NS];
         bool act[NS];
         int kv[NS], fo[NS], fsh[NS];
+        // wide values: the row offsets of the 16-byte pieces this lane copies
+        // (pieces past the chunk's last channel re-read that channel's bytes)
+        constexpr int NPC = LB >= 32 ? LB / 16 : 1;
+        int gv[NS][NPC];
 #pragma unroll
         for (int q = 0; q < NS; ++q) {
             const int kk = q * 32 + lane, kc = min(kk, nch - 1);
@@ -310,6 +322,11 @@ __global__ void __launch_bounds__(KMAX_THREADS) stack_mixed(RunArgs a)
             kv[q] = kc * LB;
             fo[q] = ((kc * P) & ~3) - ((min(lane, nch - 1) * P) & ~3);
             fsh[q] = 8 * ((kc * P) & 3);
+#pragma unroll
+            for (int i = 0; i < NPC; ++i) {
+                const int g = 512 * i + 16 * lane, ch = q * 32 + g / LB;
+                gv[q][i] = ch < nch ? q * 32 * LB + g : (nch - 1) * LB + g % LB;
+            }
             if (act[q]) n_read += (uint32_t)(n * npl);
         }
 
@@ -460,8 +477,16 @@ __global__ void __launch_bounds__(KMAX_THREADS) stack_mixed(RunArgs a)
             const uint32_t row = rb[i].row;
             const unsigned char *vrow = vis0 + (uint64_t)row * vrow_bytes;
 #pragma unroll
-            for (int q = 0; q < NS; ++q)
-                VA::copy(vring_lane + (uint32_t)((d * NS + q) * 32 * LB), vrow + kv[q]);
+            for (int q = 0; q < NS; ++q) {
+                if constexpr (LB >= 32) {
+#pragma unroll
+                    for (int i = 0; i < NPC; ++i)
+                        cp_async_16(vring_base + (uint32_t)((d * NS + q) * 32 * LB + 512 * i + 16 * lane),
+                                    vrow + gv[q][i]);
+                } else {
+                    VA::copy(vring_lane + (uint32_t)((d * NS + q) * 32 * LB), vrow + kv[q]);
+                }
+            }
             const uint8_t *frow = fw0 + (uint64_t)row * frow_bytes;
 #pragma unroll
             for (int q = 0; q < NS; ++q) cp_async_4(fring_lane + (uint32_t)(d * FWD * 4 + 128 * q), frow + fo[q]);
@@ -516,9 +541,11 @@ __global__ void __launch_bounds__(KMAX_THREADS) stack_mixed(RunArgs a)
         for (;;) {
 #pragma unroll 1
             while (i < n && count < 32u) {
+                if constexpr (LB >= 32) __syncwarp();   // every lane is done with the slot refilled next
                 fetch((i + D - 1) & (D - 1), min(i + D - 1, n - 1));
                 cp_async_commit();
                 cp_async_wait<D - 1>();
+                if constexpr (LB >= 32) __syncwarp();   // the row's pieces were copied by other lanes
                 body(i, i & (D - 1));
                 ++i;
             }

@@ -50,8 +50,6 @@ def test_batched_full_twice_mixed_against_fp64(V):
     for prec in (V.PREC_MIXED, V.PREC_FP64):
         st = V.Stack(wl.nu, wl.nv, wl.nrest, wl.npol, wl.du, wl.dv, central_freq=wl.central_freq, precision=prec)
         try:
-            if prec == V.PREC_MIXED:
-                st.set_tuning(rows_per_item=48, chans_per_lane=1, warps_per_cta=4, sort_rows=1, prefetch_rows=4)
             for _ in range(2):
                 for s in wl.spws:
                     st.add_source(s.uvw, s.freqs, s.vis, s.weights, s.flags, l=s.l, m=s.m, z=s.z,
