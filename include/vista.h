@@ -72,10 +72,12 @@ typedef struct vista_stack vista_stack;   /* opaque handle */
  *   precision  VISTA_PREC_MIXED: FP64 geometry and tables (the delay of
  *              each row kept as a float-float pair), FP32 per-visibility
  *              body, an FP32 cube whose entries are moved into an FP64 master
- *              cube at checkpoints spread over the drains (measured within
- *              ~7e-6 relative on the deepest entries of a 3.8e11-visibility
- *              stack); VISTA_PREC_FP64: the plain form, FP64 throughout with
- *              an FP64 cube.
+ *              cube at checkpoints spread over the drains and folded into it
+ *              wholly after a run once 64 visibilities per cube entry have
+ *              been stacked since the last fold (measured within 4.3e-6
+ *              relative on every entry of a 3.8e11-visibility stack, and the
+ *              same after stacking it twice); VISTA_PREC_FP64: the plain
+ *              form, FP64 throughout with an FP64 cube.
  *   hermitian_fold  1: rows with v < 0 (or v == 0, u < 0) are negated and
  *              their shifted visibility conjugated before binning.
  *   stream     cudaStream_t for all device work (NULL = legacy default stream). */

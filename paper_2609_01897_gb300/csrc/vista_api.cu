@@ -441,6 +441,7 @@ extern "C" int vista_zero_cube(vista_stack *h)
     if (e == cudaSuccess) e = cudaMemsetAsync(h->stats, 0, sizeof(DevStats), h->stream);
     if (e != cudaSuccess) return cuda_fail(h, e, "cube zeroing");
     h->host_nvis = 0;
+    h->nvis_since_fold = 0;
     return VISTA_OK;
 }
 

@@ -93,6 +93,7 @@ struct vista_stack {
     int64_t nentries = 0;
     vista::DevStats *stats = nullptr;
     uint64_t host_nvis = 0;   // visibilities read, counted from the channel tables at each run
+    uint64_t nvis_since_fold = 0;   // mixed: visibilities stacked since the FP32 partials were last folded
     int32_t *err = nullptr;
     vista::DevBuf b_srcs, b_chf, b_chd, b_recs, b_cells, b_off, b_stage, b_unpack, b_sort, b_rot, b_guvw, b_regrid,
         b_contsub;

@@ -231,6 +231,8 @@ cudaError_t launch_fp64(const RunArgs &a, cudaStream_t st);
 // The gridding baselines R (u, v, w) of the class's re-projected windows
 // (a.rot non-null; one thread per row of the class), for the FP64 form.
 cudaError_t launch_rotate(const RunArgs &a, cudaStream_t st);
+// Mixed cube: move every FP32 partial into the FP64 master and clear it.
+cudaError_t launch_fold(void *cube, double *master, int64_t n, cudaStream_t st);
 cudaError_t launch_unpack(const void *cube, const double *master, const uint32_t *count, int fp64, int64_t n,
                           void *sum_wv, void *sum_w, void *sum_wvv, uint32_t *cnt_out,
                           int out_f64, cudaStream_t st);

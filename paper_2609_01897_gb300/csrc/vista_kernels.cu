@@ -237,6 +237,36 @@ cudaError_t launch_fp64(const RunArgs &a, cudaStream_t st)
     return cudaGetLastError();
 }
 
+// ------------------------------------------------------------------ fold
+
+// Every nonzero FP32 entry of the mixed cube is added to its FP64 master
+// entry and cleared (the exact widening of each component), so the FP32
+// partials start again from zero.  Nothing else touches the cube meanwhile
+// (the handle's stream orders it after the run's stacking).
+__global__ void fold_kernel(float4 *cube, double *master, int64_t n)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const float4 c = cube[i];
+        if (c.x != 0.f || c.y != 0.f || c.z != 0.f || c.w != 0.f) {
+            double *m = master + 4 * i;
+            m[0] += (double)c.x;
+            m[1] += (double)c.y;
+            m[2] += (double)c.z;
+            m[3] += (double)c.w;
+            cube[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+    }
+}
+
+cudaError_t launch_fold(void *cube, double *master, int64_t n, cudaStream_t st)
+{
+    if (n == 0) return cudaSuccess;
+    int64_t blocks = (n + 255) / 256;
+    if (blocks > 152 * 16) blocks = 152 * 16;
+    fold_kernel<<<(unsigned)blocks, 256, 0, st>>>(reinterpret_cast<float4 *>(cube), master, n);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_unpack(const void *cube, const double *master, const uint32_t *count, int fp64, int64_t n,
                           void *sum_wv, void *sum_w, void *sum_wvv, uint32_t *cnt_out, int out_f64, cudaStream_t st)
 {

@@ -279,6 +279,26 @@ std::vector<uint8_t> run_signature(const vista_stack *h)
 
 }  // namespace
 
+// The mixed cube's FP32 partials are folded into the FP64 master once the
+// visibilities stacked since the last fold reach FOLD_DEPTH per cube entry:
+// an entry's FP32 sum then holds at most the contributions of one such
+// interval (and, inside it, those since the entry's last checkpoint), so its
+// rounding does not grow with the depth of the stack.  A fold reads the
+// float4 cube once and the master entries of the touched entries (about
+// 16 + 80 x touched / entries bytes per entry): at 64 visibilities per entry
+// between folds, below 2 bytes per 9-byte visibility.
+constexpr uint64_t FOLD_DEPTH = 64;
+
+static cudaError_t after_run(vista_stack *h, uint64_t nvis)
+{
+    if (h->desc.precision == VISTA_PREC_FP64 || !h->cube_master) return cudaSuccess;
+    h->nvis_since_fold += nvis;
+    if (h->nvis_since_fold < FOLD_DEPTH * (uint64_t)h->nentries) return cudaSuccess;
+    h->nvis_since_fold = 0;
+    if (h->timing) h->tacc.launches += 1;
+    return launch_fold(h->cube, h->cube_master, h->nentries, h->stream);
+}
+
 extern "C" int vista_run(vista_stack *h)
 {
     if (!handle_live(h)) return fail(nullptr, VISTA_E_STATE, "unknown or closed handle");
@@ -310,6 +330,7 @@ extern "C" int vista_run(vista_stack *h)
             }
         }
         if ((e = cudaGraphLaunch(h->gexec, h->stream)) != cudaSuccess) return cuda_fail(h, e, "graph launch");
+        if ((e = after_run(h, h->plan_nvis)) != cudaSuccess) return cuda_fail(h, e, "cube fold");
         ++h->graph_launches;
         h->host_nvis += h->plan_nvis;
         h->last = std::move(h->pending);
@@ -655,6 +676,10 @@ extern "C" int vista_run(vista_stack *h)
     if ((e = (nwaves > 0 ? streamed_pass(h) : device_pass(h, h->stream))) != cudaSuccess) {
         h->plan_valid = false;
         return cuda_fail(h, e, "kernel launch or host-to-device copy");
+    }
+    if ((e = after_run(h, nvis_run)) != cudaSuccess) {
+        h->plan_valid = false;
+        return cuda_fail(h, e, "cube fold");
     }
     if (h->timing) h->tacc.runs += 1;
     h->host_nvis += nvis_run;

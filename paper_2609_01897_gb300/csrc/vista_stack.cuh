@@ -46,7 +46,7 @@ constexpr int KMAX_THREADS = 256;   // blocks of at most 8 warps
 template <int NS>
 __host__ __device__ constexpr int stage_cap() { return NS == 1 ? 64 : NS == 2 ? 128 : 256; }
 constexpr uint32_t CKPT_EVERY = 8;     // valid runs of a lane between checkpoint choices (a power of two)
-constexpr uint32_t SERVICE_EVERY = 8;  // 1 / probability that a drain exchanges the chosen entries (a power of two)
+constexpr uint32_t SERVICE_EVERY = 4;  // 1 / probability that a drain exchanges the chosen entries (a power of two)
 constexpr int NO_RUN = INT_MIN;     // lane holds no run
 
 // What a window without flags reads as its flags (every row: pitch 0).
