@@ -59,6 +59,9 @@ def parse():
                         "host copies fit (GB)")
     p.add_argument("--cpu-sample", type=int, default=40,
                    help="windows timed once in the oracle baseline of our arm (0 = skip)")
+    p.add_argument("--cpu-gb", type=float, default=56.0,
+                   help="host memory the oracle baseline may take: its FP64 cube (40 B per entry) plus the "
+                        "sampled windows (GB); windows past it are left out, and a larger cube skips the leg")
     p.add_argument("--ref-sample", type=int, default=8, help="windows per step of the reference (oracle) arm")
     p.add_argument("--tuning", default="", help="rows,chans_per_lane,warps,sort,prefetch")
     p.add_argument("--regrid-reps", type=int, default=3,
@@ -365,10 +368,19 @@ def windows_in_cube(wl, f0, df, n):
     return out
 
 
-def cpu_baseline(wl, f0, df, nsample):
+def cpu_baseline(wl, f0, df, nsample, host_gb):
     from oracle import oracle as O
-    srcs = []
+    cube_b = wl.nu * wl.nv * wl.nrest * wl.npol * 40
+    if cube_b > host_gb * 1e9:
+        return {"skipped": "the oracle's FP64 cube would take %.0f GB of host memory (--cpu-gb %.0f)" % (
+            cube_b / 1e9, host_gb)}
+    srcs, used = [], cube_b
     for s in windows_in_cube(wl, f0, df, nsample):
+        b = s.vis.numel() * max(8, vis_bytes(s.vis)) + s.uvw.numel() * 8 + s.weights.numel() * 4 + (
+            0 if s.flags is None else s.flags.numel())
+        if srcs and used + b > host_gb * 1e9:
+            break
+        used += b
         srcs.append(O.Source(s.uvw.cpu().numpy(), s.freqs, host_vis(s), s.weights.cpu().numpy(),
                              None if s.flags is None else s.flags.cpu().numpy(), s.l, s.m, s.z, s.pol_map,
                              radec=s.radec))
@@ -459,7 +471,7 @@ def run_ours(args):
 
     cpu = None
     if rank == 0 and ws == 1 and args.cpu_sample > 0:
-        cpu = cpu_baseline(wl, f0, df, args.cpu_sample)
+        cpu = cpu_baseline(wl, f0, df, args.cpu_sample, args.cpu_gb)
 
     if rank == 0:
         line = {

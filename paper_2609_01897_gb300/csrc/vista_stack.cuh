@@ -297,7 +297,14 @@ __global__ void __launch_bounds__(KMAX_THREADS) stack_mixed(RunArgs a)
             for (int p = 0; p < P; ++p) plane[p] = H.plane[p];
             cb = S.cells + (I.cell0 & 1);
         }
-        const bool pack2 = (P == 2) && plane[0] >= 0 && plane[1] == plane[0] + 1 && !(plane[0] & 1) && !(npol_c & 1);
+        // pol pairs (2k, 2k + 1) whose count entries are adjacent and 8-byte
+        // aligned take one u64 reduction for both counts
+        constexpr int NPK = P >= 2 ? P / 2 : 1;
+        bool pk[NPK];
+#pragma unroll
+        for (int k = 0; k < NPK; ++k)
+            pk[k] = P >= 2 && plane[2 * k] >= 0 && plane[2 * k + 1] == plane[2 * k] + 1 && !(plane[2 * k] & 1) &&
+                    !(npol_c & 1);
         int npl = 0;
 #pragma unroll
         for (int p = 0; p < P; ++p) npl += plane[p] >= 0;
@@ -407,15 +414,19 @@ __global__ void __launch_bounds__(KMAX_THREADS) stack_mixed(RunArgs a)
                             const float4 v = st.acc[p];
                             atomicAdd(cube4 + e2 + plane[p], make_float4(ww * v.x, ww * v.y, ww * v.z, ww * v.w));
                             ++n_red;
-                            if (!pack2) {
+                            if (!(P >= 2 && pk[p / 2])) {
                                 atomicAdd(a.count + e2 + plane[p], st.cnt[p]);
                                 ++n_red;
                             }
                         }
-                        if (pack2 && (st.cnt[0] | st.cnt[P - 1])) {
-                            atomicAdd(reinterpret_cast<unsigned long long *>(a.count + e2 + plane[0]),
-                                      (unsigned long long)st.cnt[0] | ((unsigned long long)st.cnt[P - 1] << 32));
-                            ++n_red;
+#pragma unroll
+                        for (int k = 0; k < (P >= 2 ? P / 2 : 0); ++k) {
+                            if (pk[k] && (st.cnt[2 * k] | st.cnt[2 * k + 1])) {
+                                atomicAdd(reinterpret_cast<unsigned long long *>(a.count + e2 + plane[2 * k]),
+                                          (unsigned long long)st.cnt[2 * k] |
+                                              ((unsigned long long)st.cnt[2 * k + 1] << 32));
+                                ++n_red;
+                            }
                         }
                     }
                     if (comp && ((++n_runs & (CKPT_EVERY - 1)) == 0)) {
