@@ -450,6 +450,17 @@ def run_ours(args):
         del part, total
     st.close()
 
+    # end to end through the C ABI with host buffers, straight after the timed
+    # steps: run after the FP64 leg (~50 s) the same steps took 1.6x as long
+    # as alone, for reasons outside this program
+    e2e = None
+    if args.e2e_steps > 0:
+        try:
+            e2e = run_e2e(args, wl, tuning, f0, df, ws)
+        except (RuntimeError, MemoryError) as exc:
+            e2e = {"error": str(exc)[:200]}
+    link = host_link_peak() if rank == 0 and args.e2e_steps > 0 else None
+
     # plain FP64 GPU form on the same inputs
     fp64 = None
     if args.fp64_steps > 0:
@@ -459,15 +470,6 @@ def run_ours(args):
         ms64 = allmax(ws, ms64)
         fp64 = {"value": n_vis_all / (ms64 * 1e-3), "unit": UNIT, "ms_per_step": ms64,
                 "speedup_mixed_vs_fp64": ms64 / ms_max}
-
-    # end to end through the C ABI with host buffers
-    e2e = None
-    if args.e2e_steps > 0:
-        try:
-            e2e = run_e2e(args, wl, tuning, f0, df, ws)
-        except (RuntimeError, MemoryError) as exc:
-            e2e = {"error": str(exc)[:200]}
-    link = host_link_peak() if rank == 0 and args.e2e_steps > 0 else None
 
     cpu = None
     if rank == 0 and ws == 1 and args.cpu_sample > 0:
@@ -571,9 +573,10 @@ def to_pinned(t):
 
 
 def window_io(s, f0, df, nrest):
-    """(in-cube visibilities, bytes vista_run copies host->device) of one
-    window: uvw and weights of every row, and the channels it reads (the
-    in-cube range rounded out to whole flag words) of vis and flags."""
+    """(in-cube visibilities, the least bytes a host copy of one window needs):
+    uvw and weights of every row, and the channels read (the in-cube range
+    rounded out to whole flag words) of vis and flags.  vista_run may copy
+    more (whole flag rows); the e2e figure reports what it copied."""
     from paper_2609_01897_gb300 import vista as V
     _, nb, _ = V.plan_channels(s.freqs, s.z, f0, df, nrest, V.BIN_OVERLAP)
     nrow, nch, npol = (int(x) for x in s.vis.shape[:3])
@@ -639,6 +642,7 @@ def run_e2e(args, wl, tuning, f0, df, ws):
             split = {"queue_ms": (tb - ta) * 1e3, "device_ms": (tc - tb) * 1e3, "readback_ms": (td - tc) * 1e3}
     dt = (time.perf_counter() - t0) / args.e2e_steps
     d2h = sum(v.numel() * v.element_size() for v in outs.values())
+    h2d = ste.h2d_bytes()   # what vista_run copied for the windows (the last step's; every step's is the same)
     ste.close()
     dt = allmax(ws, dt)
     n_in = sum(1 for s in wl.spws if window_io(s, f0, df, wl.nrest)[0] > 0)

@@ -34,8 +34,9 @@
 extern "C" {
 #endif
 
-#define VISTA_ABI_VERSION 3   /* 2: vista_add_source_reproject, vista_regrid_rows;
-                                 3: vista_contsub, vista_set_wave_bytes, vista_get_waves */
+#define VISTA_ABI_VERSION 4   /* 2: vista_add_source_reproject, vista_regrid_rows;
+                                 3: vista_contsub, vista_set_wave_bytes, vista_get_waves;
+                                 4: vista_get_h2d_bytes */
 #define VISTA_MAX_BINS 4      /* rest bins one input channel may touch */
 #define VISTA_MAX_POL 4
 
@@ -245,6 +246,12 @@ int vista_set_wave_bytes(vista_stack *h, int64_t bytes);
 /* The number of waves the last vista_run() streamed its host-memory windows
  * in (0: it had none). */
 int vista_get_waves(vista_stack *h, int32_t *out);
+/* The host-to-device bytes the last vista_run() copied for its host-memory
+ * windows (0: none): uvw, weights, and the channels of vis and flags that
+ * it reads -- a window's flags go as whole rows when they are whole 4-byte
+ * words and at most four times the words read (or 16 MB in all), since a
+ * copy of narrow rows runs far below the host link's rate. */
+int vista_get_h2d_bytes(vista_stack *h, int64_t *out);
 
 /* Wait for the stream, then copy the cube out.  The arrays are the two
  * sums of Eq. 3 per cube entry (numerator sum W w_kj V', denominator

@@ -430,6 +430,16 @@ extern "C" int vista_get_waves(vista_stack *h, int32_t *out)
     return VISTA_OK;
 }
 
+extern "C" int vista_get_h2d_bytes(vista_stack *h, int64_t *out)
+{
+    CHECK_HANDLE(h);
+    if (!out) return fail(h, VISTA_E_ARG, "null output");
+    int64_t n = 0;
+    for (const HostCopy &c : h->hcopies) n += (int64_t)(c.width * c.height);
+    *out = n;
+    return VISTA_OK;
+}
+
 extern "C" int vista_zero_cube(vista_stack *h)
 {
     CHECK_HANDLE(h);

@@ -373,11 +373,24 @@ extern "C" int vista_run(vista_stack *h)
     // 3. waves of host-memory windows (by staged bytes, about a quarter of
     //    them each, 64 MB to 2 GB), then the launch classes, wave by wave
     //    (windows with no row or no channel in the cube are skipped)
+    // A host window's flags are staged as whole rows with one contiguous copy
+    // when its rows are whole words and not much wider than the channels
+    // read (or the whole array is small): a 2-D copy of narrow rows runs far
+    // below the host link's rate.  The kernel then reads them at the
+    // in-cube channel offset.
+    auto full_flag_rows = [&](int i) {
+        const SrcHost &s = h->pending[(size_t)i];
+        const int32_t nin = plans[(size_t)i].k_hi - plans[(size_t)i].k_lo;
+        const size_t row_in = (size_t)s.d.nchan * (size_t)s.d.npol, fp = (size_t)flag_pitch(nin, s.d.npol);
+        return s.d.flags && row_in % 4 == 0 && (row_in <= 4 * fp || (size_t)s.d.nrow * row_in <= ((size_t)16 << 20));
+    };
     auto staged_bytes = [&](int i) {
         const SrcHost &s = h->pending[(size_t)i];
         const size_t nr = (size_t)s.d.nrow;
         const int32_t nin = plans[(size_t)i].k_hi - plans[(size_t)i].k_lo;
-        const size_t fbytes = s.d.flags ? al256(nr * (size_t)flag_pitch(nin, s.d.npol)) : 0;
+        const size_t fbytes = !s.d.flags ? 0
+                              : full_flag_rows(i) ? al256(nr * (size_t)s.d.nchan * (size_t)s.d.npol)
+                                                  : al256(nr * (size_t)flag_pitch(nin, s.d.npol));
         return al256(nr * 24) + al256(nr * (size_t)nin * (size_t)s.d.npol * vis_elem_bytes(s.d.vis_type)) +
                al256(nr * 4 * (size_t)s.d.npol) + fbytes;
     };
@@ -520,17 +533,20 @@ extern "C" int vista_run(vista_stack *h)
                 char *p_w = base + pos;
                 pos += al256(nr * 4 * P);
                 char *p_f = nullptr;
-                const size_t fp = (size_t)flag_pitch(nin, s.d.npol);
+                const size_t row_in = (size_t)s.d.nchan * P, row_out = (size_t)nin * P;
+                const bool whole = full_flag_rows(i);
+                const size_t fp = whole ? row_in : (size_t)flag_pitch(nin, s.d.npol);
                 if (s.d.flags) {
                     p_f = base + pos;
                     pos += al256(nr * fp);
                 }
-                const size_t row_in = (size_t)s.d.nchan * P, row_out = (size_t)nin * P;
                 hcopies.push_back(HostCopy{wv, p_uvw, nr * 24, s.d.uvw, nr * 24, nr * 24, 1});
                 hcopies.push_back(HostCopy{wv, p_vis, row_out * esz, (const char *)s.d.vis + (size_t)pl.k_lo * P * esz,
                                            row_in * esz, row_out * esz, nr});
                 hcopies.push_back(HostCopy{wv, p_w, nr * 4 * P, s.d.weights, nr * 4 * P, nr * 4 * P, 1});
-                if (p_f)
+                if (p_f && whole)
+                    hcopies.push_back(HostCopy{wv, p_f, nr * row_in, s.d.flags, nr * row_in, nr * row_in, 1});
+                else if (p_f)
                     hcopies.push_back(HostCopy{wv, p_f, fp, s.d.flags + (size_t)pl.k_lo * P, row_in, row_out, nr});
                 d.uvw = (const double *)p_uvw;
                 d.vis = p_vis;
@@ -539,7 +555,7 @@ extern "C" int vista_run(vista_stack *h)
                 d.kbase = pl.k_lo;
                 d.fbase = (const uint8_t *)p_f;
                 d.fpitch = (int64_t)fp;
-                d.fk0 = pl.k_lo;
+                d.fk0 = whole ? 0 : pl.k_lo;
             } else if (repack_flags(s)) {
                 const size_t nr = (size_t)s.d.nrow, P = (size_t)s.d.npol;
                 const size_t fp = (size_t)flag_pitch(nin, s.d.npol);

@@ -80,6 +80,7 @@ SIGNATURES = {
     "vista_contsub": (C.c_int, [_P, _P, C.c_int32, _P, C.c_int]),
     "vista_set_wave_bytes": (C.c_int, [_P, C.c_int64]),
     "vista_get_waves": (C.c_int, [_P, C.POINTER(C.c_int32)]),
+    "vista_get_h2d_bytes": (C.c_int, [_P, C.POINTER(C.c_int64)]),
     "vista_run": (C.c_int, [_P]),
     "vista_read_cube": (C.c_int, [_P, _P, _P, _P, _P, C.c_int]),
     "vista_read_cube_f64": (C.c_int, [_P, _P, _P, _P, _P, C.c_int]),
@@ -300,6 +301,12 @@ class Stack:
         """Waves the last run streamed its host-memory windows in."""
         n = C.c_int32(0)
         _check("vista_get_waves", lib().vista_get_waves(self.h, C.byref(n)), self.h)
+        return int(n.value)
+
+    def h2d_bytes(self):
+        """Host-to-device bytes the last run copied for its host-memory windows."""
+        n = C.c_int64(0)
+        _check("vista_get_h2d_bytes", lib().vista_get_h2d_bytes(self.h, C.byref(n)), self.h)
         return int(n.value)
 
     def stats(self):
