@@ -53,7 +53,7 @@ def parse():
     p.add_argument("--nrest", type=int, default=0,
                    help="batched: rest channels of the cube (0 = 1024; fewer gives a smaller cube for captures)")
     p.add_argument("--fp64-steps", type=int, default=1, help="timed steps of the plain FP64 leg (0 = skip)")
-    p.add_argument("--e2e-steps", type=int, default=2, help="timed host-memory steps (0 = skip)")
+    p.add_argument("--e2e-steps", type=int, default=4, help="timed host-memory steps (0 = skip)")
     p.add_argument("--e2e-gb", type=float, default=24.0,
                    help="pinned host memory for the end-to-end leg: windows are taken in order while their "
                         "host copies fit (GB)")
@@ -433,6 +433,16 @@ def run_ours(args):
     peak, peak_kind = measured_peaks()
     achieved = alg / (stack_ms * 1e-3) / 1e9 if stack_ms > 0 else 0.0
     launches = int(round(tm["launches"])) * args.steps
+    # end to end through the C ABI with host buffers, straight after the timed
+    # steps (after the other legs the same steps have taken up to twice as
+    # long on this shared machine)
+    e2e = None
+    if args.e2e_steps > 0:
+        try:
+            e2e = run_e2e(args, wl, tuning, f0, df, ws)
+        except (RuntimeError, MemoryError) as exc:
+            e2e = {"error": str(exc)[:200]}
+    link = host_link_peak() if rank == 0 and args.e2e_steps > 0 else None
     regrid = time_regrid(st, wl, f0, df, args.regrid_reps, peak) if args.regrid_reps > 0 else None
     contsub = time_contsub(st, wl, args.contsub_reps, peak) if args.contsub_reps > 0 else None
     # several GPUs: the final reduce-sum of the partial cubes into rank 0 (after the timed region)
@@ -450,16 +460,6 @@ def run_ours(args):
         del part, total
     st.close()
 
-    # end to end through the C ABI with host buffers, straight after the timed
-    # steps: run after the FP64 leg (~50 s) the same steps took 1.6x as long
-    # as alone, for reasons outside this program
-    e2e = None
-    if args.e2e_steps > 0:
-        try:
-            e2e = run_e2e(args, wl, tuning, f0, df, ws)
-        except (RuntimeError, MemoryError) as exc:
-            e2e = {"error": str(exc)[:200]}
-    link = host_link_peak() if rank == 0 and args.e2e_steps > 0 else None
 
     # plain FP64 GPU form on the same inputs
     fp64 = None
