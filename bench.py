@@ -630,16 +630,21 @@ def run_e2e(args, wl, tuning, f0, df, ws):
         ta = time.perf_counter()
         one_step(ste, sub)
         tb = time.perf_counter()
-        if it >= 1 and args.e2e_steps > 1 and it == args.e2e_steps:
-            # the last step also splits its time (the wait costs nothing extra:
-            # read_cube waits for the stream anyway)
+        if it == 0:
+            # the pinned result buffers are allocated once (first, untimed step)
+            outs = ste.read_cube(device=False, out=outs)
+        elif it < args.e2e_steps:
+            # every step reads its cube back; the copy overlaps the next step's
+            ste.read_cube_async(outs)
+        else:
+            # the last step also splits its time: its run, then its readback
             torch.cuda.current_stream().synchronize()
-        tc = time.perf_counter()
-        # the pinned result buffers are allocated once (first, untimed step)
-        outs = ste.read_cube(device=False, out=outs)
-        td = time.perf_counter()
-        if it >= 1 and it == args.e2e_steps:
+            tc = time.perf_counter()
+            ste.read_cube_async(outs)
+            ste.wait_readback()
+            td = time.perf_counter()
             split = {"queue_ms": (tb - ta) * 1e3, "device_ms": (tc - tb) * 1e3, "readback_ms": (td - tc) * 1e3}
+    ste.wait_readback()
     dt = (time.perf_counter() - t0) / args.e2e_steps
     d2h = sum(v.numel() * v.element_size() for v in outs.values())
     h2d = ste.h2d_bytes()   # what vista_run copied for the windows (the last step's; every step's is the same)

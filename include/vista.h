@@ -34,9 +34,10 @@
 extern "C" {
 #endif
 
-#define VISTA_ABI_VERSION 4   /* 2: vista_add_source_reproject, vista_regrid_rows;
+#define VISTA_ABI_VERSION 5   /* 2: vista_add_source_reproject, vista_regrid_rows;
                                  3: vista_contsub, vista_set_wave_bytes, vista_get_waves;
-                                 4: vista_get_h2d_bytes */
+                                 4: vista_get_h2d_bytes;
+                                 5: vista_read_cube_async, vista_wait_readback */
 #define VISTA_MAX_BINS 4      /* rest bins one input channel may touch */
 #define VISTA_MAX_POL 4
 
@@ -268,6 +269,23 @@ int vista_read_cube(vista_stack *h, float *sum_wv, float *sum_w, float *sum_wvv,
  * VISTA_PREC_FP64; widened from FP32 for VISTA_PREC_MIXED). */
 int vista_read_cube_f64(vista_stack *h, double *sum_wv, double *sum_w, double *sum_wvv,
                         uint32_t *count, int dst_is_device);
+
+/* vista_read_cube() into HOST arrays without waiting (a library convention;
+ * Eq. 3's sums as there): the cube as of the work queued so far is copied on
+ * the handle's stream into a device snapshot, and the snapshot's copy to the
+ * host arrays runs on a stream of its own, so it overlaps the runs queued
+ * after this call (their host-to-device copies and kernels).  The host
+ * arrays (pinned memory for an asynchronous copy) must stay valid and must
+ * not be read until vista_wait_readback() returns.  A later call first lets
+ * the previous copy finish before overwriting the snapshot; vista_read_cube()
+ * and vista_close() wait for it.  FP32 sums; any pointer may be NULL to skip
+ * that array (not all four).  Errors of the runs show in
+ * vista_wait_readback(). */
+int vista_read_cube_async(vista_stack *h, float *sum_wv, float *sum_w, float *sum_wvv, uint32_t *count);
+/* Wait until the last vista_read_cube_async() copy has reached the host;
+ * VISTA_OK at once when none is pending.  E_TIMEOUT if a device-side wait
+ * of an earlier run gave up. */
+int vista_wait_readback(vista_stack *h);
 
 /* Zero the cube and the counters (the lattice stays fixed). */
 int vista_zero_cube(vista_stack *h);

@@ -356,10 +356,20 @@ extern "C" int vista_add_source_reproject(vista_stack *h, const vista_source_des
 
 namespace {
 
+// Wait for a readback still copying out of b_unpack.
+cudaError_t finish_readback(vista_stack *h)
+{
+    if (!h->rb_pending) return cudaSuccess;
+    h->rb_pending = false;
+    return cudaEventSynchronize(h->rb_done);
+}
+
 int read_common(vista_stack *h, void *sum_wv, void *sum_w, void *sum_wvv, uint32_t *count, int dst_dev,
                 int out_f64)
 {
-    cudaError_t e = cudaStreamSynchronize(h->stream);
+    cudaError_t e = finish_readback(h);
+    if (e != cudaSuccess) return cuda_fail(h, e, "earlier readback");
+    e = cudaStreamSynchronize(h->stream);
     if (e != cudaSuccess) return cuda_fail(h, e, "stream synchronize");
     int32_t err = 0;
     e = cudaMemcpy(&err, h->err, sizeof err, cudaMemcpyDeviceToHost);
@@ -412,6 +422,62 @@ extern "C" int vista_read_cube_f64(vista_stack *h, double *sum_wv, double *sum_w
 {
     CHECK_HANDLE(h);
     return read_common(h, sum_wv, sum_w, sum_wvv, count, dst_is_device, 1);
+}
+
+extern "C" int vista_read_cube_async(vista_stack *h, float *sum_wv, float *sum_w, float *sum_wvv, uint32_t *count)
+{
+    CHECK_HANDLE(h);
+    if (!sum_wv && !sum_w && !sum_wvv && !count) return fail(h, VISTA_E_ARG, "no output array");
+    cudaError_t e = cudaSuccess;
+    if (!h->rb_stream) e = cudaStreamCreateWithFlags(&h->rb_stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess && !h->rb_ready) e = cudaEventCreateWithFlags(&h->rb_ready, cudaEventDisableTiming);
+    if (e == cudaSuccess && !h->rb_done) e = cudaEventCreateWithFlags(&h->rb_done, cudaEventDisableTiming);
+    if (e != cudaSuccess) return cuda_fail(h, e, "readback stream");
+    const int fp64 = h->desc.precision == VISTA_PREC_FP64;
+    const int64_t n = h->nentries;
+    const size_t b_wv = sum_wv ? (size_t)n * 8 : 0, b_w = sum_w ? (size_t)n * 4 : 0,
+                 b_vv = sum_wvv ? (size_t)n * 4 : 0, b_c = count ? (size_t)n * 4 : 0;
+    const size_t need = b_wv + b_w + b_vv + b_c + 64;
+    // a larger scratch area replaces the one the previous copy may still read
+    if (need > h->b_unpack.cap && (e = finish_readback(h)) != cudaSuccess)
+        return cuda_fail(h, e, "earlier readback");
+    if ((e = h->b_unpack.ensure(need)) != cudaSuccess) return cuda_fail(h, e, "readback scratch allocation");
+    char *p = (char *)h->b_unpack.p;
+    char *d_wv = sum_wv ? p : nullptr;
+    char *d_w = sum_w ? p + b_wv : nullptr;
+    char *d_vv = sum_wvv ? p + b_wv + b_w : nullptr;
+    uint32_t *d_c = count ? (uint32_t *)(p + b_wv + b_w + b_vv) : nullptr;
+    // the snapshot waits for the previous copy out of the scratch area, then
+    // follows the runs queued so far on the handle's stream
+    if (h->rb_pending) e = cudaStreamWaitEvent(h->stream, h->rb_done, 0);
+    if (e == cudaSuccess)
+        e = launch_unpack(h->cube, h->cube_master, h->count, fp64, n, d_wv, d_w, d_vv, d_c, 0, h->stream);
+    if (e == cudaSuccess) e = cudaEventRecord(h->rb_ready, h->stream);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(h->rb_stream, h->rb_ready, 0);
+    if (e == cudaSuccess && sum_wv) e = cudaMemcpyAsync(sum_wv, d_wv, b_wv, cudaMemcpyDeviceToHost, h->rb_stream);
+    if (e == cudaSuccess && sum_w) e = cudaMemcpyAsync(sum_w, d_w, b_w, cudaMemcpyDeviceToHost, h->rb_stream);
+    if (e == cudaSuccess && sum_wvv) e = cudaMemcpyAsync(sum_wvv, d_vv, b_vv, cudaMemcpyDeviceToHost, h->rb_stream);
+    if (e == cudaSuccess && count) e = cudaMemcpyAsync(count, d_c, b_c, cudaMemcpyDeviceToHost, h->rb_stream);
+    if (e == cudaSuccess) e = cudaEventRecord(h->rb_done, h->rb_stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "cube readback");
+    h->rb_pending = true;
+    return VISTA_OK;
+}
+
+extern "C" int vista_wait_readback(vista_stack *h)
+{
+    CHECK_HANDLE(h);
+    const bool was = h->rb_pending;
+    cudaError_t e = finish_readback(h);
+    if (e != cudaSuccess) return cuda_fail(h, e, "readback");
+    if (!was) return VISTA_OK;
+    // the runs before the snapshot have completed: their error word
+    int32_t err = 0;
+    e = cudaMemcpyAsync(&err, h->err, sizeof err, cudaMemcpyDeviceToHost, h->rb_stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->rb_stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "error word read");
+    if (err != 0) return device_fail(h, err);
+    return VISTA_OK;
 }
 
 extern "C" int vista_set_wave_bytes(vista_stack *h, int64_t bytes)
@@ -604,6 +670,16 @@ extern "C" int vista_close(vista_stack *h)
         if (h->xfer_ev[j]) cudaEventDestroy(h->xfer_ev[j]);
     for (int j = 0; j < 2; ++j)
         if (h->slot_ev[j]) cudaEventDestroy(h->slot_ev[j]);
+    if (h->rb_stream) {
+        cudaStreamSynchronize(h->rb_stream);
+        cudaStreamDestroy(h->rb_stream);
+    }
+    for (int j = 0; j < 2; ++j) {
+        if (h->pin_ev[j]) cudaEventDestroy(h->pin_ev[j]);
+        if (h->pin[j]) cudaFreeHost(h->pin[j]);
+    }
+    if (h->rb_ready) cudaEventDestroy(h->rb_ready);
+    if (h->rb_done) cudaEventDestroy(h->rb_done);
     cudaFree(h->cube);
     cudaFree(h->cube_master);
     cudaFree(h->count);

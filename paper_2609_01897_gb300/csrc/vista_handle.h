@@ -103,6 +103,18 @@ struct vista_stack {
     int nwaves = 0;                      // waves of host-memory windows of the last run (0: none)
     int64_t wave_bytes = 0;              // staged bytes per wave (0: the library's rule)
     cudaEvent_t slot_ev[2] = {};         // a staging slot's wave has been stacked
+    // readback without waiting (vista_read_cube_async): the snapshot in
+    // b_unpack is ready (rb_ready), its copy to the host is done (rb_done)
+    // pinned host staging of a run's table uploads, two halves used by
+    // alternate runs (a copy from pageable memory would wait for the stream,
+    // so planning the next run would wait for this one's device work)
+    void *pin[2] = {};
+    size_t pin_cap[2] = {};
+    cudaEvent_t pin_ev[2] = {};
+    int pin_half = 0;
+    cudaStream_t rb_stream = nullptr;
+    cudaEvent_t rb_ready = nullptr, rb_done = nullptr;
+    bool rb_pending = false;
     vista::LaunchCfg cfg{64, 1, 4, 1, 4};
     // CUDA-graph replay of the device pass while the source set is unchanged
     bool graphs = true;

@@ -14,6 +14,7 @@
 //      persistent stacking kernel; FP64 precision: the plain kernel
 #include <algorithm>
 #include <cmath>
+#include <cstring>
 #include <vector>
 
 #include "planner.h"
@@ -90,13 +91,53 @@ int plan_source(vista_stack *h, const SrcHost &s, double gu, double gv, Plan &pl
     return VISTA_OK;
 }
 
+// A run's table uploads go through one half of the handle's pinned staging
+// area: the half is reused two runs later, after its uploads have completed
+// (an event), and the copies from it return without waiting for the stream.
+struct Uploader {
+    vista_stack *h;
+    char *base = nullptr;
+    size_t pos = 0;
+    cudaError_t begin(size_t total)
+    {
+        const int x = h->pin_half;
+        cudaError_t e = cudaSuccess;
+        if (!h->pin_ev[x]) e = cudaEventCreateWithFlags(&h->pin_ev[x], cudaEventDisableTiming);
+        else e = cudaEventSynchronize(h->pin_ev[x]);   // this half's uploads of two runs ago
+        if (e == cudaSuccess && total > h->pin_cap[x]) {
+            if (h->pin[x]) cudaFreeHost(h->pin[x]);
+            h->pin[x] = nullptr;
+            h->pin_cap[x] = 0;
+            const size_t want = total + total / 8 + 4096;
+            e = cudaHostAlloc(&h->pin[x], want, cudaHostAllocDefault);
+            if (e == cudaSuccess) h->pin_cap[x] = want;
+        }
+        base = (char *)h->pin[x];
+        pos = 0;
+        return e;
+    }
+    template <typename T>
+    cudaError_t put(DevBuf &b, const std::vector<T> &v)
+    {
+        const size_t bytes = v.size() * sizeof(T);
+        cudaError_t e = b.ensure(bytes > 0 ? bytes : 16);
+        if (e != cudaSuccess || bytes == 0) return e;
+        std::memcpy(base + pos, v.data(), bytes);
+        e = cudaMemcpyAsync(b.p, base + pos, bytes, cudaMemcpyHostToDevice, h->stream);
+        pos += (bytes + 255) & ~(size_t)255;
+        return e;
+    }
+    cudaError_t end()
+    {
+        const cudaError_t e = cudaEventRecord(h->pin_ev[h->pin_half], h->stream);
+        h->pin_half ^= 1;
+        return e;
+    }
+};
 template <typename T>
-cudaError_t upload(DevBuf &b, const std::vector<T> &v, cudaStream_t st)
+size_t upload_bytes(const std::vector<T> &v)
 {
-    const size_t bytes = v.size() * sizeof(T);
-    cudaError_t e = b.ensure(bytes > 0 ? bytes : 16);
-    if (e != cudaSuccess || bytes == 0) return e;
-    return cudaMemcpyAsync(b.p, v.data(), bytes, cudaMemcpyHostToDevice, st);
+    return (v.size() * sizeof(T) + 255) & ~(size_t)255;
 }
 
 // Smallest channels-per-lane (1, 2, 4; at most cap) whose chunk holds nin
@@ -622,12 +663,17 @@ extern "C" int vista_run(vista_stack *h)
     }
 
     // uploads and buffers
-    if ((e = upload(h->b_srcs, sdev, h->stream)) != cudaSuccess) return cuda_fail(h, e, "source table upload");
-    if ((e = upload(h->b_chf, chf, h->stream)) != cudaSuccess) return cuda_fail(h, e, "channel table upload");
-    if ((e = upload(h->b_chd, chd, h->stream)) != cudaSuccess) return cuda_fail(h, e, "channel table upload");
-    if ((e = upload(h->b_off, offs, h->stream)) != cudaSuccess) return cuda_fail(h, e, "offset table upload");
-    if (!rots.empty() && (e = upload(h->b_rot, rots, h->stream)) != cudaSuccess)
+    Uploader up{h};
+    if ((e = up.begin(upload_bytes(sdev) + upload_bytes(chf) + upload_bytes(chd) + upload_bytes(offs) +
+                      upload_bytes(rots))) != cudaSuccess)
+        return cuda_fail(h, e, "pinned staging of the tables");
+    if ((e = up.put(h->b_srcs, sdev)) != cudaSuccess) return cuda_fail(h, e, "source table upload");
+    if ((e = up.put(h->b_chf, chf)) != cudaSuccess) return cuda_fail(h, e, "channel table upload");
+    if ((e = up.put(h->b_chd, chd)) != cudaSuccess) return cuda_fail(h, e, "channel table upload");
+    if ((e = up.put(h->b_off, offs)) != cudaSuccess) return cuda_fail(h, e, "offset table upload");
+    if (!rots.empty() && (e = up.put(h->b_rot, rots)) != cudaSuccess)
         return cuda_fail(h, e, "re-projection table upload");
+    if ((e = up.end()) != cudaSuccess) return cuda_fail(h, e, "pinned staging of the tables");
     if (!fp64) {
         if ((e = h->b_recs.ensure((size_t)(rec_total > 0 ? rec_total : 1) * sizeof(RowRec))) != cudaSuccess)
             return cuda_fail(h, e, "row record allocation");

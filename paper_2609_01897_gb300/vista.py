@@ -81,6 +81,8 @@ SIGNATURES = {
     "vista_set_wave_bytes": (C.c_int, [_P, C.c_int64]),
     "vista_get_waves": (C.c_int, [_P, C.POINTER(C.c_int32)]),
     "vista_get_h2d_bytes": (C.c_int, [_P, C.POINTER(C.c_int64)]),
+    "vista_read_cube_async": (C.c_int, [_P, _P, _P, _P, _P]),
+    "vista_wait_readback": (C.c_int, [_P]),
     "vista_run": (C.c_int, [_P]),
     "vista_read_cube": (C.c_int, [_P, _P, _P, _P, _P, C.c_int]),
     "vista_read_cube_f64": (C.c_int, [_P, _P, _P, _P, _P, C.c_int]),
@@ -275,6 +277,28 @@ class Stack:
                self.h)
         self._inflight = []
         return {k: v for k, v in out.items() if v is not None}
+
+    def read_cube_async(self, out):
+        """vista_read_cube_async: queue the cube's readback into the pinned
+        host tensors of `out` (a dict from read_cube(device=False)) and return
+        at once; call wait_readback() before reading them."""
+        nv, nu, nrest, npol = self.shape
+        shapes = {"sum_wv": (nv, nu, nrest, npol, 2), "sum_w": (nv, nu, nrest, npol),
+                  "sum_wvv": (nv, nu, nrest, npol), "count": (nv, nu, nrest, npol)}
+        for k, t in out.items():
+            if t is None:
+                continue
+            dt = torch.int32 if k == "count" else torch.float32
+            if t.is_cuda or tuple(t.shape) != shapes[k] or t.dtype != dt or not t.is_contiguous():
+                raise ValueError("out[%r] must be a contiguous host %s tensor of shape %s" % (k, dt, shapes[k]))
+        _check("vista_read_cube_async", lib().vista_read_cube_async(
+            self.h, _ptr(out.get("sum_wv")), _ptr(out.get("sum_w")), _ptr(out.get("sum_wvv")),
+            _ptr(out.get("count"))), self.h)
+        return out
+
+    def wait_readback(self):
+        _check("vista_wait_readback", lib().vista_wait_readback(self.h), self.h)
+        self._inflight = []
 
     def contsub(self, line_free, order=1, device=True, out=None):
         """Continuum-subtracted sum W w V' of the cube (vista_contsub): a

@@ -75,3 +75,39 @@ def test_streamed_equals_device_path(V):
     d = H.run_gpu(wl)
     np.testing.assert_array_equal(g["count"], d["count"])
     np.testing.assert_allclose(g["sum_w"], d["sum_w"], rtol=1e-6, atol=1e-6)
+
+
+def test_async_readback_overlaps_runs_and_matches(V):
+    """vista_read_cube_async after each streamed run (the next run's copies
+    overlap the previous readback): every readback equals the cube after its
+    run, read synchronously, and the oracle's sums times the run count."""
+    from paper_2609_01897_gb300 import synth
+    wl = synth.tiny("cuda")
+    st = V.Stack(wl.nu, wl.nv, wl.nrest, wl.npol, wl.du, wl.dv, rest_f0=wl.rest_f0, rest_df=wl.rest_df,
+                 central_freq=wl.central_freq)
+    try:
+        st.set_wave_bytes(1 << 20)
+        host = [[a.cpu().pin_memory() if isinstance(a, torch.Tensor) else a
+                 for a in (s.uvw, s.vis, s.weights, s.flags)] for s in wl.spws]
+        outs = [st.read_cube(device=False) for _ in range(3)]   # pinned buffers (a zero cube)
+        for r in range(3):
+            for s, (u, v, w, f) in zip(wl.spws, host):
+                st.add_source(u, s.freqs, v, w, f, l=s.l, m=s.m, z=s.z, pol_map=s.pol_map)
+            st.run()
+            st.read_cube_async(outs[r])          # returns at once; the next run is queued behind it
+        st.wait_readback()
+        final = st.read_cube(device=False)
+        assert st.h2d_bytes() > 0
+    finally:
+        st.close()
+    o = H.run_oracle(wl)
+    for r in range(3):
+        g = {k: v.numpy().astype(np.float64) for k, v in outs[r].items()}
+        g["sum_wv"] = g["sum_wv"][..., 0] + 1j * g["sum_wv"][..., 1]
+        g["count"] = outs[r]["count"].numpy().astype(np.uint64)
+        k = r + 1
+        ok = {"sum_wv": k * o["sum_wv"], "sum_w": k * o["sum_w"], "sum_wvv": k * o["sum_wvv"],
+              "sum_wabs": k * o["sum_wabs"], "count": k * o["count"]}
+        H.compare(g, ok, H.TOL_MIXED, what="async readback after run %d" % k)
+    for key in ("count", "sum_w"):
+        assert torch.equal(outs[2][key], final[key]), key
