@@ -7,7 +7,8 @@
 // pair; then one thread per (row, output channel) forms each contributor's
 // phasor as the stacking kernel does (float-float product tau nu_k / c,
 // reduced mod 1 turn, __sincosf: below 5e-7 rad) and sums in FP32 (a few
-// terms per output channel).
+// terms per output channel).  For complex64 with 2 or 4 pols on 16-byte
+// aligned arrays a channel's pols and their flags come in vector loads.
 #include <cmath>
 #include <vector>
 
@@ -35,6 +36,7 @@ struct RegridArgs {
     double *out_uvw;        // [nrow][3] or null
     int64_t nrow;
     int32_t nchan, npol, nrest, vis_type;
+    int32_t vec;            // complex64 with 2 or 4 pols, 16-byte aligned: a channel's pols in vector loads
     float vis_scale;
     double l, m, n1, inv_zf;
 };
@@ -72,6 +74,26 @@ __global__ void __launch_bounds__(256) k_regrid_tau(RegridArgs a)
         for (int c = 0; c < 3; ++c) a.out_uvw[3 * r + c] = x[c] * a.inv_zf;
 }
 
+// One channel's P visibilities (and their flag bytes, 0 = unflagged) with
+// vector loads: complex64 pols of a channel are 8 P contiguous, 16-byte
+// aligned bytes, their flags 4 (P = 4) or 2 (P = 2) aligned bytes.
+template <int P>
+__device__ __forceinline__ void load_channel_c64(const RegridArgs &a, int64_t i0, float2 (&v)[4], uint32_t &fl)
+{
+    const float4 *q = reinterpret_cast<const float4 *>(reinterpret_cast<const float2 *>(a.vis) + i0);
+    const float4 x = q[0];
+    v[0] = make_float2(x.x, x.y);
+    v[1] = make_float2(x.z, x.w);
+    if constexpr (P == 4) {
+        const float4 y = q[1];
+        v[2] = make_float2(y.x, y.y);
+        v[3] = make_float2(y.z, y.w);
+        fl = a.flags ? *reinterpret_cast<const uint32_t *>(a.flags + i0) : 0u;
+    } else {
+        fl = a.flags ? (uint32_t)*reinterpret_cast<const uint16_t *>(a.flags + i0) : 0u;
+    }
+}
+
 __global__ void __launch_bounds__(256) k_regrid(RegridArgs a)
 {
     const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -85,10 +107,25 @@ __global__ void __launch_bounds__(256) k_regrid(RegridArgs a)
         const float w = a.w[e];
         const float2 nuc = a.nuc[k];
         const float2 ph = shift_phasor(tau.x, tau.y, nuc.x, nuc.y);
+        const int64_t i0 = (r * a.nchan + k) * a.npol;
+        if (a.vec) {
+            float2 v[4];
+            uint32_t fl;
+            if (a.npol == 4) load_channel_c64<4>(a, i0, v, fl);
+            else load_channel_c64<2>(a, i0, v, fl);
+#pragma unroll
+            for (int p = 0; p < 4; ++p) {
+                if (p >= a.npol || ((fl >> (8 * p)) & 0xffu)) continue;
+                sr[p] = __fmaf_rn(w, v[p].x * ph.x - v[p].y * ph.y, sr[p]);
+                si[p] = __fmaf_rn(w, v[p].x * ph.y + v[p].y * ph.x, si[p]);
+                sw[p] += w;
+            }
+            continue;
+        }
 #pragma unroll
         for (int p = 0; p < 4; ++p) {
             if (p >= a.npol) break;
-            const int64_t i = (r * a.nchan + k) * a.npol + p;
+            const int64_t i = i0 + p;
             if (a.flags && a.flags[i]) continue;
             const float2 v = load_vis(a, i);
             sr[p] = __fmaf_rn(w, v.x * ph.x - v.y * ph.y, sr[p]);
@@ -200,6 +237,8 @@ extern "C" int vista_regrid_rows(vista_stack *h, const vista_source_desc *s, flo
     a.nrest = nrest;
     a.vis_type = s->vis_type;
     a.vis_scale = (s->vis_type == VISTA_VIS_F16X2 || s->vis_type == VISTA_VIS_BF16X2) ? s->vis_scale : 1.0f;
+    a.vec = s->vis_type == VISTA_VIS_C64 && (s->npol == 2 || s->npol == 4) && ((uintptr_t)s->vis % 16) == 0 &&
+            (!s->flags || ((uintptr_t)s->flags % (uintptr_t)s->npol) == 0);
     a.l = s->l;
     a.m = s->m;
     a.n1 = std::sqrt(1.0 - s->l * s->l - s->m * s->m) - 1.0;
