@@ -622,12 +622,15 @@ def run_e2e(args, wl, tuning, f0, df, ws):
     ste = open_stack(sub, V.PREC_MIXED, tuning)
     outs, t0 = None, 0.0
     split = {"queue_ms": 0.0, "device_ms": 0.0, "readback_ms": 0.0}
+    starts = []
     for it in range(1 + args.e2e_steps):
         if it == 1:
             torch.cuda.synchronize()
             barrier(ws)
             t0 = time.perf_counter()
         ta = time.perf_counter()
+        if it >= 1:
+            starts.append(ta)
         one_step(ste, sub)
         tb = time.perf_counter()
         if it == 0:
@@ -645,7 +648,8 @@ def run_e2e(args, wl, tuning, f0, df, ws):
             td = time.perf_counter()
             split = {"queue_ms": (tb - ta) * 1e3, "device_ms": (tc - tb) * 1e3, "readback_ms": (td - tc) * 1e3}
     ste.wait_readback()
-    dt = (time.perf_counter() - t0) / args.e2e_steps
+    t_end = time.perf_counter()
+    dt = (t_end - t0) / args.e2e_steps
     d2h = sum(v.numel() * v.element_size() for v in outs.values())
     h2d = ste.h2d_bytes()   # what vista_run copied for the windows (the last step's; every step's is the same)
     ste.close()
@@ -656,6 +660,10 @@ def run_e2e(args, wl, tuning, f0, df, ws):
             "windows": "%d of the %d windows that reach the cube (%d visibilities, %.1f GB pinned on the host)" % (
                 len(host), n_in, n_vis, pinned / 1e9),
             "link_gbs": (h2d + d2h) / dt / 1e9,
+            # host time between successive steps' starts (the host runs ahead
+            # of the device by up to two steps, so single values are not a
+            # step's device time; their spread shows this shared machine's noise)
+            "step_starts_ms": [round((b - a) * 1e3, 1) for a, b in zip(starts, starts[1:] + [t_end])],
             "last_step_split": split}
 
 
