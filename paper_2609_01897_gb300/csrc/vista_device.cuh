@@ -195,16 +195,6 @@ __device__ __forceinline__ int chunk_cell_step(int2 cc, int kk, int nu)
     return c;
 }
 
-// The P flag bytes of one lane's (row, channel) from shared memory, as one
-// word (byte p = pol p); p is P-byte aligned.
-template <int P>
-__device__ __forceinline__ uint32_t ld_flags_smem(const uint8_t *p)
-{
-    if constexpr (P == 1) return (uint32_t)*p;
-    else if constexpr (P == 2) return (uint32_t)*reinterpret_cast<const uint16_t *>(p);
-    else return *reinterpret_cast<const uint32_t *>(p);
-}
-
 // ----------------------------------------------------------- vis loaders
 
 template <int P, int VT>

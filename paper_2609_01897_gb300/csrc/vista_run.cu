@@ -94,6 +94,8 @@ int plan_source(vista_stack *h, const SrcHost &s, double gu, double gv, Plan &pl
 // A run's table uploads go through one half of the handle's pinned staging
 // area: the half is reused two runs later, after its uploads have completed
 // (an event), and the copies from it return without waiting for the stream.
+// Without pinned memory to be had, the tables are copied from pageable
+// memory (correct, but the call then waits for the stream).
 struct Uploader {
     vista_stack *h;
     char *base = nullptr;
@@ -109,8 +111,12 @@ struct Uploader {
             h->pin[x] = nullptr;
             h->pin_cap[x] = 0;
             const size_t want = total + total / 8 + 4096;
-            e = cudaHostAlloc(&h->pin[x], want, cudaHostAllocDefault);
-            if (e == cudaSuccess) h->pin_cap[x] = want;
+            if (cudaHostAlloc(&h->pin[x], want, cudaHostAllocDefault) == cudaSuccess) {
+                h->pin_cap[x] = want;
+            } else {
+                h->pin[x] = nullptr;
+                (void)cudaGetLastError();   // no pinned memory: pageable copies below
+            }
         }
         base = (char *)h->pin[x];
         pos = 0;
@@ -122,6 +128,7 @@ struct Uploader {
         const size_t bytes = v.size() * sizeof(T);
         cudaError_t e = b.ensure(bytes > 0 ? bytes : 16);
         if (e != cudaSuccess || bytes == 0) return e;
+        if (!base) return cudaMemcpyAsync(b.p, v.data(), bytes, cudaMemcpyHostToDevice, h->stream);
         std::memcpy(base + pos, v.data(), bytes);
         e = cudaMemcpyAsync(b.p, base + pos, bytes, cudaMemcpyHostToDevice, h->stream);
         pos += (bytes + 255) & ~(size_t)255;
