@@ -161,3 +161,26 @@ def test_contsub_removes_a_flat_continuum_from_stacked_data(V):
     np.testing.assert_allclose(swv[..., 0][sw > 0] / sw[sw > 0], 2.0, rtol=2e-5)
     assert np.abs(out[..., 0][sw > 0] / sw[sw > 0]).max() < 1e-4
     assert np.abs(out[..., 1][sw > 0] / sw[sw > 0]).max() < 1e-4
+
+
+@pytest.mark.parametrize("planes", [1, 3, 4])
+def test_contsub_kernel_other_plane_counts(V, planes):
+    """Cubes of 1 and 4 planes (a warp per uv cell, lane L on plane L mod
+    npol) and of 3 planes (a warp per cell and plane), against the oracle's
+    fit on the same cube, orders 1 and 3."""
+    from paper_2609_01897_gb300 import synth
+    pols = {1: (1,), 3: (2,), 4: (4,)}[planes]
+    wl = synth.random_case(57 + planes, "cuda", nsrc=5, max_rows=200, npol_choices=pols, nrest=64)
+    wl.npol = planes      # three planes: the windows' two pols fill planes 0 and 1
+    for order in (1, 3):
+        st = _stack(V, wl, V.PREC_MIXED)
+        try:
+            cube = st.read_cube(device=True, f64=True)
+            wv = (cube["sum_wv"][..., 0] + 1j * cube["sum_wv"][..., 1]).cpu().numpy()
+            w = cube["sum_w"].cpu().numpy()
+            free = _line_free(wl.nrest, order)
+            got = st.contsub(free, order).cpu().numpy()
+        finally:
+            st.close()
+        assert (w > 0).sum() > 100
+        _kernel_check(got, wv, w, free, order)

@@ -123,3 +123,35 @@ def test_regrid_rows_full_wide_window(V):
     o_vis, o_w = H.O.regrid_rows(src, f0, rest_df, nrest)
     assert (o_w > 0).sum() > nrow * npol * (nchan // 32 - 2)
     _check(g_vis, g_w, o_vis, o_w, float(vis.abs().max()))
+
+
+def test_regrid_rows_ragged_pols_axes_and_alignment(V):
+    """Ragged windows (1, 2 and 4 pols, descending channel axes, odd channel
+    counts; the vector-load path and the per-element path), and one 2-pol
+    window whose visibilities start 8 bytes past a 16-byte boundary (the
+    per-element path), each against the oracle."""
+    from paper_2609_01897_gb300 import synth
+    wl = synth.random_case(41, "cuda", nsrc=6, max_rows=60, npol_choices=(1, 2, 4), descending=True)
+    f0, df = H.lattice_of(wl)
+    st = V.Stack(wl.nu, wl.nv, wl.nrest, wl.npol, wl.du, wl.dv, rest_f0=f0, rest_df=df)
+    checked = 0
+    try:
+        for s in wl.spws:
+            if s.vis.shape[0] == 0:
+                continue
+            vis = s.vis
+            if vis.shape[2] == 2 and checked % 2 == 0:
+                buf = torch.empty(vis.numel() + 1, dtype=torch.complex64, device=vis.device)
+                vis = buf[1:].view(vis.shape)
+                vis.copy_(s.vis)
+                assert vis.data_ptr() % 16 == 8
+            g_vis, g_w, _ = st.regrid_rows(s.uvw, s.freqs, vis, s.flags, l=s.l, m=s.m, z=s.z)
+            src = H.O.Source(s.uvw.cpu().numpy(), s.freqs, s.vis.cpu().numpy(), s.weights.cpu().numpy(),
+                             s.flags.cpu().numpy(), s.l, s.m, s.z)
+            o_vis, o_w = H.O.regrid_rows(src, f0, df, wl.nrest)
+            if (o_w > 0).any():
+                _check(g_vis, g_w, o_vis, o_w, float(s.vis.abs().max()))
+                checked += 1
+    finally:
+        st.close()
+    assert checked >= 3, checked
