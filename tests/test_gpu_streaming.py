@@ -111,3 +111,31 @@ def test_async_readback_overlaps_runs_and_matches(V):
         H.compare(g, ok, H.TOL_MIXED, what="async readback after run %d" % k)
     for key in ("count", "sum_w"):
         assert torch.equal(outs[2][key], final[key]), key
+
+
+@pytest.mark.parametrize("kind", ["f16", "bf16"])
+def test_streamed_half_storage(V, kind):
+    """Host windows in 16-bit storage (per-window power-of-two scales)
+    streamed in several waves, against the oracle on the stored values."""
+    from paper_2609_01897_gb300 import synth
+    wl = synth.tiny("cuda")
+    st = V.Stack(wl.nu, wl.nv, wl.nrest, wl.npol, wl.du, wl.dv, rest_f0=wl.rest_f0, rest_df=wl.rest_df,
+                 central_freq=wl.central_freq)
+    deq = {}
+    try:
+        st.set_wave_bytes(256 << 10)
+        for s in wl.spws:
+            q, scale, d = H.quantise(s.vis, kind)
+            deq[id(s)] = d
+            st.add_source(s.uvw.cpu().pin_memory(), s.freqs, q.cpu().pin_memory(), s.weights.cpu().pin_memory(),
+                          s.flags.cpu().pin_memory(), l=s.l, m=s.m, z=s.z, vis_scale=scale)
+        st.run()
+        waves = st.waves()
+        cube = st.read_cube(device=True, f64=True)
+        g = {k: v.cpu().numpy() for k, v in cube.items()}
+    finally:
+        st.close()
+    assert waves >= 4, waves
+    g["sum_wv"] = g["sum_wv"][..., 0] + 1j * g["sum_wv"][..., 1]
+    o = H.run_oracle(wl, dequant=deq)
+    H.compare(g, o, H.TOL_MIXED, what="streamed %s" % kind)
