@@ -435,13 +435,14 @@ def run_ours(args):
     launches = int(round(tm["launches"])) * args.steps
     # end to end through the C ABI with host buffers, straight after the timed
     # steps (after the other legs the same steps have taken up to twice as
-    # long on this shared machine)
-    e2e = None
+    # long on this shared machine); where its stack does not fit beside the
+    # main one, again once the main stack is closed (below)
+    e2e, e2e_retry = None, False
     if args.e2e_steps > 0:
         try:
             e2e = run_e2e(args, wl, tuning, f0, df, ws)
         except (RuntimeError, MemoryError) as exc:
-            e2e = {"error": str(exc)[:200]}
+            e2e, e2e_retry = {"error": str(exc)[:200]}, True
     link = host_link_peak() if rank == 0 and args.e2e_steps > 0 else None
     regrid = time_regrid(st, wl, f0, df, args.regrid_reps, peak) if args.regrid_reps > 0 else None
     contsub = time_contsub(st, wl, args.contsub_reps, peak) if args.contsub_reps > 0 else None
@@ -459,6 +460,13 @@ def run_ours(args):
         cube_reduce_ms = allmax(ws, (time.perf_counter() - t0) * 1e3)
         del part, total
     st.close()
+    if e2e_retry:
+        torch.cuda.empty_cache()
+        try:
+            e2e = run_e2e(args, wl, tuning, f0, df, ws)
+            e2e["order"] = "after the main stack was closed (both stacks did not fit on the device)"
+        except (RuntimeError, MemoryError) as exc:
+            e2e = {"error": str(exc)[:200]}
 
 
     # plain FP64 GPU form on the same inputs
@@ -620,39 +628,41 @@ def run_e2e(args, wl, tuning, f0, df, ws):
     sub = synth.Workload(wl.name, wl.nu, wl.nv, wl.nrest, wl.npol, wl.du, wl.dv, wl.central_freq, host,
                          df, f0)
     ste = open_stack(sub, V.PREC_MIXED, tuning)
-    outs, t0 = None, 0.0
-    split = {"queue_ms": 0.0, "device_ms": 0.0, "readback_ms": 0.0}
-    starts = []
-    for it in range(1 + args.e2e_steps):
-        if it == 1:
-            torch.cuda.synchronize()
-            barrier(ws)
-            t0 = time.perf_counter()
-        ta = time.perf_counter()
-        if it >= 1:
-            starts.append(ta)
-        one_step(ste, sub)
-        tb = time.perf_counter()
-        if it == 0:
-            # the pinned result buffers are allocated once (first, untimed step)
-            outs = ste.read_cube(device=False, out=outs)
-        elif it < args.e2e_steps:
-            # every step reads its cube back; the copy overlaps the next step's
-            ste.read_cube_async(outs)
-        else:
-            # the last step also splits its time: its run, then its readback
-            torch.cuda.current_stream().synchronize()
-            tc = time.perf_counter()
-            ste.read_cube_async(outs)
-            ste.wait_readback()
-            td = time.perf_counter()
-            split = {"queue_ms": (tb - ta) * 1e3, "device_ms": (tc - tb) * 1e3, "readback_ms": (td - tc) * 1e3}
-    ste.wait_readback()
-    t_end = time.perf_counter()
-    dt = (t_end - t0) / args.e2e_steps
-    d2h = sum(v.numel() * v.element_size() for v in outs.values())
-    h2d = ste.h2d_bytes()   # what vista_run copied for the windows (the last step's; every step's is the same)
-    ste.close()
+    try:
+        outs, t0 = None, 0.0
+        split = {"queue_ms": 0.0, "device_ms": 0.0, "readback_ms": 0.0}
+        starts = []
+        for it in range(1 + args.e2e_steps):
+            if it == 1:
+                torch.cuda.synchronize()
+                barrier(ws)
+                t0 = time.perf_counter()
+            ta = time.perf_counter()
+            if it >= 1:
+                starts.append(ta)
+            one_step(ste, sub)
+            tb = time.perf_counter()
+            if it == 0:
+                # the pinned result buffers are allocated once (first, untimed step)
+                outs = ste.read_cube(device=False, out=outs)
+            elif it < args.e2e_steps:
+                # every step reads its cube back; the copy overlaps the next step's
+                ste.read_cube_async(outs)
+            else:
+                # the last step also splits its time: its run, then its readback
+                torch.cuda.current_stream().synchronize()
+                tc = time.perf_counter()
+                ste.read_cube_async(outs)
+                ste.wait_readback()
+                td = time.perf_counter()
+                split = {"queue_ms": (tb - ta) * 1e3, "device_ms": (tc - tb) * 1e3, "readback_ms": (td - tc) * 1e3}
+        ste.wait_readback()
+        t_end = time.perf_counter()
+        dt = (t_end - t0) / args.e2e_steps
+        d2h = sum(v.numel() * v.element_size() for v in outs.values())
+        h2d = ste.h2d_bytes()   # what vista_run copied for the windows (the last step's; every step's is the same)
+    finally:
+        ste.close()
     dt = allmax(ws, dt)
     n_in = sum(1 for s in wl.spws if window_io(s, f0, df, wl.nrest)[0] > 0)
     return {"value": allsum(ws, n_vis) / dt, "unit": UNIT, "h2d_bytes_per_step": int(h2d),

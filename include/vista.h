@@ -50,6 +50,11 @@ enum {
     VISTA_E_RANGE = -5,    /* inputs exceed a supported size */
     VISTA_E_TIMEOUT = -6   /* a bounded device-side wait gave up (reported by read/stats) */
 };
+/* A call that fails on a CUDA runtime error (VISTA_E_NOMEM, VISTA_E_CUDA)
+ * clears that error from the calling thread's CUDA state (cudaGetLastError)
+ * before it returns: a failed allocation does not resurface in the caller's
+ * later launch checks or in the next call.  The handle stays usable after
+ * VISTA_E_NOMEM; free device memory and repeat the call. */
 
 enum { VISTA_VIS_C64 = 0, VISTA_VIS_C128 = 1, VISTA_VIS_F16X2 = 2, VISTA_VIS_BF16X2 = 3 };
 enum { VISTA_BIN_OVERLAP = 0, VISTA_BIN_NEAREST = 1 };

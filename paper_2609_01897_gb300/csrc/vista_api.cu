@@ -66,6 +66,11 @@ int fail(vista_stack *h, int code, const char *fmt, ...)
 
 int cuda_fail(vista_stack *h, cudaError_t e, const char *what)
 {
+    // a failed allocation or launch also leaves its code as the thread's last
+    // CUDA error; cleared here, so that it cannot surface later in the
+    // caller's own launch checks or in this library's next call (a sticky
+    // error that ruined the context stays whatever this does)
+    (void)cudaGetLastError();
     return fail(h, e == cudaErrorMemoryAllocation ? VISTA_E_NOMEM : VISTA_E_CUDA, "%s: %s", what,
                 cudaGetErrorString(e));
 }

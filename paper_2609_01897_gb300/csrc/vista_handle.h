@@ -26,6 +26,7 @@ struct DevBuf {
         const size_t want = bytes + bytes / 8 + 256;   // headroom against regrowth
         cudaError_t e = cudaMalloc(&p, want);
         if (e == cudaSuccess) cap = want;
+        else (void)cudaGetLastError();   // the failure is returned, not left pending
         return e;
     }
     void release()

@@ -281,6 +281,23 @@ def test_errors(V, tiny):
     assert V.lib().vista_add_source(h, None) == V.E_STATE
 
 
+def test_failed_allocation_leaves_no_pending_error(V, tiny):
+    # a cube of 1024 x 1024 cells x 262144 rest channels x 4 pols needs
+    # about 57 TB: cudaMalloc refuses it at once and the open reports
+    # VISTA_E_NOMEM.  The refused allocation must not stay behind as the
+    # thread's last CUDA error, where the next launch check (torch's own, or
+    # the library's in a later run) would take it for its own failure.
+    with pytest.raises(V.VistaError) as e:
+        V.Stack(1024, 1024, 262144, 4, tiny.du, tiny.dv, central_freq=tiny.central_freq)
+    assert e.value.code == V.E_NOMEM
+    x = torch.arange(1024, dtype=torch.float32, device="cuda") * 2.0
+    torch.cuda.synchronize()
+    assert float(x.sum()) == 1023.0 * 1024.0
+    g = H.run_gpu(tiny)
+    o = H.run_oracle(tiny)
+    H.compare(g, o, H.TOL_MIXED, what="tiny after a refused allocation")
+
+
 def test_all_flagged_and_empty(V, tiny):
     s = tiny.spws[0]
     st = V.Stack(tiny.nu, tiny.nv, tiny.nrest, tiny.npol, tiny.du, tiny.dv, central_freq=tiny.central_freq)
