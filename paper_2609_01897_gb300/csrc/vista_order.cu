@@ -381,16 +381,58 @@ __global__ void __launch_bounds__(256) k_bucket_sort(RunArgs a)
     }
 }
 
-// First chunk-local channel in (lo, hi] whose floor(coord * s) differs from
-// f_lo (the cell is monotone in frequency; hi is known to differ).
-__device__ int axis_step(float c32, const ChanF *cf, const ChanD *cd, int e0, int lo, int hi, const double *coord64,
-                         bool neg, bool v_axis, float f_lo)
+// The cell scales (su, sv) of channel k of a window's table (read-only).
+__device__ __forceinline__ float2 chan_scales(const ChanF *cf, int k)
 {
+    return __ldg(reinterpret_cast<const float2 *>(cf + k));
+}
+
+// The scales of a chunk's first and last channel: all a chunk's entry needs
+// unless its cell changes inside it.
+struct ChunkEnds {
+    float2 s0, s1;
+};
+__device__ __forceinline__ ChunkEnds chunk_ends(const RunArgs &a, const ChanF *cf, int nin, int c)
+{
+    const int e0 = c * a.cw, last = min(nin, e0 + a.cw) - 1 - e0;
+    return ChunkEnds{chan_scales(cf, e0), chan_scales(cf, e0 + last)};
+}
+
+// First chunk-local channel in (lo, hi] whose floor(coord * s) differs from
+// f_lo; f_hi = the floor at hi (different), x_lo, x_hi = fl32(coord * s) at
+// lo and hi.  The cell is monotone in frequency.  The scales are close to
+// linear in the channel index across a chunk, so the crossing is first
+// estimated by linear interpolation and the floors at the estimate and the
+// channel before it are evaluated (two loads issued together); they either
+// settle the answer or narrow the bisection that follows, so the result is
+// the exact first differing channel whatever the estimate.
+__device__ int axis_step(float c32, const ChanF *cf, const ChanD *cd, int e0, int lo, int hi, const double *coord64,
+                         bool neg, bool v_axis, float f_lo, float f_hi, float x_lo, float x_hi)
+{
+    auto f_at = [&](int k) {
+        const float2 sc = chan_scales(cf, e0 + k);
+        return axis_floor(c32, v_axis ? sc.y : sc.x, coord64, neg, v_axis ? &cd[e0 + k].sv : &cd[e0 + k].su);
+    };
+    if (hi - lo > 1) {
+        const float B = f_hi > f_lo ? f_lo + 1.0f : f_lo;   // the value coord * s crosses
+        const float dx = x_hi - x_lo, span = (float)(hi - lo);
+        int k = (lo + hi + 1) >> 1;
+        if (dx != 0.0f) {
+            const float t = (B - x_lo) / dx * span;
+            if (t > 0.0f && t < span) k = lo + (int)ceilf(t);   // a NaN fails both tests
+        }
+        k = min(max(k, lo + 1), hi);
+        const float fk = f_at(k), fm = f_at(k - 1);   // k - 1 >= lo, where the floor is f_lo
+        if (fk == f_lo)
+            lo = k;
+        else if (fm == f_lo)
+            return k;
+        else
+            hi = k - 1;
+    }
     while (hi - lo > 1) {
         const int mid = (lo + hi) >> 1;
-        const float f = v_axis ? axis_floor(c32, cf[e0 + mid].sv, coord64, neg, &cd[e0 + mid].sv)
-                               : axis_floor(c32, cf[e0 + mid].su, coord64, neg, &cd[e0 + mid].su);
-        if (f == f_lo)
+        if (f_at(mid) == f_lo)
             lo = mid;
         else
             hi = mid;
@@ -399,19 +441,20 @@ __device__ int axis_step(float c32, const ChanF *cf, const ChanD *cd, int e0, in
 }
 
 // The chunk-cell entry of chunk c of one row (coordinates uf, vf after the
-// fold; uvw the row's FP64 coordinates for the exact fall-backs).  The cell
-// index is monotone in frequency along each axis, so the cells at a chunk's
-// two end channels bound every channel between.
+// fold; uvw the row's FP64 coordinates for the exact fall-backs; ce the
+// scales at the chunk's two end channels).  The cell index is monotone in
+// frequency along each axis, so the cells at a chunk's two end channels
+// bound every channel between.
 __device__ int2 chunk_cell(const RunArgs &a, const SrcDev &S, const ChanF *cf, const ChanD *cd, int c, float uf,
-                           float vf, const double *uvw, bool fold)
+                           float vf, const double *uvw, bool fold, const ChunkEnds &ce)
 {
     const int nin = S.k_hi - S.k_lo;
     const float hu = (float)(a.g.nu >> 1), hv = (float)(a.g.nv >> 1);
     const int e0 = c * a.cw, last = min(nin, e0 + a.cw) - 1 - e0;
-    const float fu0 = axis_floor(uf, cf[e0].su, uvw, fold, &cd[e0].su);
-    const float fu1 = axis_floor(uf, cf[e0 + last].su, uvw, fold, &cd[e0 + last].su);
-    const float fv0 = axis_floor(vf, cf[e0].sv, uvw + 1, fold, &cd[e0].sv);
-    const float fv1 = axis_floor(vf, cf[e0 + last].sv, uvw + 1, fold, &cd[e0 + last].sv);
+    const float fu0 = axis_floor(uf, ce.s0.x, uvw, fold, &cd[e0].su);
+    const float fu1 = axis_floor(uf, ce.s1.x, uvw, fold, &cd[e0 + last].su);
+    const float fv0 = axis_floor(vf, ce.s0.y, uvw + 1, fold, &cd[e0].sv);
+    const float fv1 = axis_floor(vf, ce.s1.y, uvw + 1, fold, &cd[e0 + last].sv);
     // both ends off the grid on the same side of one axis: off throughout
     const bool offu = (fu0 < -hu && fu1 < -hu) || (fu0 >= hu && fu1 >= hu);
     const bool offv = (fv0 < -hv && fv1 < -hv) || (fv0 >= hv && fv1 >= hv);
@@ -421,11 +464,13 @@ __device__ int2 chunk_cell(const RunArgs &a, const SrcDev &S, const ChanF *cf, c
     if (!in || fabsf(fu1 - fu0) > 1.0f || fabsf(fv1 - fv0) > 1.0f) return make_int2(-1, CC_MIXED);
     uint32_t m = CC_NOCHANGE;
     if (fu1 != fu0) {
-        const int b = axis_step(uf, cf, cd, e0, 0, last, uvw, fold, false, fu0);
+        const int b = axis_step(uf, cf, cd, e0, 0, last, uvw, fold, false, fu0, fu1, __fmul_rn(uf, ce.s0.x),
+                                __fmul_rn(uf, ce.s1.x));
         m = (m & ~0xffu) | (uint32_t)b | (fu1 < fu0 ? 0x10000u : 0u);
     }
     if (fv1 != fv0) {
-        const int b = axis_step(vf, cf, cd, e0, 0, last, uvw + 1, fold, true, fv0);
+        const int b = axis_step(vf, cf, cd, e0, 0, last, uvw + 1, fold, true, fv0, fv1, __fmul_rn(vf, ce.s0.y),
+                                __fmul_rn(vf, ce.s1.y));
         m = (m & ~0xff00u) | ((uint32_t)b << 8) | (fv1 < fv0 ? 0x20000u : 0u);
     }
     return make_int2(((int)fv0 + (a.g.nv >> 1)) * a.g.nu + ((int)fu0 + (a.g.nu >> 1)), (int)m);
@@ -435,7 +480,10 @@ __device__ int2 chunk_cell(const RunArgs &a, const SrcDev &S, const ChanF *cf, c
 // of Eq. 2 as a float-float pair, the fold-signed weights, the row index)
 // and the chunk-cell entries of all the window's chunks, laid out
 // [chunk][row] per window so that an item's entries are contiguous.  The
-// row's coordinates are read once for both.
+// row's coordinates are read once for both.  The window's channel table is
+// read from L2 (the tables of the windows a block's rows span do not stay
+// in L1), so the end scales of chunk c + 1 are loaded before chunk c's entry
+// is formed: one load latency per chunk overlaps the previous chunk's work.
 __global__ void __launch_bounds__(256) k_rows(RunArgs a)
 {
     const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -464,8 +512,14 @@ __global__ void __launch_bounds__(256) k_rows(RunArgs a)
     const ChanD *cd = a.chd + S.chan_off;
     const ChanF *cf = a.chf + S.chan_off;
     int2 *out = a.ccells + S.cell_off + q;
-    const int nchunk = S.nchunk;
-    for (int c = 0; c < nchunk; ++c) out[(int64_t)c * S.nrow] = chunk_cell(a, S, cf, cd, c, uf, vf, guvw, fold);
+    const int nchunk = S.nchunk, nin = S.k_hi - S.k_lo;
+    if (nchunk <= 0) return;
+    ChunkEnds nx = chunk_ends(a, cf, nin, 0);
+    for (int c = 0; c < nchunk; ++c) {
+        const ChunkEnds ce = nx;
+        if (c + 1 < nchunk) nx = chunk_ends(a, cf, nin, c + 1);
+        out[(int64_t)c * S.nrow] = chunk_cell(a, S, cf, cd, c, uf, vf, guvw, fold, ce);
+    }
 }
 
 // Re-projected windows (Eq. 1): their gridding baselines R (u, v, w) (see
