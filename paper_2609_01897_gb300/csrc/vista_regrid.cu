@@ -37,6 +37,7 @@ struct RegridArgs {
     int64_t nrow;
     int32_t nchan, npol, nrest, vis_type;
     int32_t vec;            // complex64 with 2 or 4 pols, 16-byte aligned: a channel's pols in vector loads
+    int32_t vout;           // 2 or 4 pols, outputs 16-byte (wsum of 2 pols: 8-byte) aligned: vector stores
     float vis_scale;
     double l, m, n1, inv_zf;
 };
@@ -133,12 +134,34 @@ __global__ void __launch_bounds__(256) k_regrid(RegridArgs a)
             sw[p] += w;
         }
     }
-    for (int p = 0; p < a.npol; ++p) {
-        const int64_t o = (r * a.nrest + j) * a.npol + p;
+    float ov[8];
+#pragma unroll
+    for (int p = 0; p < 4; ++p) {
         const bool any = sw[p] > 0.0f;
-        a.out_vis[2 * o] = any ? sr[p] / sw[p] : 0.0f;
-        a.out_vis[2 * o + 1] = any ? si[p] / sw[p] : 0.0f;
-        a.out_wsum[o] = sw[p];
+        ov[2 * p] = any ? sr[p] / sw[p] : 0.0f;
+        ov[2 * p + 1] = any ? si[p] / sw[p] : 0.0f;
+    }
+    const int64_t o = (r * a.nrest + j) * a.npol;
+    if (a.vout) {
+        // a thread's outputs are contiguous: whole 16-byte stores rather
+        // than one 4-byte store per value (each of those spans 32 sectors
+        // across the warp)
+        float4 *dv = reinterpret_cast<float4 *>(a.out_vis + 2 * o);
+        dv[0] = make_float4(ov[0], ov[1], ov[2], ov[3]);
+        if (a.npol == 4) {
+            dv[1] = make_float4(ov[4], ov[5], ov[6], ov[7]);
+            *reinterpret_cast<float4 *>(a.out_wsum + o) = make_float4(sw[0], sw[1], sw[2], sw[3]);
+        } else {
+            *reinterpret_cast<float2 *>(a.out_wsum + o) = make_float2(sw[0], sw[1]);
+        }
+        return;
+    }
+#pragma unroll
+    for (int p = 0; p < 4; ++p) {
+        if (p >= a.npol) break;
+        a.out_vis[2 * (o + p)] = ov[2 * p];
+        a.out_vis[2 * (o + p) + 1] = ov[2 * p + 1];
+        a.out_wsum[o + p] = sw[p];
     }
 }
 
@@ -239,6 +262,8 @@ extern "C" int vista_regrid_rows(vista_stack *h, const vista_source_desc *s, flo
     a.vis_scale = (s->vis_type == VISTA_VIS_F16X2 || s->vis_type == VISTA_VIS_BF16X2) ? s->vis_scale : 1.0f;
     a.vec = s->vis_type == VISTA_VIS_C64 && (s->npol == 2 || s->npol == 4) && ((uintptr_t)s->vis % 16) == 0 &&
             (!s->flags || ((uintptr_t)s->flags % (uintptr_t)s->npol) == 0);
+    a.vout = (s->npol == 2 || s->npol == 4) && ((uintptr_t)out_vis % 16) == 0 &&
+             ((uintptr_t)out_wsum % (uintptr_t)(s->npol == 4 ? 16 : 8)) == 0;
     a.l = s->l;
     a.m = s->m;
     a.n1 = std::sqrt(1.0 - s->l * s->l - s->m * s->m) - 1.0;

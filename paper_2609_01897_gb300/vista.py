@@ -217,11 +217,15 @@ class Stack:
                    lib().vista_add_source_reproject(self.h, C.byref(d), ra0, dec0, ra1, dec1), self.h)
         self._pending.append((uvw, vis, weights, flags))
 
-    def regrid_rows(self, uvw, freqs, vis, flags=None, *, l=0.0, m=0.0, z, vis_scale=1.0, with_uvw=False):
+    def regrid_rows(self, uvw, freqs, vis, flags=None, *, l=0.0, m=0.0, z, vis_scale=1.0, with_uvw=False,
+                    out=None):
         """The paper's per-row output (Eq. 3) of one window of device arrays:
         returns (vis_out complex64 [nrow, nrest, npol], wsum float32 [nrow,
         nrest, npol], uvw / (1 + z) float64 [nrow, 3] or None), on the device.
-        The rest lattice must be fixed (rest_df at open, or after a run)."""
+        The rest lattice must be fixed (rest_df at open, or after a run).
+        `out` = (float32 [nrow, nrest, npol, 2], float32 [nrow, nrest, npol])
+        contiguous device tensors are written in place instead of allocating,
+        and returned as given (vis_out then as float pairs)."""
         vt = _vis_type(vis)
         nrow, nchan, npol = int(vis.shape[0]), int(vis.shape[1]), int(vis.shape[2])
         if not vis.is_cuda or not uvw.is_cuda or (flags is not None and not flags.is_cuda):
@@ -232,15 +236,23 @@ class Stack:
         if uvw.dtype != torch.float64 or (flags is not None and flags.dtype != torch.uint8):
             raise TypeError("uvw must be float64 and flags uint8")
         nrest = self.shape[2]
-        out = torch.zeros((nrow, nrest, npol, 2), dtype=torch.float32, device=vis.device)
-        wsum = torch.zeros((nrow, nrest, npol), dtype=torch.float32, device=vis.device)
+        given = out is not None
+        if out is None:   # every entry is written (0 where no channel contributes)
+            out = torch.empty((nrow, nrest, npol, 2), dtype=torch.float32, device=vis.device)
+            wsum = torch.empty((nrow, nrest, npol), dtype=torch.float32, device=vis.device)
+        else:
+            out, wsum = out
+            for name, t, shp in (("out[0]", out, (nrow, nrest, npol, 2)), ("out[1]", wsum, (nrow, nrest, npol))):
+                if (tuple(t.shape) != shp or t.dtype != torch.float32 or not t.is_cuda
+                        or not t.is_contiguous()):
+                    raise ValueError("%s must be a contiguous float32 device tensor of shape %s" % (name, shp))
         ruvw = torch.empty((nrow, 3), dtype=torch.float64, device=vis.device) if with_uvw else None
         f = np.ascontiguousarray(np.asarray(freqs, dtype=np.float64))
         d = SourceDesc(nrow, nchan, npol, _ptr(uvw), f.ctypes.data, _ptr(vis), vt, float(vis_scale),
                        None, _ptr(flags), None, float(l), float(m), float(z), MEM_DEVICE, 0)
         _check("vista_regrid_rows", lib().vista_regrid_rows(self.h, C.byref(d), _ptr(out), _ptr(wsum),
                                                             _ptr(ruvw)), self.h)
-        return torch.view_as_complex(out), wsum, ruvw
+        return (out if given else torch.view_as_complex(out)), wsum, ruvw
 
     def run(self):
         _check("vista_run", lib().vista_run(self.h), self.h)

@@ -127,14 +127,16 @@ def test_regrid_rows_full_wide_window(V):
 
 def test_regrid_rows_ragged_pols_axes_and_alignment(V):
     """Ragged windows (1, 2 and 4 pols, descending channel axes, odd channel
-    counts; the vector-load path and the per-element path), and one 2-pol
-    window whose visibilities start 8 bytes past a 16-byte boundary (the
-    per-element path), each against the oracle."""
+    counts; the vector-load path and the per-element path), one 2-pol window
+    whose visibilities start 8 bytes past a 16-byte boundary (the
+    per-element path), and 2- and 4-pol windows whose outputs start 4 bytes
+    past a 16-byte boundary (the per-value stores), each against the
+    oracle."""
     from paper_2609_01897_gb300 import synth
     wl = synth.random_case(41, "cuda", nsrc=6, max_rows=60, npol_choices=(1, 2, 4), descending=True)
     f0, df = H.lattice_of(wl)
     st = V.Stack(wl.nu, wl.nv, wl.nrest, wl.npol, wl.du, wl.dv, rest_f0=f0, rest_df=df)
-    checked = 0
+    checked, unaligned_out = 0, 0
     try:
         for s in wl.spws:
             if s.vis.shape[0] == 0:
@@ -145,7 +147,19 @@ def test_regrid_rows_ragged_pols_axes_and_alignment(V):
                 vis = buf[1:].view(vis.shape)
                 vis.copy_(s.vis)
                 assert vis.data_ptr() % 16 == 8
-            g_vis, g_w, _ = st.regrid_rows(s.uvw, s.freqs, vis, s.flags, l=s.l, m=s.m, z=s.z)
+            out = None
+            if vis.shape[2] in (2, 4) and checked % 2 == 1:
+                shp = (vis.shape[0], wl.nrest, vis.shape[2])
+                n = int(np.prod(shp))
+                bo = torch.zeros(2 * n + 1, dtype=torch.float32, device=vis.device)
+                bw = torch.zeros(n + 1, dtype=torch.float32, device=vis.device)
+                out = (bo[1:].view(*shp, 2), bw[1:].view(shp))
+                assert out[0].data_ptr() % 16 == 4 and out[1].data_ptr() % 8 == 4
+                unaligned_out += 1
+            g_vis, g_w, _ = st.regrid_rows(s.uvw, s.freqs, vis, s.flags, l=s.l, m=s.m, z=s.z, out=out)
+            if out is not None:
+                assert g_vis.data_ptr() == out[0].data_ptr() and g_w.data_ptr() == out[1].data_ptr()
+                g_vis = torch.complex(g_vis[..., 0], g_vis[..., 1])
             src = H.O.Source(s.uvw.cpu().numpy(), s.freqs, s.vis.cpu().numpy(), s.weights.cpu().numpy(),
                              s.flags.cpu().numpy(), s.l, s.m, s.z)
             o_vis, o_w = H.O.regrid_rows(src, f0, df, wl.nrest)
@@ -154,4 +168,4 @@ def test_regrid_rows_ragged_pols_axes_and_alignment(V):
                 checked += 1
     finally:
         st.close()
-    assert checked >= 3, checked
+    assert checked >= 3 and unaligned_out >= 1, (checked, unaligned_out)
