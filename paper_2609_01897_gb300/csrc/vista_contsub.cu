@@ -204,44 +204,33 @@ __device__ __forceinline__ EntryFF entry_ff(const void *cube, const double *mast
     return r;
 }
 
-// Warp per cell (npol divides 32): lane L handles entries L, L + 32, ... of
-// the cell ([nrest][npol], so plane L mod npol); x_j = (2 j - (nrest - 1)) *
-// (1 / nrest) with 1 / nrest as a float pair inv (exact products by FMA).
-template <int ORDER>
-__global__ void __launch_bounds__(256) k_contsub_cell(const void *cube, const double *master, int fp64,
-                                                      const uint8_t *line_free, int64_t ncell, int nrest, int npol,
-                                                      float2 inv, float2 *out)
+// x_j = (2 j - (nrest - 1)) / nrest as a float pair, from 1 / nrest as a
+// float pair inv (the numerator is exact in FP32, |2 j - (nrest - 1)| < 2^24,
+// and its product with inv.x exact by FMA).
+__device__ __forceinline__ float2 absc_ff(int j, int nrest, float2 inv)
 {
-    constexpr int NM = 2 * ORDER + 1;
-    constexpr int NB = ORDER + 1;
-    const int lane = threadIdx.x & 31;
-    const int64_t cell = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    if (cell >= ncell) return;   // whole warps
-    const int64_t e0 = cell * nrest * npol;
-    const int nent = nrest * npol;
-    // x_j as a float pair (numerator exact in FP32: |2 j - (nrest - 1)| < 2^24)
-    auto absc = [&](int j) {
-        const float a = (float)(2 * j - (nrest - 1));
-        const float h = a * inv.x;
-        return make_float2(h, __fmaf_rn(a, inv.x, -h) + a * inv.y);
-    };
+    const float a = (float)(2 * j - (nrest - 1));
+    const float h = a * inv.x;
+    return make_float2(h, __fmaf_rn(a, inv.x, -h) + a * inv.y);
+}
+
+// The moments of one plane's fit set as compensated float-pair sums, entry
+// by entry: sum t x^n (n = 0 .. 2 ORDER) with t = sum_w, and sum v x^k
+// (k = 0 .. ORDER) with v = sum_wv (re and im); t, v, x and every power as
+// float pairs (products to about 2^-44).
+template <int ORDER>
+struct MomentsFF {
+    static constexpr int NM = 2 * ORDER + 1, NB = ORDER + 1;
     float Ms[NM], Mc[NM], Brs[NB], Brc[NB], Bis[NB], Bic[NB];
+    __device__ __forceinline__ void zero()
+    {
 #pragma unroll
-    for (int k = 0; k < NM; ++k) Ms[k] = Mc[k] = 0.f;
+        for (int k = 0; k < NM; ++k) Ms[k] = Mc[k] = 0.f;
 #pragma unroll
-    for (int k = 0; k < NB; ++k) Brs[k] = Brc[k] = Bis[k] = Bic[k] = 0.f;
-    int nfit = 0;
-    float xmin = 2.f, xmax = -2.f;
-    for (int f = lane; f < nent; f += 32) {
-        const int j = f / npol;
-        if (!line_free[j]) continue;
-        const EntryFF v = entry_ff(cube, master, fp64, e0 + f);
-        if (!(v.z.x > 0.f)) continue;
-        ++nfit;
-        const float2 x = absc(j);
-        xmin = fminf(xmin, x.x);
-        xmax = fmaxf(xmax, x.x);
-        // terms t x^n and b x^k with t, b, x float pairs; products to ~2^-44
+        for (int k = 0; k < NB; ++k) Brs[k] = Brc[k] = Bis[k] = Bic[k] = 0.f;
+    }
+    __device__ __forceinline__ void add(const EntryFF &v, float2 x)
+    {
         float th = v.z.x, tl = v.z.y;
 #pragma unroll
         for (int k = 0; k < NM; ++k) {
@@ -265,15 +254,90 @@ __global__ void __launch_bounds__(256) k_contsub_cell(const void *cube, const do
             ih = pi;
         }
     }
+    __device__ __forceinline__ void to_double(double (&M)[NM], double (&Br)[NB], double (&Bi)[NB]) const
+    {
+#pragma unroll
+        for (int k = 0; k < NM; ++k) M[k] = (double)Ms[k] + (double)Mc[k];
+#pragma unroll
+        for (int k = 0; k < NB; ++k) {
+            Br[k] = (double)Brs[k] + (double)Brc[k];
+            Bi[k] = (double)Bis[k] + (double)Bic[k];
+        }
+    }
+};
+
+// The same moments in FP64 from an entry's FP64 sums (the refit of an
+// ill-conditioned plane).
+template <int ORDER>
+__device__ __forceinline__ void add_moments_fp64(const double3 &v, double x, double (&Md)[2 * ORDER + 1],
+                                                 double (&Brd)[ORDER + 1], double (&Bid)[ORDER + 1])
+{
+    double t = v.z, xr = v.x, xi = v.y;
+#pragma unroll
+    for (int k = 0; k < 2 * ORDER + 1; ++k) {
+        Md[k] += t;
+        t *= x;
+    }
+#pragma unroll
+    for (int k = 0; k < ORDER + 1; ++k) {
+        Brd[k] += xr;
+        Bid[k] += xi;
+        xr *= x;
+        xi *= x;
+    }
+}
+
+// One output entry, sum_wv - sum_w p(x): p by Horner in float-pair
+// arithmetic from its float-pair coefficients (a nearly interpolating fit
+// has large coefficients whose terms cancel, so single floats would not do).
+template <int NB>
+__device__ __forceinline__ float2 subtract_fit(const EntryFF &v, float2 x, const float2 (&fr)[NB],
+                                               const float2 (&fi)[NB])
+{
+    float2 pr = fr[NB - 1], pi = fi[NB - 1];
+#pragma unroll
+    for (int k = NB - 2; k >= 0; --k) {
+        pr = ff_add(ff_mul(pr, x), fr[k]);
+        pi = ff_add(ff_mul(pi, x), fi[k]);
+    }
+    const float2 neg_w = make_float2(-v.z.x, -v.z.y);
+    const float2 orr = ff_add(v.x, ff_mul(neg_w, pr)), oi = ff_add(v.y, ff_mul(neg_w, pi));
+    return make_float2(orr.x + orr.y, oi.x + oi.y);
+}
+
+// Warp per cell (npol divides 32): lane L handles entries L, L + 32, ... of
+// the cell ([nrest][npol], so plane L mod npol); x_j = (2 j - (nrest - 1)) *
+// (1 / nrest) with 1 / nrest as a float pair inv (exact products by FMA).
+template <int ORDER>
+__global__ void __launch_bounds__(256) k_contsub_cell(const void *cube, const double *master, int fp64,
+                                                      const uint8_t *line_free, int64_t ncell, int nrest, int npol,
+                                                      float2 inv, float2 *out)
+{
+    constexpr int NM = 2 * ORDER + 1;
+    constexpr int NB = ORDER + 1;
+    const int lane = threadIdx.x & 31;
+    const int64_t cell = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (cell >= ncell) return;   // whole warps
+    const int64_t e0 = cell * nrest * npol;
+    const int nent = nrest * npol;
+    MomentsFF<ORDER> mo;
+    mo.zero();
+    int nfit = 0;
+    float xmin = 2.f, xmax = -2.f;
+    for (int f = lane; f < nent; f += 32) {
+        const int j = f / npol;
+        if (!line_free[j]) continue;
+        const EntryFF v = entry_ff(cube, master, fp64, e0 + f);
+        if (!(v.z.x > 0.f)) continue;
+        ++nfit;
+        const float2 x = absc_ff(j, nrest, inv);
+        xmin = fminf(xmin, x.x);
+        xmax = fmaxf(xmax, x.x);
+        mo.add(v, x);
+    }
     // sums over the lanes of this lane's plane, in FP64
     double M[NM], Br[NB], Bi[NB];
-#pragma unroll
-    for (int k = 0; k < NM; ++k) M[k] = (double)Ms[k] + (double)Mc[k];
-#pragma unroll
-    for (int k = 0; k < NB; ++k) {
-        Br[k] = (double)Brs[k] + (double)Brc[k];
-        Bi[k] = (double)Bis[k] + (double)Bic[k];
-    }
+    mo.to_double(M, Br, Bi);
     for (int o = 16; o >= npol; o >>= 1) {
         nfit += __shfl_xor_sync(0xffffffffu, nfit, o);
         xmin = fminf(xmin, __shfl_xor_sync(0xffffffffu, xmin, o));
@@ -302,20 +366,7 @@ __global__ void __launch_bounds__(256) k_contsub_cell(const void *cube, const do
             if (!line_free[j]) continue;
             const double3 v = entry_sums(cube, master, fp64, e0 + f);
             if (!(v.z > 0.0)) continue;
-            const double x = (double)(2 * j - (nrest - 1)) * inv_n;
-            double t = v.z, xr = v.x, xi = v.y;
-#pragma unroll
-            for (int k = 0; k < NM; ++k) {
-                Md[k] += t;
-                t *= x;
-            }
-#pragma unroll
-            for (int k = 0; k < NB; ++k) {
-                Brd[k] += xr;
-                Bid[k] += xi;
-                xr *= x;
-                xi *= x;
-            }
+            add_moments_fp64<ORDER>(v, (double)(2 * j - (nrest - 1)) * inv_n, Md, Brd, Bid);
         }
         for (int o = 16; o >= npol; o >>= 1) {
 #pragma unroll
@@ -338,10 +389,7 @@ __global__ void __launch_bounds__(256) k_contsub_cell(const void *cube, const do
     }
     double cr[NB], ci[NB];
     solve_fit<ORDER>(M, Br, Bi, nfit, cr, ci);
-    // the coefficients as float pairs: p(x) by Horner in float-pair
-    // arithmetic (a nearly interpolating fit has large coefficients whose
-    // terms cancel, so single floats would not do)
-    float2 fr[NB], fi[NB];
+    float2 fr[NB], fi[NB];   // the coefficients as float pairs
 #pragma unroll
     for (int k = 0; k < NB; ++k) {
         fr[k] = ff_of(cr[k]);
@@ -349,17 +397,7 @@ __global__ void __launch_bounds__(256) k_contsub_cell(const void *cube, const do
     }
     for (int f = lane; f < nent; f += 32) {
         const int j = f / npol;
-        const EntryFF v = entry_ff(cube, master, fp64, e0 + f);
-        const float2 x = absc(j);
-        float2 pr = fr[NB - 1], pi = fi[NB - 1];
-#pragma unroll
-        for (int k = NB - 2; k >= 0; --k) {
-            pr = ff_add(ff_mul(pr, x), fr[k]);
-            pi = ff_add(ff_mul(pi, x), fi[k]);
-        }
-        const float2 neg_w = make_float2(-v.z.x, -v.z.y);
-        const float2 orr = ff_add(v.x, ff_mul(neg_w, pr)), oi = ff_add(v.y, ff_mul(neg_w, pi));
-        out[e0 + f] = make_float2(orr.x + orr.y, oi.x + oi.y);
+        out[e0 + f] = subtract_fit<NB>(entry_ff(cube, master, fp64, e0 + f), absc_ff(j, nrest, inv), fr, fi);
     }
 }
 

@@ -184,3 +184,30 @@ def test_contsub_kernel_other_plane_counts(V, planes):
             st.close()
         assert (w > 0).sum() > 100
         _kernel_check(got, wv, w, free, order)
+
+
+@pytest.mark.parametrize("planes,nrest", [(1, 1024), (2, 512), (4, 256)])
+def test_contsub_long_spectra(V, planes, nrest):
+    """Cells of 1024 entries (1, 2 or 4 planes of 1024, 512 or 256 rest
+    channels): against the oracle's fit on the same cube, orders 0-3, mixed
+    and FP64 cubes, with a random line-free mask and with a fit set of six
+    channels (the FP64 refit of quadratic and cubic planes)."""
+    from paper_2609_01897_gb300 import synth
+    pols = {1: (1,), 2: (2,), 4: (4,)}[planes]
+    wl = synth.random_case(71 + planes, "cuda", nsrc=6, max_rows=200, npol_choices=pols, nrest=nrest)
+    wl.npol = planes
+    few = np.zeros(nrest, dtype=bool)
+    few[np.linspace(nrest // 8, nrest - nrest // 8, 6).astype(int)] = True
+    for prec in ("mixed", "fp64"):
+        st = _stack(V, wl, V.PREC_MIXED if prec == "mixed" else V.PREC_FP64)
+        try:
+            cube = st.read_cube(device=True, f64=True)
+            wv = (cube["sum_wv"][..., 0] + 1j * cube["sum_wv"][..., 1]).cpu().numpy()
+            w = cube["sum_w"].cpu().numpy()
+            assert (w > 0).sum() > 1000
+            for order in range(4):
+                for free in (_line_free(nrest, order), few):
+                    got = st.contsub(free, order).cpu().numpy()
+                    _kernel_check(got, wv, w, free, order)
+        finally:
+            st.close()
