@@ -22,7 +22,8 @@
 // accumulated as compensated FP32 sums (hi + lo, about 2^-44 relative), and
 // the output is formed in FP32 (the output is a float; its error is about
 // 2^-23 of |sum_wv| + |sum_w p|).  Memory bound: the entries are read twice
-// (the second time mostly from L2) and the output written once.
+// (with thousands of cells in flight, the second time from DRAM as well)
+// and the output written once.
 #include "vista_handle.h"
 
 using namespace vista;
