@@ -54,6 +54,9 @@ def parse():
                    help="batched: rest channels of the cube (0 = 1024; fewer gives a smaller cube for captures)")
     p.add_argument("--fp64-steps", type=int, default=1, help="timed steps of the plain FP64 leg (0 = skip)")
     p.add_argument("--e2e-steps", type=int, default=4, help="timed host-memory steps (0 = skip)")
+    p.add_argument("--e2e-readback", choices=["sparse", "dense"], default="sparse",
+                   help="what each end-to-end step reads back: the touched cube entries (index and sums) or "
+                        "the whole cube")
     p.add_argument("--e2e-gb", type=float, default=24.0,
                    help="pinned host memory for the end-to-end leg: windows are taken in order while their "
                         "host copies fit (GB)")
@@ -606,7 +609,9 @@ def window_io(s, f0, df, nrest):
 def run_e2e(args, wl, tuning, f0, df, ws):
     """Same metric through the public API with pinned HOST buffers: every step
     copies its inputs host->device (inside vista_run) and reads the cube back
-    to host memory.  The windows are taken in order while their pinned host
+    to host memory (by default its touched entries, vista_read_cube_sparse;
+    --e2e-readback dense: the whole cube, overlapping the next step).  The
+    windows are taken in order while their pinned host
     copies fit in --e2e-gb (all of them for the array workloads; for the
     batched stack, whose windows are views into a device pool, a stated
     leading subset)."""
@@ -630,6 +635,7 @@ def run_e2e(args, wl, tuning, f0, df, ws):
     sub = synth.Workload(wl.name, wl.nu, wl.nv, wl.nrest, wl.npol, wl.du, wl.dv, wl.central_freq, host,
                          df, f0)
     ste = open_stack(sub, V.PREC_MIXED, tuning)
+    sparse = args.e2e_readback == "sparse"
     try:
         outs, t0 = None, 0.0
         split = {"queue_ms": 0.0, "device_ms": 0.0, "readback_ms": 0.0}
@@ -646,7 +652,19 @@ def run_e2e(args, wl, tuning, f0, df, ws):
             tb = time.perf_counter()
             if it == 0:
                 # the pinned result buffers are allocated once (first, untimed step)
-                outs = ste.read_cube(device=False, out=outs)
+                outs = ste.read_cube_sparse(out=outs) if sparse else ste.read_cube(device=False, out=outs)
+            elif sparse:
+                # the touched entries only (the same set every step): a
+                # synchronous call, the last step's split into run and readback
+                last = it == args.e2e_steps
+                if last:
+                    torch.cuda.current_stream().synchronize()
+                tc = time.perf_counter()
+                outs = ste.read_cube_sparse(out=outs)
+                if last:
+                    td = time.perf_counter()
+                    split = {"queue_ms": (tb - ta) * 1e3, "device_ms": (tc - tb) * 1e3,
+                             "readback_ms": (td - tc) * 1e3}
             elif it < args.e2e_steps:
                 # every step reads its cube back; the copy overlaps the next step's
                 ste.read_cube_async(outs)
@@ -661,7 +679,9 @@ def run_e2e(args, wl, tuning, f0, df, ws):
         ste.wait_readback()
         t_end = time.perf_counter()
         dt = (t_end - t0) / args.e2e_steps
-        d2h = sum(v.numel() * v.element_size() for v in outs.values())
+        # the arrays read back (and, sparse, the 8-byte count of touched entries)
+        d2h = sum(v.numel() * v.element_size() for v in outs.values()) + (8 if sparse else 0)
+        n_back = int(outs["index"].numel()) if sparse else int(outs["count"].numel())
         h2d = ste.h2d_bytes()   # what vista_run copied for the windows (the last step's; every step's is the same)
     finally:
         ste.close()
@@ -672,6 +692,8 @@ def run_e2e(args, wl, tuning, f0, df, ws):
             "windows": "%d of the %d windows that reach the cube (%d visibilities, %.1f GB pinned on the host)" % (
                 len(host), n_in, n_vis, pinned / 1e9),
             "link_gbs": (h2d + d2h) / dt / 1e9,
+            "readback": ("the %d touched cube entries (index, sums and count: 28 B each)" % n_back if sparse
+                         else "the whole cube (%d entries, 20 B each), overlapping the next step" % n_back),
             # host time between successive steps' starts (the host runs ahead
             # of the device by up to two steps, so single values are not a
             # step's device time; their spread shows this shared machine's noise)

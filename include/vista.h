@@ -34,10 +34,11 @@
 extern "C" {
 #endif
 
-#define VISTA_ABI_VERSION 5   /* 2: vista_add_source_reproject, vista_regrid_rows;
+#define VISTA_ABI_VERSION 6   /* 2: vista_add_source_reproject, vista_regrid_rows;
                                  3: vista_contsub, vista_set_wave_bytes, vista_get_waves;
                                  4: vista_get_h2d_bytes;
-                                 5: vista_read_cube_async, vista_wait_readback */
+                                 5: vista_read_cube_async, vista_wait_readback;
+                                 6: vista_read_cube_sparse */
 #define VISTA_MAX_BINS 4      /* rest bins one input channel may touch */
 #define VISTA_MAX_POL 4
 
@@ -297,6 +298,23 @@ int vista_read_cube_async(vista_stack *h, float *sum_wv, float *sum_w, float *su
  * VISTA_OK at once when none is pending.  E_TIMEOUT if a device-side wait
  * of an earlier run gave up. */
 int vista_wait_readback(vista_stack *h);
+
+/* The cube's touched entries only (a library convention; Eq. 3's sums as
+ * in vista_read_cube): the entries with count > 0, in entry order.  An
+ * entry with count 0 received no contribution and holds zero sums, so they
+ * give the whole cube.  index[i] is the flat entry index
+ * ((iv * nu + iu) * nrest + j) * npol + p of the i-th touched entry.  Its
+ * FP32 sums and count go to sum_wv[2 i], sum_wv[2 i + 1], sum_w[i],
+ * sum_wvv[i] and count[i], with the same values vista_read_cube gives.  Any
+ * sums or count pointer may be NULL to skip that array.  dst_is_device:
+ * 1 = device pointers, 0 = host.  *n_touched gets the number of touched
+ * entries.  cap = 0 only counts them and writes nothing.  With
+ * 0 < cap < *n_touched, nothing is written and the call returns E_RANGE.
+ * Waits for the stream (as vista_read_cube) and returns after the copy.
+ * E_ARG: n_touched NULL, cap < 0, or index NULL with cap > 0.  E_TIMEOUT:
+ * as vista_read_cube. */
+int vista_read_cube_sparse(vista_stack *h, int64_t cap, int64_t *index, float *sum_wv, float *sum_w,
+                           float *sum_wvv, uint32_t *count, int64_t *n_touched, int dst_is_device);
 
 /* Zero the cube and the counters (the lattice stays fixed). */
 int vista_zero_cube(vista_stack *h);

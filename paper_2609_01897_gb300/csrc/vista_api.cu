@@ -485,6 +485,71 @@ extern "C" int vista_wait_readback(vista_stack *h)
     return VISTA_OK;
 }
 
+extern "C" int vista_read_cube_sparse(vista_stack *h, int64_t cap, int64_t *index, float *sum_wv, float *sum_w,
+                                      float *sum_wvv, uint32_t *count, int64_t *n_touched, int dst_is_device)
+{
+    CHECK_HANDLE(h);
+    if (!n_touched) return fail(h, VISTA_E_ARG, "null n_touched");
+    if (cap < 0) return fail(h, VISTA_E_ARG, "cap must be >= 0");
+    if (cap > 0 && !index) return fail(h, VISTA_E_ARG, "null index with cap > 0");
+    cudaError_t e = finish_readback(h);
+    if (e != cudaSuccess) return cuda_fail(h, e, "earlier readback");
+    e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "stream synchronize");
+    int32_t err = 0;
+    e = cudaMemcpy(&err, h->err, sizeof err, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(h, e, "error word read");
+    if (err != 0) return device_fail(h, err);
+    const int fp64 = h->desc.precision == VISTA_PREC_FP64;
+    const int64_t n = h->nentries, ntile = sparse_tiles(n);
+    auto al = [](size_t b) { return (b + 255) & ~(size_t)255; };
+    // scratch: tile counts | tile offsets | total (the touched entries of a
+    // host destination go through the dense readback's scratch, free here)
+    const size_t o_off = al((size_t)ntile * 4), o_tot = o_off + al((size_t)ntile * 8), o_end = o_tot + 256;
+    if ((e = h->b_sparse.ensure(o_end)) != cudaSuccess) return cuda_fail(h, e, "sparse readback scratch");
+    char *b = (char *)h->b_sparse.p;
+    e = launch_sparse_count(h->count, n, (uint32_t *)b, (int64_t *)(b + o_off), (int64_t *)(b + o_tot), h->stream);
+    int64_t total = 0;
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(&total, b + o_tot, sizeof total, cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "sparse readback count");
+    *n_touched = total;
+    if (cap == 0) return VISTA_OK;   // the count only
+    if (total > cap)
+        return fail(h, VISTA_E_RANGE, "the cube has %lld touched entries, more than cap = %lld", (long long)total,
+                    (long long)cap);
+    if (dst_is_device) {
+        e = launch_sparse_write(h->cube, h->cube_master, h->count, fp64, n, (const int64_t *)(b + o_off), cap, index,
+                                sum_wv, sum_w, sum_wvv, count, h->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+        if (e != cudaSuccess) return cuda_fail(h, e, "sparse readback");
+        return VISTA_OK;
+    }
+    // host destination: the touched entries into the scratch, then one copy per array
+    const size_t t = (size_t)total;
+    const size_t o_wv = al(t * 8), o_w = o_wv + al(t * 8), o_vv = o_w + al(t * 4), o_c = o_vv + al(t * 4),
+                 need = o_c + al(t * 4);
+    if ((e = h->b_unpack.ensure(need)) != cudaSuccess) return cuda_fail(h, e, "readback scratch allocation");
+    char *u = (char *)h->b_unpack.p;
+    e = launch_sparse_write(h->cube, h->cube_master, h->count, fp64, n, (const int64_t *)(b + o_off), cap,
+                            (int64_t *)u, sum_wv ? (float *)(u + o_wv) : nullptr, sum_w ? (float *)(u + o_w) : nullptr,
+                            sum_wvv ? (float *)(u + o_vv) : nullptr, count ? (uint32_t *)(u + o_c) : nullptr,
+                            h->stream);
+    if (e == cudaSuccess && t > 0) e = xfer_fork(h);
+    if (e == cudaSuccess && t > 0) {
+        e = cudaMemcpyAsync(index, u, t * 8, cudaMemcpyDeviceToHost, h->xfer[0]);
+        if (e == cudaSuccess && sum_wv) e = cudaMemcpyAsync(sum_wv, u + o_wv, t * 8, cudaMemcpyDeviceToHost, h->xfer[1]);
+        if (e == cudaSuccess && sum_w) e = cudaMemcpyAsync(sum_w, u + o_w, t * 4, cudaMemcpyDeviceToHost, h->xfer[2]);
+        if (e == cudaSuccess && sum_wvv) e = cudaMemcpyAsync(sum_wvv, u + o_vv, t * 4, cudaMemcpyDeviceToHost, h->xfer[3]);
+        if (e == cudaSuccess && count) e = cudaMemcpyAsync(count, u + o_c, t * 4, cudaMemcpyDeviceToHost, h->xfer[0]);
+        if (e == cudaSuccess) e = xfer_join(h);
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "sparse readback");
+    return VISTA_OK;
+}
+
 extern "C" int vista_set_wave_bytes(vista_stack *h, int64_t bytes)
 {
     CHECK_HANDLE(h);
@@ -703,6 +768,7 @@ extern "C" int vista_close(vista_stack *h)
     h->b_guvw.release();
     h->b_regrid.release();
     h->b_contsub.release();
+    h->b_sparse.release();
     delete h;
     return VISTA_OK;
 }

@@ -97,7 +97,7 @@ struct vista_stack {
     uint64_t nvis_since_fold = 0;   // mixed: visibilities stacked since the FP32 partials were last folded
     int32_t *err = nullptr;
     vista::DevBuf b_srcs, b_chf, b_chd, b_recs, b_cells, b_off, b_stage, b_unpack, b_sort, b_rot, b_guvw, b_regrid,
-        b_contsub;
+        b_contsub, b_sparse;
     std::vector<vista::ClassRun> classes;
     std::vector<vista::Copy2D> copies;   // device copies of the last planned run
     std::vector<vista::HostCopy> hcopies;   // host-memory windows of the last run, by wave

@@ -236,6 +236,17 @@ cudaError_t launch_fold(void *cube, double *master, int64_t n, cudaStream_t st);
 cudaError_t launch_unpack(const void *cube, const double *master, const uint32_t *count, int fp64, int64_t n,
                           void *sum_wv, void *sum_w, void *sum_wvv, uint32_t *cnt_out,
                           int out_f64, cudaStream_t st);
+// Sparse readback (the entries with count > 0, in entry order): per tile of
+// 4096 entries the touched count (tile_cnt [ntile]), their exclusive scan
+// (tile_off [ntile]) and the total (one int64 on the device); then each
+// touched entry's index and sums at its position (positions >= cap are not
+// written).
+inline int64_t sparse_tiles(int64_t n) { return (n + 4095) / 4096; }
+cudaError_t launch_sparse_count(const uint32_t *count, int64_t n, uint32_t *tile_cnt, int64_t *tile_off,
+                                int64_t *total, cudaStream_t st);
+cudaError_t launch_sparse_write(const void *cube, const double *master, const uint32_t *count, int fp64, int64_t n,
+                                const int64_t *tile_off, int64_t cap, int64_t *index, float *sum_wv, float *sum_w,
+                                float *sum_wvv, uint32_t *cnt_out, cudaStream_t st);
 cudaError_t launch_debug(const RunArgs &a, int ns, int src, int fp64, double *ph, int32_t *cells,
                          cudaStream_t st);
 

@@ -182,32 +182,40 @@ __global__ void __launch_bounds__(128) stack_fp64(RunArgs a, int only_src, doubl
 
 // ------------------------------------------------------------------ unpack
 
+// Entry i's four sums (re and im of sum wV, sum w, sum w|V|^2) in FP64: the
+// FP64 cube, or the mixed cube's float4 sums since the last checkpoint plus
+// its FP64 master sums.
+__device__ __forceinline__ void entry_value(const void *cube, const double *master, int fp64, int64_t i,
+                                            double (&e)[4])
+{
+    if (fp64) {
+        const double *c = reinterpret_cast<const double *>(cube) + 4 * i;
+        e[0] = c[0];
+        e[1] = c[1];
+        e[2] = c[2];
+        e[3] = c[3];
+        return;
+    }
+    const float4 c = reinterpret_cast<const float4 *>(cube)[i];
+    e[0] = c.x;
+    e[1] = c.y;
+    e[2] = c.z;
+    e[3] = c.w;
+    if (master) {
+        const double *m = master + 4 * i;
+        e[0] += m[0];
+        e[1] += m[1];
+        e[2] += m[2];
+        e[3] += m[3];
+    }
+}
+
 __global__ void unpack_kernel(const void *cube, const double *master, const uint32_t *count, int fp64, int64_t n,
                               void *sum_wv, void *sum_w, void *sum_wvv, uint32_t *cnt_out, int out_f64)
 {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         double e[4];
-        if (fp64) {
-            const double *c = reinterpret_cast<const double *>(cube) + 4 * i;
-            e[0] = c[0];
-            e[1] = c[1];
-            e[2] = c[2];
-            e[3] = c[3];
-        } else {
-            // the float4 sums since the last checkpoint plus the FP64 master sums
-            const float4 c = reinterpret_cast<const float4 *>(cube)[i];
-            e[0] = c.x;
-            e[1] = c.y;
-            e[2] = c.z;
-            e[3] = c.w;
-            if (master) {
-                const double *m = master + 4 * i;
-                e[0] += m[0];
-                e[1] += m[1];
-                e[2] += m[2];
-                e[3] += m[3];
-            }
-        }
+        entry_value(cube, master, fp64, i, e);
         if (out_f64) {
             if (sum_wv) {
                 reinterpret_cast<double *>(sum_wv)[2 * i] = e[0];
@@ -224,6 +232,107 @@ __global__ void unpack_kernel(const void *cube, const double *master, const uint
             if (sum_wvv) reinterpret_cast<float *>(sum_wvv)[i] = (float)e[3];
         }
         if (cnt_out) cnt_out[i] = count[i];
+    }
+}
+
+// Sparse readback: the entries with count > 0, in entry order, in three
+// passes over tiles of SPARSE_TILE consecutive entries (thread t of a block
+// reads entries t, t + 256, ... of its tile, so every load is coalesced):
+// the touched entries of each tile; one block's exclusive scan of the tile
+// counts, with the total at the end; and each tile's touched entries
+// written from its offset on, in entry order (a ballot per warp and a count
+// per warp in shared memory per round of 256 entries).
+constexpr int SPARSE_THREADS = 256, SPARSE_ROUNDS = 16, SPARSE_TILE = SPARSE_THREADS * SPARSE_ROUNDS;
+constexpr int SPARSE_WARPS = SPARSE_THREADS / 32, SCAN_THREADS = 1024;
+static_assert(SPARSE_TILE == 4096, "sparse_tiles() counts tiles of 4096 entries");
+
+__global__ void __launch_bounds__(SPARSE_THREADS) sparse_count_kernel(const uint32_t *count, int64_t n,
+                                                                      uint32_t *tile_cnt)
+{
+    __shared__ int ws[SPARSE_WARPS];
+    const int64_t base = (int64_t)blockIdx.x * SPARSE_TILE;
+    int c = 0;
+    for (int k = 0; k < SPARSE_ROUNDS; ++k) {
+        const int64_t i = base + (int64_t)k * SPARSE_THREADS + threadIdx.x;
+        c += (i < n && count[i] != 0u) ? 1 : 0;
+    }
+    c = __reduce_add_sync(0xffffffffu, c);
+    if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = c;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int t = 0;
+        for (int w = 0; w < SPARSE_WARPS; ++w) t += ws[w];
+        tile_cnt[blockIdx.x] = (uint32_t)t;
+    }
+}
+
+// One block of SCAN_THREADS: thread t sums a contiguous run of tiles, the
+// block scans those sums (warp shuffles, then the warps' totals), and each
+// thread writes its tiles' offsets; the last thread writes the total.
+__global__ void __launch_bounds__(SCAN_THREADS) sparse_scan_kernel(const uint32_t *tile_cnt, int64_t ntile,
+                                                                   int64_t *tile_off, int64_t *total)
+{
+    __shared__ long long wtot[SCAN_THREADS / 32];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int64_t per = (ntile + SCAN_THREADS - 1) / SCAN_THREADS;
+    const int64_t t0 = min((int64_t)threadIdx.x * per, ntile), t1 = min(t0 + per, ntile);
+    long long s = 0;
+    for (int64_t t = t0; t < t1; ++t) s += tile_cnt[t];
+    long long x = s;   // inclusive scan over the warp
+    for (int o = 1; o < 32; o <<= 1) {
+        const long long y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) wtot[wid] = x;
+    __syncthreads();
+    long long before = 0;
+    for (int w = 0; w < wid; ++w) before += wtot[w];
+    long long off = before + x - s;   // exclusive
+    for (int64_t t = t0; t < t1; ++t) {
+        tile_off[t] = off;
+        off += tile_cnt[t];
+    }
+    if (threadIdx.x == SCAN_THREADS - 1) *total = before + x;
+}
+
+__global__ void __launch_bounds__(SPARSE_THREADS) sparse_write_kernel(const void *cube, const double *master,
+                                                                      const uint32_t *count, int fp64, int64_t n,
+                                                                      const int64_t *tile_off, int64_t cap,
+                                                                      int64_t *idx_out, float *sum_wv, float *sum_w,
+                                                                      float *sum_wvv, uint32_t *cnt_out)
+{
+    __shared__ int ws[SPARSE_WARPS];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int64_t base = (int64_t)blockIdx.x * SPARSE_TILE;
+    int64_t pos = tile_off[blockIdx.x];
+    for (int k = 0; k < SPARSE_ROUNDS; ++k) {
+        const int64_t i = base + (int64_t)k * SPARSE_THREADS + threadIdx.x;
+        const uint32_t c = i < n ? count[i] : 0u;
+        const unsigned bal = __ballot_sync(0xffffffffu, c != 0u);
+        if (lane == 0) ws[wid] = __popc(bal);
+        __syncthreads();
+        int before = 0, all = 0;
+        for (int w = 0; w < SPARSE_WARPS; ++w) {
+            before += w < wid ? ws[w] : 0;
+            all += ws[w];
+        }
+        if (c != 0u) {
+            const int64_t q = pos + before + __popc(bal & ((1u << lane) - 1u));
+            if (q < cap) {
+                double e[4];
+                entry_value(cube, master, fp64, i, e);
+                idx_out[q] = i;
+                if (sum_wv) {
+                    sum_wv[2 * q] = (float)e[0];
+                    sum_wv[2 * q + 1] = (float)e[1];
+                }
+                if (sum_w) sum_w[q] = (float)e[2];
+                if (sum_wvv) sum_wvv[q] = (float)e[3];
+                if (cnt_out) cnt_out[q] = c;
+            }
+        }
+        pos += all;
+        __syncthreads();   // ws is written again in the next round
     }
 }
 
@@ -275,6 +384,27 @@ cudaError_t launch_unpack(const void *cube, const double *master, const uint32_t
     if (blocks > 152 * 16) blocks = 152 * 16;
     unpack_kernel<<<(unsigned)blocks, 256, 0, st>>>(cube, master, count, fp64, n, sum_wv, sum_w, sum_wvv, cnt_out,
                                                     out_f64);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sparse_count(const uint32_t *count, int64_t n, uint32_t *tile_cnt, int64_t *tile_off,
+                                int64_t *total, cudaStream_t st)
+{
+    const int64_t ntile = sparse_tiles(n);
+    if (ntile == 0) return cudaMemsetAsync(total, 0, sizeof(int64_t), st);
+    sparse_count_kernel<<<(unsigned)ntile, SPARSE_THREADS, 0, st>>>(count, n, tile_cnt);
+    sparse_scan_kernel<<<1, SCAN_THREADS, 0, st>>>(tile_cnt, ntile, tile_off, total);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sparse_write(const void *cube, const double *master, const uint32_t *count, int fp64, int64_t n,
+                                const int64_t *tile_off, int64_t cap, int64_t *index, float *sum_wv, float *sum_w,
+                                float *sum_wvv, uint32_t *cnt_out, cudaStream_t st)
+{
+    const int64_t ntile = sparse_tiles(n);
+    if (ntile == 0 || cap == 0) return cudaSuccess;
+    sparse_write_kernel<<<(unsigned)ntile, SPARSE_THREADS, 0, st>>>(cube, master, count, fp64, n, tile_off, cap, index,
+                                                                   sum_wv, sum_w, sum_wvv, cnt_out);
     return cudaGetLastError();
 }
 

@@ -83,6 +83,7 @@ SIGNATURES = {
     "vista_get_h2d_bytes": (C.c_int, [_P, C.POINTER(C.c_int64)]),
     "vista_read_cube_async": (C.c_int, [_P, _P, _P, _P, _P]),
     "vista_wait_readback": (C.c_int, [_P]),
+    "vista_read_cube_sparse": (C.c_int, [_P, C.c_int64, _P, _P, _P, _P, _P, C.POINTER(C.c_int64), C.c_int]),
     "vista_run": (C.c_int, [_P]),
     "vista_read_cube": (C.c_int, [_P, _P, _P, _P, _P, C.c_int]),
     "vista_read_cube_f64": (C.c_int, [_P, _P, _P, _P, _P, C.c_int]),
@@ -307,6 +308,41 @@ class Stack:
             self.h, _ptr(out.get("sum_wv")), _ptr(out.get("sum_w")), _ptr(out.get("sum_wvv")),
             _ptr(out.get("count"))), self.h)
         return out
+
+    def read_cube_sparse(self, device=False, out=None):
+        """The touched cube entries (count > 0) in entry order
+        (vista_read_cube_sparse): index int64 [n] (the flat entry index into
+        [nv][nu][nrest][npol]), sum_wv float32 [n, 2], sum_w and sum_wvv
+        float32 [n], count int32 [n]; on the device, or in pinned host memory.
+        `out` (a dict from an earlier call) is written in place when it holds
+        at least n entries.  Returns the first n rows of each array."""
+        L, n = lib(), C.c_int64(0)
+        dev = 1 if device else 0
+
+        def alloc(cap):
+            kw = {"device": "cuda"} if device else {"pin_memory": torch.cuda.is_available()}
+            return {"index": torch.empty(cap, dtype=torch.int64, **kw),
+                    "sum_wv": torch.empty((cap, 2), dtype=torch.float32, **kw),
+                    "sum_w": torch.empty(cap, dtype=torch.float32, **kw),
+                    "sum_wvv": torch.empty(cap, dtype=torch.float32, **kw),
+                    "count": torch.empty(cap, dtype=torch.int32, **kw)}
+
+        if out is None or any(out[k].is_cuda != bool(device) for k in out):
+            _check("vista_read_cube_sparse", L.vista_read_cube_sparse(self.h, 0, None, None, None, None, None,
+                                                                      C.byref(n), dev), self.h)
+            out = alloc(n.value)
+
+        def call(o):
+            return L.vista_read_cube_sparse(self.h, int(o["index"].shape[0]), _ptr(o["index"]), _ptr(o["sum_wv"]),
+                                            _ptr(o["sum_w"]), _ptr(o["sum_wvv"]), _ptr(o["count"]), C.byref(n), dev)
+
+        rc = call(out)
+        if rc == E_RANGE and n.value > int(out["index"].shape[0]):
+            out = alloc(n.value)
+            rc = call(out)
+        _check("vista_read_cube_sparse", rc, self.h)
+        self._inflight = []
+        return {k: v[:n.value] for k, v in out.items()}
 
     def wait_readback(self):
         _check("vista_wait_readback", lib().vista_wait_readback(self.h), self.h)

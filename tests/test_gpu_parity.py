@@ -298,6 +298,53 @@ def test_failed_allocation_leaves_no_pending_error(V, tiny):
     H.compare(g, o, H.TOL_MIXED, what="tiny after a refused allocation")
 
 
+@pytest.mark.parametrize("prec", ["mixed", "fp64"])
+def test_sparse_readback_matches_dense(V, tiny, prec):
+    """vista_read_cube_sparse: the entries with count > 0, in entry order, with
+    the values vista_read_cube gives (bit for bit), into host and device
+    arrays; the entries with count 0 hold zero sums; cap = 0 only counts, a
+    smaller cap returns E_RANGE with the count, bad arguments E_ARG; a zeroed
+    cube has no touched entry."""
+    import ctypes as C
+    p = V.PREC_MIXED if prec == "mixed" else V.PREC_FP64
+    st = V.Stack(tiny.nu, tiny.nv, tiny.nrest, tiny.npol, tiny.du, tiny.dv, central_freq=tiny.central_freq,
+                 precision=p)
+    try:
+        for s in tiny.spws:
+            st.add_source(s.uvw, s.freqs, s.vis, s.weights, s.flags, l=s.l, m=s.m, z=s.z)
+        st.run()
+        dense = st.read_cube(device=True)
+        cnt = dense["count"].reshape(-1)
+        want = torch.nonzero(cnt != 0).reshape(-1)
+        assert 0 < want.numel() < cnt.numel()
+        flat = {"sum_wv": dense["sum_wv"].reshape(-1, 2), "sum_w": dense["sum_w"].reshape(-1),
+                "sum_wvv": dense["sum_wvv"].reshape(-1), "count": cnt}
+        for k in ("sum_wv", "sum_w", "sum_wvv"):
+            assert (flat[k][cnt == 0] == 0).all(), k
+        out = None
+        for device in (False, True, False):
+            sp = st.read_cube_sparse(device=device, out=out)
+            assert sp["index"].is_cuda == device
+            assert torch.equal(sp["index"].cuda(), want)
+            for k in ("sum_wv", "sum_w", "sum_wvv", "count"):
+                assert torch.equal(sp[k].cuda(), flat[k][want]), k
+            out = sp if not device else None
+        L, n = V.lib(), C.c_int64(-1)
+        assert L.vista_read_cube_sparse(st.h, 0, None, None, None, None, None, C.byref(n), 0) == V.VISTA_OK
+        assert n.value == want.numel()
+        small = torch.empty(5, dtype=torch.int64, pin_memory=True)
+        n.value = -1
+        assert L.vista_read_cube_sparse(st.h, 5, small.data_ptr(), None, None, None, None, C.byref(n), 0) == V.E_RANGE
+        assert n.value == want.numel() and "touched" in V.last_error(st.h)
+        assert L.vista_read_cube_sparse(st.h, -1, None, None, None, None, None, C.byref(n), 0) == V.E_ARG
+        assert L.vista_read_cube_sparse(st.h, 5, None, None, None, None, None, C.byref(n), 0) == V.E_ARG
+        assert L.vista_read_cube_sparse(st.h, 5, small.data_ptr(), None, None, None, None, None, 0) == V.E_ARG
+        st.zero()
+        assert st.read_cube_sparse()["index"].numel() == 0
+    finally:
+        st.close()
+
+
 def test_all_flagged_and_empty(V, tiny):
     s = tiny.spws[0]
     st = V.Stack(tiny.nu, tiny.nv, tiny.nrest, tiny.npol, tiny.du, tiny.dv, central_freq=tiny.central_freq)

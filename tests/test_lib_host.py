@@ -34,7 +34,7 @@ def test_exports_every_declared_symbol(V):
     for n in names:
         assert hasattr(L, n), n
     assert set(names) == set(V.SIGNATURES), set(names) ^ set(V.SIGNATURES)
-    assert V.lib().vista_abi_version() == 5
+    assert V.lib().vista_abi_version() == 6
 
 
 def test_null_and_closed_handles(V):
