@@ -640,23 +640,25 @@ def run_e2e(args, wl, tuning, f0, df, ws):
         outs, t0 = None, 0.0
         split = {"queue_ms": 0.0, "device_ms": 0.0, "readback_ms": 0.0}
         starts = []
-        for it in range(1 + args.e2e_steps):
-            if it == 1:
+        # as many untimed warm-up steps as the main timing (the first of them
+        # allocates the pinned result buffers)
+        nw = max(1, args.warmup)
+        for it in range(nw + args.e2e_steps):
+            if it == nw:
                 torch.cuda.synchronize()
                 barrier(ws)
                 t0 = time.perf_counter()
             ta = time.perf_counter()
-            if it >= 1:
+            if it >= nw:
                 starts.append(ta)
             one_step(ste, sub)
             tb = time.perf_counter()
-            if it == 0:
-                # the pinned result buffers are allocated once (first, untimed step)
+            if it < nw:
                 outs = ste.read_cube_sparse(out=outs) if sparse else ste.read_cube(device=False, out=outs)
             elif sparse:
                 # the touched entries only (the same set every step): a
                 # synchronous call, the last step's split into run and readback
-                last = it == args.e2e_steps
+                last = it == nw + args.e2e_steps - 1
                 if last:
                     torch.cuda.current_stream().synchronize()
                 tc = time.perf_counter()
@@ -665,7 +667,7 @@ def run_e2e(args, wl, tuning, f0, df, ws):
                     td = time.perf_counter()
                     split = {"queue_ms": (tb - ta) * 1e3, "device_ms": (tc - tb) * 1e3,
                              "readback_ms": (td - tc) * 1e3}
-            elif it < args.e2e_steps:
+            elif it < nw + args.e2e_steps - 1:
                 # every step reads its cube back; the copy overlaps the next step's
                 ste.read_cube_async(outs)
             else:
