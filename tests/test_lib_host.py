@@ -142,3 +142,62 @@ def test_noalloc_rejects_misaligned_outputs_without_gpu(V):
                                (0x10000, 0x20004, "count"), (0x10000, 0x20002, "count")):
         assert L.vista_stack_noalloc(C.byref(d), C.byref(s), cube4, count) == V.E_ARG
         assert what in V.last_error(None)
+
+
+def test_sparse_readback_binding_counts_allocates_and_retries(V, monkeypatch):
+    """Stack.read_cube_sparse's host logic (the binding only), against a fake
+    library that keeps vista_read_cube_sparse's contract on an 8-entry cube:
+    without buffers it asks for the count (cap = 0) and then allocates; given
+    buffers too small it gets E_RANGE and the count, allocates and calls
+    again; it returns the first n rows; a real error is raised."""
+    import torch
+    counts = np.array([0, 3, 0, 0, 7, 1, 0, 2], dtype=np.uint32)
+    touched = [int(i) for i in np.nonzero(counts)[0]]
+    n = len(touched)
+    caps, fail = [], {"rc": None}
+
+    class FakeLib:
+        def vista_read_cube_sparse(self, h, cap, idx, wv, w, vv, c, nref, dev):
+            caps.append(cap)
+            if fail["rc"] is not None:
+                return fail["rc"]
+            nref._obj.value = n
+            if cap == 0:
+                return V.VISTA_OK
+            if cap < n:
+                return V.E_RANGE
+            (C.c_int64 * n).from_address(idx)[:] = touched
+            (C.c_float * (2 * n)).from_address(wv)[:] = [float(v) for i in touched for v in (i, -i)]
+            (C.c_float * n).from_address(w)[:] = [10.0 * i for i in touched]
+            (C.c_float * n).from_address(vv)[:] = [100.0 * i for i in touched]
+            (C.c_int32 * n).from_address(c)[:] = [int(counts[i]) for i in touched]
+            return V.VISTA_OK
+
+        def vista_last_error(self, h):
+            return b"fake failure"
+
+    monkeypatch.setattr(V, "_lib", FakeLib())
+    st = V.Stack.__new__(V.Stack)
+    st.h, st._inflight = None, []
+
+    def check(sp):
+        assert sp["index"].tolist() == touched
+        assert sp["sum_wv"].tolist() == [[float(i), float(-i)] for i in touched]
+        assert sp["sum_w"].tolist() == [10.0 * i for i in touched]
+        assert sp["count"].tolist() == [int(counts[i]) for i in touched]
+        assert not sp["index"].is_cuda
+
+    sp = st.read_cube_sparse()
+    assert caps == [0, n]
+    check(sp)
+    sp = st.read_cube_sparse(out=sp)           # reused in place
+    assert caps[2:] == [n]
+    check(sp)
+    small = {k: v[:2] for k, v in sp.items()}
+    sp = st.read_cube_sparse(out=small)        # too small: E_RANGE, then a buffer of n
+    assert caps[3:] == [2, n]
+    check(sp)
+    fail["rc"] = V.E_CUDA
+    with pytest.raises(V.VistaError) as e:
+        st.read_cube_sparse(out=sp)
+    assert e.value.code == V.E_CUDA and "fake failure" in str(e.value)
